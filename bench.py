@@ -1,0 +1,349 @@
+"""Benchmark of CPA singular value shrinkage on one or more GB300s.
+
+One step = one full shrinkage (every stage of Algorithm 1: operand split,
+Gram, Lambda_max power iteration, coefficients, shift, recurrence with fused
+accumulation, final product) of one synthetic matrix, through the C ABI.
+
+Default workload: the 1024 x 1024 RPCA frame (D = L0 + S0, rank-30
+low-rank part plus 5 % +-U[5,10] outliers, soft threshold 1/mu, L = 30 terms,
+Lambda_max computed on the device).  Inputs rotate over a set of distinct
+matrices whose total size exceeds the 129 MB L2, so no step starts from a
+warm cache.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16|bf16x3|fp32]
+                  [--workload rpca_frame|single_lowrank|video_background]
+                  [--impl reference]
+
+Prints ONE JSON line.  `--impl reference` times the FP64 CPU oracle (the
+paper has no code to run) on a bounded row sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SVT matrices/sec & tensor-pipe % at ≤1e-3 rel-Frob err: learned+BF16 vs plain FP32 CPA"
+L2_BYTES = 129 * 1024 * 1024
+SEED = 0x1705071120000000
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d["bf16_tflops_sustained"], "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+def make_workload(name, index=0):
+    from paper_1705_07112_gb300 import inputs
+    if name == "rpca_frame":
+        return inputs.rpca_frame(seed_index=index)
+    if name == "single_lowrank":
+        return inputs.single_lowrank(seed_index=index)
+    if name == "video_background":
+        return inputs.video_background(seed_index=index)
+    raise SystemExit("unknown workload %s" % name)
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl != "reference" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value, device=None):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- CPU oracle
+
+def oracle_rows_rate(w, rows, L):
+    """Time the FP64 oracle producing `rows` rows (m >= n) or columns of the
+    shrinkage through its vector form; returns (matrices/s, seconds, cores)."""
+    import oracle as O
+    X64 = w.X.astype(np.float64)
+    m, n = X64.shape
+    s = O.Shrink(w.shrink.kind, w.shrink.tau, w.shrink.c, w.shrink.eps, w.shrink.noise)
+    t0 = time.perf_counter()
+    lam = O.lambda_bound(X64, w.power_iters, 0.01, O.start_vector(SEED, min(m, n)))["lam"]
+    for i in range(rows):
+        v = X64[i % m] if m >= n else X64[:, i % n]
+        O.cpa_vec(X64, s, L, lam, v)
+    dt = time.perf_counter() - t0
+    frac = rows / float(m if m >= n else n)
+    return frac / dt, dt, 1
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    w = make_workload(args.workload)
+    m, n = w.X.shape
+    rows = args.ref_rows
+    times = []
+    for it in range(args.warmup + args.steps):
+        rate, dt, cores = oracle_rows_rate(w, rows, w.L)
+        if it >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = args.steps * rows / float(m if m >= n else n) / tot
+    sample = "%d of %d output %s per step via the oracle's vector form (plus its FP64 power-iteration bound)" % (
+        rows, m if m >= n else n, "rows" if m >= n else "columns")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w, args, reference=True),
+            "cpu_baseline": {"value": value, "unit": "matrices/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(w, args, reference=False):
+    m, n = w.X.shape
+    kinds = {0: "hard", 1: "soft", 2: "weighted_soft"}
+    cfg = {"workload": w.name, "m": m, "n": n, "L": w.L, "shrink": kinds[w.shrink.kind], "tau": w.shrink.tau,
+           "lambda_max": "device power iteration, %d steps, +1%% margin" % w.power_iters}
+    if not reference:
+        cfg["prec"] = args.prec
+        cfg["cuda_graph"] = not args.no_graph
+    return cfg
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args, world, rank, local):
+    import torch
+
+    import paper_1705_07112_gb300 as cpa
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks = load_peaks()
+    w0 = make_workload(args.workload, 0)
+    m, n = w0.X.shape
+    per = m * n * 4
+    n_in = max(2, min(64, -(-2 * L2_BYTES // per) if per < L2_BYTES else 2))
+    Xs = [torch.from_numpy(make_workload(args.workload, i + 1000 * rank).X).to(dev) for i in range(n_in)]
+    Y = torch.empty((m, n), dtype=torch.float32, device=dev)
+    h = cpa.Handle(local)
+    shrink = w0.shrink
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i, X=None, Yo=None):
+        cpa.cpa_svt(h, Xs[i % n_in] if X is None else X, shrink, w0.L, 0.0, args.prec,
+                    Y=Y if Yo is None else Yo, stream=stream)
+
+    # warm-up (allocates the workspace once)
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+
+    graphs = None
+    if not args.no_graph:
+        graphs = []
+        for i in range(n_in):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                cpa.cpa_svt(h, Xs[i], shrink, w0.L, 0.0, args.prec, Y=Y,
+                            stream=torch.cuda.current_stream(dev))
+            graphs.append(g)
+        for i in range(min(args.warmup, n_in)):
+            graphs[i].replay()
+        torch.cuda.synchronize()
+
+    # per-stage device time of one pass (events on the launching stream)
+    cpa.cpa_profile_read(h, reset=True)
+    cpa.cpa_profile_enable(h, True)
+    for i in range(args.steps):
+        step(i)
+    prof = cpa.cpa_profile_read(h, reset=True)
+    cpa.cpa_profile_enable(h, False)
+    launches_per_step = sum(v["launches"] for v in prof.values()) / args.steps
+
+    # timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        if graphs is not None:
+            graphs[i % n_in].replay()
+        else:
+            step(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    barrier(world)
+    clk = clocks.stop()
+    ms_max = max_over_ranks(world, ms, dev)
+    value = world * args.steps / (ms_max / 1e3)
+
+    # end to end through the public API from pinned host memory
+    hx = [torch.empty((m, n), dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    for k in range(2):
+        hx[k].copy_(Xs[k].cpu())
+    hy = torch.empty((m, n), dtype=torch.float32, pin_memory=True)
+    Xd = torch.empty((m, n), dtype=torch.float32, device=dev)
+    for i in range(2):
+        Xd.copy_(hx[i % 2], non_blocking=True)
+        step(0, Xd, Y)
+        hy.copy_(Y, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        Xd.copy_(hx[i % 2], non_blocking=True)
+        step(0, Xd, Y)
+        hy.copy_(Y, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0, dev)
+    e2e = {"value": world * args.steps / e2e_s, "unit": "matrices/s", "h2d_bytes_per_step": m * n * 4,
+           "d2h_bytes_per_step": m * n * 4}
+
+    # roofline of the dominant kernel: one recurrence product, 2 p^3 flops
+    p = min(m, n)
+    rec = prof["recur"]
+    rec_ms = rec["ms"] / max(1, rec["launches"])
+    flops = 2.0 * p ** 3
+    achieved = flops / (rec_ms / 1e3) / 1e12 if rec_ms > 0 else None
+    peak = peaks["bf16_tflops"] if args.prec != "fp32" else None
+    roof = {"kernel": "recurrence product (tcgen05)" if args.prec != "fp32" else "recurrence product (FP32 SIMT)",
+            "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if (achieved and peak) else None, "traffic": None,
+            "flops_per_launch": flops, "ms_per_launch": rec_ms,
+            "peak_source": "%s bf16 burst" % peaks["source"],
+            "stage_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()}}
+
+    line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3", "tf32": "tf32"}[args.prec],
+            "data": "synthetic", "config": workload_config(w0, args), "roofline": roof, "e2e": e2e,
+            "gpu_launches": int(round(launches_per_step * args.steps)), "clocks": clk}
+    line["config"]["inputs"] = "%d distinct inputs, %.0f MB total > L2 (129 MB)" % (n_in, n_in * per / 1e6)
+    line["config"]["parallelism"] = "replicas x%d" % world
+
+    if rank == 0 and not args.no_cpu_baseline:
+        wb = make_workload(args.workload, 0)
+        rate, dt, cores = oracle_rows_rate(wb, args.cpu_rows, wb.L)
+        line["cpu_baseline"] = {"value": rate, "unit": "matrices/s", "cores": cores, "kind": "oracle",
+                                "sample": "%d of %d output rows through the FP64 oracle's vector form, "
+                                          "%.1f s" % (args.cpu_rows, max(m, n) if m < n else m, dt)}
+    h.close()
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rpca_frame")
+    ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16", "bf16x3"])
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=256)
+    ap.add_argument("--ref-rows", type=int, default=32)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, world, rank)
+        return run_gpu(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,225 @@
+/*
+ * cpa.h -- C ABI of the GB300 (sm_103a) library for CPA-based singular value
+ * shrinkage (Onuki et al., "Fast Singular Value Shrinkage with Chebyshev
+ * Polynomial Approximation Based on Signal Sparsity", arXiv 1705.07112).
+ *
+ * The library computes, for a real m x n matrix X,
+ *
+ *     G_hat(X) = X H_hat(X^T X)        (m >= n)
+ *     G_hat(X) = H_hat(X X^T) X        (m <  n)
+ *
+ * with H_hat(G) = c_0/2 Id + sum_{k=1}^{L-1} c_k Psi_k(B_hat), B_hat =
+ * (2/lambda_max) G - Id, the matrix Chebyshev polynomials Psi_k built by the
+ * three-term recurrence Psi_k = 2 B_hat Psi_{k-1} - Psi_{k-2} (Section III-B,
+ * Algorithm 1, Eqs. sing_shrink_from_eig_shrink, chebychev_series_matrix,
+ * transform_lamB, cheby_matrix_eigen_saiki3, recurrence_our_method) and c_k
+ * the shifted Chebyshev coefficients of h(x) = g(sqrt x)/sqrt x (Eq.
+ * chebychev_coeff_shifted).  It approximates the exact shrinkage
+ * G(X) = U diag(g(sigma_i)) V^T (Eq. sing_shrink_exact) without an SVD.
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are row-major FP32 with a leading dimension in elements
+ *     (ld >= number of columns).  Pointers named d* are DEVICE pointers
+ *     owned by the caller; the library never frees them.
+ *   - "L" is the number of Chebyshev terms (the paper's alpha): terms
+ *     k = 0..L-1, polynomial degree L-1, L-2 recurrence products.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = the legacy default stream) unless they return a host value.
+ *   - Every call returns a cpa_status and never throws or aborts.  On an
+ *     argument error nothing is launched and no output is written.
+ *   - A handle owns its device workspace; one handle must not be used from
+ *     two host threads at once.  Different handles are independent.
+ */
+#ifndef CPA_H
+#define CPA_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CPA_API __attribute__((visibility("default")))
+#else
+#define CPA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CPA_OK = 0,
+    CPA_ERR_INVALID_ARG = 1,   /* bad size, pointer, L, lambda or option        */
+    CPA_ERR_CUDA = 2,          /* a CUDA runtime/driver call failed             */
+    CPA_ERR_NO_MEMORY = 3,     /* workspace allocation failed                   */
+    CPA_ERR_NONFINITE = 4,     /* NaN/Inf met in the input or the bound         */
+    CPA_ERR_BOUND = 5,         /* lambda_max bound invalid (not > 0)            */
+    CPA_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up            */
+    CPA_ERR_UNSUPPORTED = 7    /* option not available on this device/build     */
+} cpa_status;
+
+/* Shrinkage kinds of the generic response h(x; W, tau) = (sqrt x - W)/sqrt x
+ * when sqrt x > tau, else 0 (Section IV-A, Eq. filter_response_ours). */
+typedef enum {
+    CPA_HARD = 0,   /* W = 0,     threshold tau          g(s) = s [s > tau]     */
+    CPA_SOFT = 1,   /* W = tau,   threshold tau          g(s) = max(s - tau, 0) */
+    CPA_WSOFT = 2   /* W = w(x),  threshold w(x),  w(x) = c / (sqrt(max(x - noise, 0)) + eps) */
+} cpa_kind;
+
+/* Arithmetic of the dense products (Gram, recurrence, final product). */
+typedef enum {
+    CPA_FP32 = 0,    /* FP32 CUDA-core FMA throughout ("plain FP32 CPA")        */
+    CPA_TF32 = 1,    /* tcgen05 kind::tf32 tensor cores, FP32 accumulate        */
+    CPA_BF16 = 2,    /* tcgen05 kind::f16, FP32 accumulate: recurrence in BF16,
+                        Gram and final product with the BF16 hi/lo split      */
+    CPA_BF16X3 = 3   /* every product with the BF16 hi/lo split
+                        (hi*hi + hi*lo + lo*hi), FP32 accumulate               */
+} cpa_prec;
+
+typedef struct {
+    int kind;       /* cpa_kind                                                 */
+    double tau;     /* HARD/SOFT threshold on sigma (>= 0)                      */
+    double c;       /* WSOFT weight numerator (>= 0)                            */
+    double eps;     /* WSOFT weight regulariser (> 0)                           */
+    double noise;   /* WSOFT noise energy subtracted from sigma^2 (>= 0)        */
+} cpa_shrink;
+
+/* Optional sparsity-based reduction (Eqs. sing_shrink_exact_sparse and
+ * threshold_components): Phi = T G T^T, entries with |Phi_ij| < eps set to 0,
+ * result X T^T H_hat(Phi_) T.  Pass NULL for "off" (T = Id, no threshold). */
+typedef enum {
+    CPA_T_IDENTITY = 0,
+    CPA_T_HAAR1_LOWPASS = 1,   /* one-level Haar DWT, high band set to zero     */
+    CPA_T_BLOCK_DCT8 = 2,      /* 8 x 8 block-diagonal orthonormal DCT-II       */
+    CPA_T_DCT = 3              /* full orthonormal DCT-II                       */
+} cpa_transform;
+
+typedef enum {
+    CPA_SPARSE_OFF = 0,        /* no entry threshold                            */
+    CPA_SPARSE_ABS = 1,        /* keep |Phi_ij| >= eps_or_frac                  */
+    CPA_SPARSE_TOPK = 2        /* eps = k-th largest |Phi_ij|, k = frac * p^2   */
+} cpa_sparse_mode;
+
+typedef struct {
+    int transform;       /* cpa_transform                                        */
+    int mode;            /* cpa_sparse_mode                                      */
+    double eps_or_frac;  /* absolute threshold or fraction of entries kept       */
+} cpa_sparsify;
+
+typedef struct cpa_ctx *cpa_handle;
+
+/* Create a handle bound to CUDA device `device`.  Allocates nothing on the
+ * device until the first call that needs workspace. */
+CPA_API cpa_status cpa_create(cpa_handle *out, int device);
+
+/* Free the handle and its workspace (synchronises the device first). */
+CPA_API cpa_status cpa_destroy(cpa_handle h);
+
+/* Static string for a status code. */
+CPA_API const char *cpa_status_string(cpa_status s);
+
+/* Text of the last CUDA failure seen by the calling thread ("" if none). */
+CPA_API const char *cpa_last_error(void);
+
+/* Shifted Chebyshev coefficients (Eq. chebychev_coeff_shifted), host FP64:
+ *   c_k = (2/L) sum_{l=1}^{L} cos(k theta_l) h(lambda_max/2 (cos theta_l + 1)),
+ *   theta_l = pi (l - 1/2)/L,  k = 0..L-1.
+ * c_out: host array of L doubles.  Errors: INVALID_ARG if L < 1, L > 4096,
+ * lambda_max not > 0, or the shrink parameters are out of range. */
+CPA_API cpa_status cpa_coeffs(const cpa_shrink *s, int L, double lambda_max, double *c_out);
+
+/* Upper estimate of Lambda_max, the largest eigenvalue of the Gram matrix G
+ * of the smaller side of X (Algorithm 1's interval bound; the paper does not
+ * say how it is computed).  Definition: `iters` power iterations
+ * v <- G v / |G v| from the start vector v0_i = u_i - 1/2 (u_i output i of
+ * SplitMix64 seeded with 0x1705071120000000, top 53 bits scaled to [0,1)),
+ * then w = G v, theta = v.w, r = |w - theta v| and
+ *     lambda = min((theta + r) * 1.01, trace G).
+ * G is formed in FP32 on the device; theta, r and the trace are summed in
+ * FP64.  Synchronises `stream` and writes the bound to *lambda_out (host).
+ * Errors: INVALID_ARG (sizes, iters < 0), NONFINITE (NaN/Inf in X). */
+CPA_API cpa_status cpa_lambda_bound(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t ldx,
+                            int iters, double *lambda_out, void *stream);
+
+/* CPA singular value shrinkage of one matrix (Algorithm 1).
+ *   dX: m x n input (device), dY: m x n output (device; must not overlap
+ *   dX, INVALID_ARG otherwise), lambda_max: interval bound; <= 0 means "compute it on the
+ *   device" with the definition of cpa_lambda_bound and iters = 20, in which
+ *   case the coefficients are also formed on the device (FP64) and the whole
+ *   call stays asynchronous.  prec: cpa_prec.  sp: NULL or sparsity option.
+ * Errors: INVALID_ARG, UNSUPPORTED (prec not built for this device),
+ * NO_MEMORY, CUDA.  Device-side failures of a computed bound (non-finite or
+ * non-positive) are reported by the next cpa_get_lambda on the handle. */
+CPA_API cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t ldx,
+                   const cpa_shrink *s, int L, double lambda_max, int prec,
+                   const cpa_sparsify *sp, float *dY, int64_t ldy, void *stream);
+
+/* The Lambda_max used by the last cpa_svt on this handle (synchronises
+ * `stream`).  Returns NONFINITE / BOUND if the device-computed bound was
+ * not a positive finite number (the output of that call is then unusable). */
+CPA_API cpa_status cpa_get_lambda(cpa_handle h, double *lambda_out, void *stream);
+
+/* The L coefficients used by the last cpa_svt (synchronises `stream`). */
+CPA_API cpa_status cpa_get_coeffs(cpa_handle h, double *c_out, int L, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Diagnostics: per-stage device time and kernel-launch counts.
+ * When enabled, every stage of cpa_svt is bracketed by CUDA events recorded
+ * on the call's stream (each recurrence product separately), so the average
+ * device time of one launch of a stage is ms[stage] / launches[stage].
+ * Launch counts are kept whether or not timing is enabled.  Not for use while
+ * the stream is being captured into a CUDA graph.
+ * ------------------------------------------------------------------------- */
+typedef enum {
+    CPA_STAGE_PREP = 0,    /* FP32 -> BF16 hi/lo operand splits              */
+    CPA_STAGE_GRAM = 1,    /* Gram product                                   */
+    CPA_STAGE_BOUND = 2,   /* Lambda_max power iteration                     */
+    CPA_STAGE_COEFF = 3,   /* device Chebyshev coefficients                  */
+    CPA_STAGE_SHIFT = 4,   /* B_hat, Psi_1 and the initial sum               */
+    CPA_STAGE_RECUR = 5,   /* recurrence products with fused accumulation    */
+    CPA_STAGE_APPLY = 6,   /* final product                                  */
+    CPA_NSTAGES = 7
+} cpa_stage;
+
+CPA_API cpa_status cpa_profile_enable(cpa_handle h, int enable);
+
+/* Synchronises the device; ms and launches: host arrays of CPA_NSTAGES
+ * (either may be NULL).  reset != 0 clears the accumulators afterwards. */
+CPA_API cpa_status cpa_profile_read(cpa_handle h, double *ms, int64_t *launches, int reset);
+
+/* ---------------------------------------------------------------------------
+ * Batched shrinkage of many small independent matrices (patch groups), one
+ * persistent launch.  The matrices live packed in one device buffer: matrix
+ * i starts at element offset off[i] and is row-major m[i] x n[i] with
+ * leading dimension n[i]; the output uses the same offsets in dY.
+ *
+ * A plan uploads the descriptor table once (shapes, offsets, per-matrix L);
+ * the same plan can be run many times on new data, and a run can be captured
+ * in a CUDA graph.  Supported shapes: 1 <= min(m,n) <= 128, max(m,n) <= 4096.
+ * ------------------------------------------------------------------------- */
+typedef struct cpa_batch_ctx *cpa_batch;
+
+/* L: host array of count term counts, or NULL to use L0 for every matrix. */
+CPA_API cpa_status cpa_batch_create(cpa_handle h, int count, const int64_t *off, const int32_t *m,
+                            const int32_t *n, const int32_t *L, int L0, cpa_batch *out);
+CPA_API cpa_status cpa_batch_destroy(cpa_batch b);
+
+/* Run the batched shrinkage.
+ *   s: one shrink for all matrices (s_count = 1) or one per matrix
+ *      (s_count = count), host array.
+ *   lambda: NULL to compute each bound on the device (power iteration with
+ *      `iters` steps, definition of cpa_lambda_bound), or a DEVICE array of
+ *      count doubles.
+ *   prec: CPA_FP32 or CPA_BF16X3 (split BF16, FP32 accumulate) or CPA_BF16.
+ * Asynchronous on `stream`. */
+CPA_API cpa_status cpa_svt_batched(cpa_handle h, cpa_batch b, const float *dX, const cpa_shrink *s,
+                           int s_count, const double *lambda, int iters, int prec, float *dY,
+                           void *stream);
+
+/* Per-matrix Lambda_max used by the last run of the plan (device array of
+ * count doubles owned by the plan; valid until cpa_batch_destroy). */
+CPA_API const double *cpa_batch_lambdas(cpa_batch b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPA_H */

@@ -1,0 +1,221 @@
+"""ctypes binding of libcpa (include/cpa.h).  Argument marshalling only: every
+step of the shrinkage runs in the library's CUDA kernels.  PyTorch provides
+device memory and the current stream.  There is no CPU fallback: if the
+library is missing or cannot load, every call raises."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcpa.so")
+
+CPA_OK, CPA_ERR_INVALID_ARG, CPA_ERR_CUDA, CPA_ERR_NO_MEMORY = 0, 1, 2, 3
+CPA_ERR_NONFINITE, CPA_ERR_BOUND, CPA_ERR_TIMEOUT, CPA_ERR_UNSUPPORTED = 4, 5, 6, 7
+HARD, SOFT, WSOFT = 0, 1, 2
+FP32, TF32, BF16, BF16X3 = 0, 1, 2, 3
+PREC = {"fp32": FP32, "tf32": TF32, "bf16": BF16, "bf16x3": BF16X3}
+
+# every function include/cpa.h declares
+EXPORTS = ["cpa_create", "cpa_destroy", "cpa_status_string", "cpa_last_error", "cpa_coeffs",
+           "cpa_lambda_bound", "cpa_svt", "cpa_get_lambda", "cpa_get_coeffs", "cpa_batch_create",
+           "cpa_batch_destroy", "cpa_svt_batched", "cpa_batch_lambdas", "cpa_profile_enable",
+           "cpa_profile_read"]
+STAGES = ["prep", "gram", "bound", "coeff", "shift", "recur", "apply"]
+
+
+class CpaShrink(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("tau", ctypes.c_double), ("c", ctypes.c_double),
+                ("eps", ctypes.c_double), ("noise", ctypes.c_double)]
+
+
+class CpaSparsify(ctypes.Structure):
+    _fields_ = [("transform", ctypes.c_int), ("mode", ctypes.c_int), ("eps_or_frac", ctypes.c_double)]
+
+
+class CpaError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s failed: %s (%s)" % (where, _status_string(status), _last_error()))
+
+
+_lib = None
+_lock = threading.Lock()
+_vp, _i64, _i32, _d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+_P = ctypes.POINTER
+
+
+def load(path: str = LIB_PATH):
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError("libcpa.so not built (%s); run __graft_entry__.build()" % path)
+        lib = ctypes.CDLL(path)
+        sig = {
+            "cpa_create": (ctypes.c_int, [_P(_vp), ctypes.c_int]),
+            "cpa_destroy": (ctypes.c_int, [_vp]),
+            "cpa_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "cpa_last_error": (ctypes.c_char_p, []),
+            "cpa_coeffs": (ctypes.c_int, [_P(CpaShrink), ctypes.c_int, _d, _P(_d)]),
+            "cpa_lambda_bound": (ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, ctypes.c_int, _P(_d), _vp]),
+            "cpa_svt": (ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, _P(CpaShrink), ctypes.c_int, _d,
+                                       ctypes.c_int, _P(CpaSparsify), _vp, _i64, _vp]),
+            "cpa_get_lambda": (ctypes.c_int, [_vp, _P(_d), _vp]),
+            "cpa_get_coeffs": (ctypes.c_int, [_vp, _P(_d), ctypes.c_int, _vp]),
+            "cpa_batch_create": (ctypes.c_int, [_vp, ctypes.c_int, _P(_i64), _P(_i32), _P(_i32), _P(_i32),
+                                                ctypes.c_int, _P(_vp)]),
+            "cpa_batch_destroy": (ctypes.c_int, [_vp]),
+            "cpa_svt_batched": (ctypes.c_int, [_vp, _vp, _vp, _P(CpaShrink), ctypes.c_int, _vp, ctypes.c_int,
+                                               ctypes.c_int, _vp, _vp]),
+            "cpa_batch_lambdas": (_vp, [_vp]),
+            "cpa_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
+            "cpa_profile_read": (ctypes.c_int, [_vp, _P(_d), _P(_i64), ctypes.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _status_string(s):
+    try:
+        return load().cpa_status_string(int(s)).decode()
+    except Exception:
+        return "status %d" % s
+
+
+def _last_error():
+    try:
+        return load().cpa_last_error().decode()
+    except Exception:
+        return ""
+
+
+def _check(status, where):
+    if status != CPA_OK:
+        raise CpaError(status, where)
+
+
+def shrink_struct(kind=SOFT, tau=0.0, c=0.0, eps=1e-8, noise=0.0) -> CpaShrink:
+    return CpaShrink(int(kind), float(tau), float(c), float(eps), float(noise))
+
+
+def _as_shrink(s) -> CpaShrink:
+    if isinstance(s, CpaShrink):
+        return s
+    if isinstance(s, dict):
+        return shrink_struct(**s)
+    # dataclass-like (inputs.ShrinkSpec)
+    return shrink_struct(s.kind, s.tau, s.c, s.eps, s.noise)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _matrix(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or t.dim() != 2:
+        raise ValueError("%s must be a 2-D float32 CUDA tensor" % name)
+    if t.stride(1) != 1 or t.stride(0) < t.shape[1]:
+        raise ValueError("%s must be row-major with unit column stride" % name)
+    return t.data_ptr(), t.shape[0], t.shape[1], t.stride(0)
+
+
+class Handle:
+    """Owns a cpa_handle (device workspace) on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        _check(self._lib.cpa_create(ctypes.byref(h), int(device)), "cpa_create")
+        self.ptr = h
+        self.device = device
+
+    def close(self):
+        if self.ptr:
+            self._lib.cpa_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def cpa_coeffs(shrink, L: int, lambda_max: float) -> np.ndarray:
+    out = np.zeros(int(L), dtype=np.float64)
+    s = _as_shrink(shrink)
+    _check(load().cpa_coeffs(ctypes.byref(s), int(L), float(lambda_max),
+                             out.ctypes.data_as(_P(_d))), "cpa_coeffs")
+    return out
+
+
+def cpa_lambda_bound(h: Handle, X, iters: int = 20, stream=None) -> float:
+    ptr, m, n, ld = _matrix(X, "X")
+    out = ctypes.c_double()
+    _check(load().cpa_lambda_bound(h.ptr, ctypes.c_void_p(ptr), m, n, ld, int(iters), ctypes.byref(out),
+                                   _stream_ptr(stream)), "cpa_lambda_bound")
+    return out.value
+
+
+def cpa_svt(h: Handle, X, shrink, L: int, lambda_max: float = 0.0, prec="fp32", sparsify=None, Y=None,
+            stream=None):
+    """CPA singular value shrinkage of X (Algorithm 1).  Returns Y (allocated
+    with torch if not given).  lambda_max <= 0: computed on the device."""
+    import torch
+    ptr, m, n, ld = _matrix(X, "X")
+    if Y is None:
+        Y = torch.empty((m, n), dtype=torch.float32, device=X.device)
+    yptr, ym, yn, ldy = _matrix(Y, "Y")
+    if (ym, yn) != (m, n):
+        raise ValueError("Y shape mismatch")
+    s = _as_shrink(shrink)
+    sp = None
+    if sparsify is not None:
+        sp = ctypes.byref(CpaSparsify(int(sparsify[0]), int(sparsify[1]), float(sparsify[2])))
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    _check(load().cpa_svt(h.ptr, ctypes.c_void_p(ptr), m, n, ld, ctypes.byref(s), int(L), float(lambda_max), p,
+                          sp, ctypes.c_void_p(yptr), ldy, _stream_ptr(stream)), "cpa_svt")
+    return Y
+
+
+def cpa_get_lambda(h: Handle, stream=None) -> float:
+    out = ctypes.c_double()
+    _check(load().cpa_get_lambda(h.ptr, ctypes.byref(out), _stream_ptr(stream)), "cpa_get_lambda")
+    return out.value
+
+
+def cpa_get_coeffs(h: Handle, L: int, stream=None) -> np.ndarray:
+    out = np.zeros(int(L), dtype=np.float64)
+    _check(load().cpa_get_coeffs(h.ptr, out.ctypes.data_as(_P(_d)), int(L), _stream_ptr(stream)),
+           "cpa_get_coeffs")
+    return out
+
+
+def cpa_profile_enable(h: Handle, enable: bool = True):
+    _check(load().cpa_profile_enable(h.ptr, 1 if enable else 0), "cpa_profile_enable")
+
+
+def cpa_profile_read(h: Handle, reset: bool = True) -> dict:
+    ms = (ctypes.c_double * len(STAGES))()
+    n = (ctypes.c_int64 * len(STAGES))()
+    _check(load().cpa_profile_read(h.ptr, ms, n, 1 if reset else 0), "cpa_profile_read")
+    return {st: {"ms": ms[i], "launches": n[i]} for i, st in enumerate(STAGES)}

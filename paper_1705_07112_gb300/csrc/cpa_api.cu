@@ -1,0 +1,536 @@
+// C ABI of libcpa: argument checking, workspace management and the launch
+// sequence of Algorithm 1 (Gram -> Lambda_max bound -> coefficients -> shift
+// -> recurrence with fused accumulation -> final product).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+using namespace cpa;
+
+struct cpa_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int cc = 0;
+    char *ws = nullptr;       // device workspace
+    size_t ws_bytes = 0;
+    double *h_pin = nullptr;  // pinned host scalars for read-back
+    // layout of the last cpa_svt (for the query functions)
+    double *d_out = nullptr;  // {theta, r, trace, lambda, status}
+    double *d_coef = nullptr;
+    int last_L = 0;
+    bool have_last = false;
+    // diagnostics
+    bool profiling = false;
+    int64_t launches[CPA_NSTAGES] = {};
+    double ms[CPA_NSTAGES] = {};
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+cudaEvent_t take_event(cpa_ctx *h) {
+    if (!h->event_pool.empty()) {
+        cudaEvent_t e = h->event_pool.back();
+        h->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one stage (or one launch of a stage) with events when profiling,
+// and counts its kernel launches.
+struct StageScope {
+    cpa_ctx *h;
+    int stage;
+    cudaStream_t st;
+    cudaEvent_t e0 = nullptr;
+    StageScope(cpa_ctx *h_, int stage_, cudaStream_t st_, int nlaunch) : h(h_), stage(stage_), st(st_) {
+        h->launches[stage] += nlaunch;
+        if (h->profiling) {
+            e0 = take_event(h);
+            cudaEventRecord(e0, st);
+        }
+    }
+    ~StageScope() {
+        if (h->profiling && e0) {
+            cudaEvent_t e1 = take_event(h);
+            cudaEventRecord(e1, st);
+            h->pending.push_back({stage, {e0, e1}});
+        }
+    }
+};
+
+}  // namespace
+
+namespace {
+
+thread_local char g_err[256] = "";
+
+cpa_status cuda_fail(cudaError_t e, const char *where) {
+    snprintf(g_err, sizeof g_err, "%s: %s", where, cudaGetErrorString(e));
+    return CPA_ERR_CUDA;
+}
+
+#define CK(call)                                            \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+cpa_status check_shrink(const cpa_shrink *s) {
+    if (!s) return CPA_ERR_INVALID_ARG;
+    if (s->kind == CPA_HARD || s->kind == CPA_SOFT) {
+        if (!(s->tau >= 0.0) || !std::isfinite(s->tau)) return CPA_ERR_INVALID_ARG;
+    } else if (s->kind == CPA_WSOFT) {
+        if (!(s->c >= 0.0) || !(s->eps > 0.0) || !(s->noise >= 0.0) || !std::isfinite(s->c) ||
+            !std::isfinite(s->noise))
+            return CPA_ERR_INVALID_ARG;
+    } else {
+        return CPA_ERR_INVALID_ARG;
+    }
+    return CPA_OK;
+}
+
+ShrinkParams to_params(const cpa_shrink *s) {
+    ShrinkParams p;
+    p.kind = s->kind;
+    p.tau = s->tau;
+    p.c = s->c;
+    p.eps = s->eps;
+    p.noise = s->noise;
+    return p;
+}
+
+// Bump allocator over the handle's workspace; 256-byte aligned pieces.
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(char *b) : base(b) {}
+    template <class T>
+    T *take(size_t count) {
+        off = (size_t)round_up((int64_t)off, 256);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+cpa_status ensure_ws(cpa_ctx *h, size_t bytes, cudaStream_t st) {
+    if (bytes <= h->ws_bytes) return CPA_OK;
+    if (h->ws) {
+        CK(cudaStreamSynchronize(st));
+        CK(cudaDeviceSynchronize());
+        cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    size_t want = (size_t)round_up((int64_t)bytes, 1 << 20);
+    cudaError_t e = cudaMalloc(&h->ws, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->ws = nullptr;
+        snprintf(g_err, sizeof g_err, "workspace of %zu bytes: %s", want, cudaGetErrorString(e));
+        return CPA_ERR_NO_MEMORY;
+    }
+    h->ws_bytes = want;
+    return CPA_OK;
+}
+
+__global__ void set_scalar2_kernel(double *p, double v0, double v1) {
+    p[0] = v0;
+    p[1] = v1;
+}
+
+bool ranges_overlap(const void *a, size_t abytes, const void *b, size_t bbytes) {
+    uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
+    return a0 < b0 + bbytes && b0 < a0 + abytes;
+}
+
+// Workspace pieces of one single-matrix shrinkage.
+struct SvtWs {
+    int64_t ldp = 0;
+    float *G = nullptr, *A = nullptr, *Z[2] = {nullptr, nullptr}, *H = nullptr, *v0 = nullptr, *v1 = nullptr;
+    double *out = nullptr, *norm2 = nullptr, *coef = nullptr;
+    int *flag = nullptr;
+    // tensor-core operands
+    __nv_bfloat16 *Ahi = nullptr, *Alo = nullptr, *Zhi[2] = {}, *Zlo[2] = {}, *Hhi = nullptr, *Hlo = nullptr;
+    __nv_bfloat16 *Xhi = nullptr, *Xlo = nullptr, *Xthi = nullptr, *Xtlo = nullptr;
+    int64_t ldn = 0, ldm = 0;
+    size_t bytes = 0;
+};
+
+SvtWs carve(char *base, int64_t m, int64_t n, int L, int iters, int prec) {
+    SvtWs w;
+    int64_t p = std::min(m, n);
+    w.ldp = round_up(p, 8);
+    size_t pp = (size_t)(p * w.ldp);
+    Carver c(base);
+    w.out = c.take<double>(8);
+    w.norm2 = c.take<double>(iters + 2);
+    w.coef = c.take<double>(std::max(L, 2));
+    w.flag = c.take<int>(4);
+    w.G = c.take<float>(pp);
+    w.A = c.take<float>(pp);
+    w.Z[0] = c.take<float>(pp);
+    w.Z[1] = c.take<float>(pp);
+    w.H = c.take<float>(pp);
+    w.v0 = c.take<float>(round_up(p, 4));
+    w.v1 = c.take<float>(round_up(p, 4));
+    if (prec != CPA_FP32) {
+        // Gram and final product always use the hi/lo split (their BF16
+        // rounding would otherwise dominate the error); the recurrence
+        // operands carry a lo part only in the all-split mode.
+        bool split_rec = prec == CPA_BF16X3;
+        w.ldn = round_up(n, 8);
+        w.ldm = round_up(m, 8);
+        w.Ahi = c.take<__nv_bfloat16>(pp);
+        w.Zhi[0] = c.take<__nv_bfloat16>(pp);
+        w.Zhi[1] = c.take<__nv_bfloat16>(pp);
+        w.Hhi = c.take<__nv_bfloat16>(pp);
+        w.Hlo = c.take<__nv_bfloat16>(pp);
+        w.Xhi = c.take<__nv_bfloat16>((size_t)(m * w.ldn));
+        w.Xlo = c.take<__nv_bfloat16>((size_t)(m * w.ldn));
+        w.Xthi = c.take<__nv_bfloat16>((size_t)(n * w.ldm));
+        w.Xtlo = c.take<__nv_bfloat16>((size_t)(n * w.ldm));
+        if (split_rec) {
+            w.Alo = c.take<__nv_bfloat16>(pp);
+            w.Zlo[0] = c.take<__nv_bfloat16>(pp);
+            w.Zlo[1] = c.take<__nv_bfloat16>(pp);
+        }
+    }
+    w.bytes = c.off;
+    return w;
+}
+
+cpa_status set_device(cpa_ctx *h) {
+    CK(cudaSetDevice(h->device));
+    return CPA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cpa_status_string(cpa_status s) {
+    switch (s) {
+        case CPA_OK: return "ok";
+        case CPA_ERR_INVALID_ARG: return "invalid argument";
+        case CPA_ERR_CUDA: return "CUDA error";
+        case CPA_ERR_NO_MEMORY: return "out of device memory";
+        case CPA_ERR_NONFINITE: return "non-finite value in input or bound";
+        case CPA_ERR_BOUND: return "invalid lambda_max bound";
+        case CPA_ERR_TIMEOUT: return "device-side wait timed out";
+        case CPA_ERR_UNSUPPORTED: return "unsupported option";
+    }
+    return "unknown status";
+}
+
+const char *cpa_last_error(void) { return g_err; }
+
+cpa_status cpa_create(cpa_handle *out, int device) {
+    if (!out) return CPA_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= count) return CPA_ERR_INVALID_ARG;
+    cpa_ctx *h = new cpa_ctx();
+    h->device = device;
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "cudaGetDeviceProperties");
+    }
+    h->num_sms = prop.multiProcessorCount;
+    h->cc = prop.major * 10 + prop.minor;
+    e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_pin, 64 * sizeof(double));
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "cudaMallocHost");
+    }
+    *out = h;
+    return CPA_OK;
+}
+
+cpa_status cpa_destroy(cpa_handle h) {
+    if (!h) return CPA_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    if (h->ws) cudaFree(h->ws);
+    if (h->h_pin) cudaFreeHost(h->h_pin);
+    for (auto &p : h->pending) {
+        cudaEventDestroy(p.second.first);
+        cudaEventDestroy(p.second.second);
+    }
+    for (auto e : h->event_pool) cudaEventDestroy(e);
+    delete h;
+    return CPA_OK;
+}
+
+cpa_status cpa_coeffs(const cpa_shrink *s, int L, double lambda_max, double *c_out) {
+    if (check_shrink(s) != CPA_OK || L < 1 || L > kMaxTerms || !(lambda_max > 0.0) ||
+        !std::isfinite(lambda_max) || !c_out)
+        return CPA_ERR_INVALID_ARG;
+    ShrinkParams p = to_params(s);
+    for (int k = 0; k < L; ++k) {
+        double acc = 0.0;
+        for (int l = 1; l <= L; ++l) {
+            double th = kPi * ((double)l - 0.5) / (double)L;
+            double x = 0.5 * lambda_max * (cos(th) + 1.0);
+            acc += cos((double)k * th) * response(p, x);
+        }
+        c_out[k] = 2.0 / (double)L * acc;
+    }
+    return CPA_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Gram matrix of the smaller side into w.G (FP32 accumulate).
+cpa_status run_gram(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t ldx, const SvtWs &w, int prec,
+                    cudaStream_t st) {
+    int64_t p = std::min(m, n);
+    Epilogue e;
+    e.D = w.G;
+    e.ldd = w.ldp;
+    if (prec == CPA_FP32) {
+        e.symmetric_upper = 1;
+        if (m >= n)   // G = X^T X: A(i,k) = X[k][i]
+            CK(gemm_f32((int)p, (int)p, (int)m, dX, ldx, false, dX, ldx, false, e, st));
+        else          // G = X X^T
+            CK(gemm_f32((int)p, (int)p, (int)n, dX, ldx, true, dX, ldx, true, e, st));
+        return CPA_OK;
+    }
+    // tensor cores: K-major BF16 hi/lo operand of the contraction dimension
+    const int nsplit = 3;
+    TcOperand op;
+    if (m >= n) {   // rows of X^T (n x m)
+        op.hi = w.Xthi; op.lo = w.Xtlo; op.ld = w.ldm; op.rows = (int)n;
+        CK(gemm_tc((int)p, (int)p, (int)m, op, op, nsplit, e, st, h->num_sms));
+    } else {
+        op.hi = w.Xhi; op.lo = w.Xlo; op.ld = w.ldn; op.rows = (int)m;
+        CK(gemm_tc((int)p, (int)p, (int)n, op, op, nsplit, e, st, h->num_sms));
+    }
+    return CPA_OK;
+}
+
+cpa_status validate_matrix(const float *dX, int64_t m, int64_t n, int64_t ldx) {
+    if (!dX || m < 1 || n < 1 || ldx < n) return CPA_ERR_INVALID_ARG;
+    if (std::min(m, n) > 32768 || std::max(m, n) > (int64_t)1 << 24) return CPA_ERR_INVALID_ARG;
+    return CPA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cpa_status cpa_lambda_bound(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t ldx, int iters,
+                            double *lambda_out, void *stream) {
+    if (!h || !lambda_out || iters < 0 || iters > 100000) return CPA_ERR_INVALID_ARG;
+    cpa_status s = validate_matrix(dX, m, n, ldx);
+    if (s != CPA_OK) return s;
+    if ((s = set_device(h)) != CPA_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    SvtWs w = carve(nullptr, m, n, 1, iters, CPA_FP32);
+    if ((s = ensure_ws(h, w.bytes, st)) != CPA_OK) return s;
+    w = carve(h->ws, m, n, 1, iters, CPA_FP32);
+    int64_t p = std::min(m, n);
+    if ((s = run_gram(h, dX, m, n, ldx, w, CPA_FP32, st)) != CPA_OK) return s;
+    CK(power_bound(w.G, w.ldp, (int)p, iters, w.v0, w.v1, w.norm2, w.out, st));
+    CK(cudaMemcpyAsync(h->h_pin, w.out, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h->h_pin[4] != 0.0) return (cpa_status)(int)h->h_pin[4];
+    *lambda_out = h->h_pin[3];
+    return CPA_OK;
+}
+
+cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t ldx, const cpa_shrink *sh,
+                   int L, double lambda_max, int prec, const cpa_sparsify *sp, float *dY, int64_t ldy,
+                   void *stream) {
+    if (!h || !dY || ldy < n || L < 1 || L > kMaxTerms) return CPA_ERR_INVALID_ARG;
+    cpa_status s = validate_matrix(dX, m, n, ldx);
+    if (s != CPA_OK) return s;
+    if ((s = check_shrink(sh)) != CPA_OK) return s;
+    if (!std::isfinite(lambda_max)) return CPA_ERR_INVALID_ARG;
+    if (prec < CPA_FP32 || prec > CPA_BF16X3) return CPA_ERR_INVALID_ARG;
+    if (sp && (sp->transform != CPA_T_IDENTITY || sp->mode != CPA_SPARSE_OFF)) return CPA_ERR_UNSUPPORTED;
+    if (ranges_overlap(dX, (size_t)((m - 1) * ldx + n) * sizeof(float), dY,
+                       (size_t)((m - 1) * ldy + n) * sizeof(float)))
+        return CPA_ERR_INVALID_ARG;
+    if (prec != CPA_FP32 && h->cc < 100) return CPA_ERR_UNSUPPORTED;
+    if (prec == CPA_TF32) return CPA_ERR_UNSUPPORTED;
+    if ((s = set_device(h)) != CPA_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int iters = kDefaultPowerIters;
+    SvtWs w = carve(nullptr, m, n, L, iters, prec);
+    if ((s = ensure_ws(h, w.bytes, st)) != CPA_OK) return s;
+    w = carve(h->ws, m, n, L, iters, prec);
+    const int64_t p = std::min(m, n);
+    const bool tc = prec != CPA_FP32;
+    const int nsplit_rec = prec == CPA_BF16X3 ? 3 : 1;   // Gram and final product: always 3
+    ShrinkParams sp_ = to_params(sh);
+
+    // operand preparation for the tensor-core path: X and X^T as BF16 hi/lo
+    if (tc) {
+        StageScope sc(h, CPA_STAGE_PREP, st, 2);
+        CK(split_bf16(dX, (int)m, (int)n, ldx, false, w.Xhi, w.Xlo, w.ldn, st));
+        CK(split_bf16(dX, (int)m, (int)n, ldx, true, w.Xthi, w.Xtlo, w.ldm, st));
+    }
+    // Gram step
+    {
+        StageScope sc(h, CPA_STAGE_GRAM, st, 1);
+        if ((s = run_gram(h, dX, m, n, ldx, w, prec, st)) != CPA_OK) return s;
+    }
+    // interval bound
+    if (lambda_max > 0.0) {
+        StageScope sc(h, CPA_STAGE_BOUND, st, 1);
+        set_scalar2_kernel<<<1, 1, 0, st>>>(w.out + 3, lambda_max, 0.0);
+        CK(cudaGetLastError());
+    } else {
+        StageScope sc(h, CPA_STAGE_BOUND, st, iters + 3);
+        CK(power_bound(w.G, w.ldp, (int)p, iters, w.v0, w.v1, w.norm2, w.out, st));
+    }
+    // coefficients (FP64, on the device so the call stays asynchronous)
+    {
+        StageScope sc(h, CPA_STAGE_COEFF, st, 1);
+        CK(device_coeffs(w.out + 3, 0.0, L, sp_, w.coef, st));
+    }
+    // shift and initial sum; Psi_1 = B_hat lives in ring slot 1
+    {
+        StageScope sc(h, CPA_STAGE_SHIFT, st, 1);
+        CK(shift_init(w.G, w.ldp, (int)p, w.out + 3, w.coef, L, w.A, w.Z[1], w.H, w.ldp, tc ? w.Ahi : nullptr,
+                      tc ? w.Alo : nullptr, w.ldp, st, h->num_sms));
+    }
+    // recurrence with fused accumulation: Psi_k = 2 B_hat Psi_{k-1} - Psi_{k-2}, H += c_k Psi_k
+    for (int k = 2; k < L; ++k) {
+        StageScope sc(h, CPA_STAGE_RECUR, st, 1);
+        Epilogue e;
+        int cur = k & 1, prev = (k - 1) & 1;
+        e.D = w.Z[cur];
+        e.ldd = w.ldp;
+        e.C = (k == 2) ? nullptr : w.Z[cur];
+        e.ldc = w.ldp;
+        e.s_acc = 2.f;
+        e.s_c = -1.f;
+        e.diag = (k == 2) ? -1.f : 0.f;   // Psi_0 = Id
+        e.H = w.H;
+        e.ldh = w.ldp;
+        e.coef = w.coef;
+        e.k = k;
+        if (!tc) {
+            e.symmetric_upper = 1;
+            CK(gemm_f32((int)p, (int)p, (int)p, w.A, w.ldp, true, w.Z[prev], w.ldp, true, e, st));
+        } else {
+            e.Dhi = w.Zhi[cur];
+            e.Dlo = w.Zlo[cur];
+            e.ldb = w.ldp;
+            TcOperand a, b;
+            a.hi = w.Ahi; a.lo = w.Alo; a.ld = w.ldp; a.rows = (int)p;
+            if (k == 2) {   // Psi_1 = B_hat: its BF16 parts are A's
+                b = a;
+            } else {
+                b.hi = w.Zhi[prev]; b.lo = w.Zlo[prev]; b.ld = w.ldp; b.rows = (int)p;
+            }
+            CK(gemm_tc((int)p, (int)p, (int)p, a, b, nsplit_rec, e, st, h->num_sms));
+        }
+    }
+    // final product: Y = X H (m >= n) or H X (m < n)
+    StageScope sc(h, CPA_STAGE_APPLY, st, tc ? 2 : 1);
+    Epilogue e;
+    e.D = dY;
+    e.ldd = ldy;
+    if (!tc) {
+        if (m >= n)
+            CK(gemm_f32((int)m, (int)n, (int)n, dX, ldx, true, w.H, w.ldp, true, e, st));
+        else
+            CK(gemm_f32((int)m, (int)n, (int)m, w.H, w.ldp, true, dX, ldx, false, e, st));
+    } else {
+        CK(split_bf16(w.H, (int)p, (int)p, w.ldp, false, w.Hhi, w.Hlo, w.ldp, st));
+        TcOperand hop, xop;
+        hop.hi = w.Hhi; hop.lo = w.Hlo; hop.ld = w.ldp; hop.rows = (int)p;
+        if (m >= n) {   // Y(r,j) = sum_l X[r][l] H[j][l]
+            xop.hi = w.Xhi; xop.lo = w.Xlo; xop.ld = w.ldn; xop.rows = (int)m;
+            CK(gemm_tc((int)m, (int)n, (int)n, xop, hop, 3, e, st, h->num_sms));
+        } else {        // Y(i,c) = sum_l H[i][l] X^T[c][l]
+            xop.hi = w.Xthi; xop.lo = w.Xtlo; xop.ld = w.ldm; xop.rows = (int)n;
+            CK(gemm_tc((int)m, (int)n, (int)m, hop, xop, 3, e, st, h->num_sms));
+        }
+    }
+    h->d_out = w.out;
+    h->d_coef = w.coef;
+    h->last_L = L;
+    h->have_last = true;
+    return CPA_OK;
+}
+
+cpa_status cpa_get_lambda(cpa_handle h, double *lambda_out, void *stream) {
+    if (!h || !lambda_out || !h->have_last) return CPA_ERR_INVALID_ARG;
+    cpa_status s = set_device(h);
+    if (s != CPA_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(h->h_pin, h->d_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *lambda_out = h->h_pin[3];
+    if (h->h_pin[4] != 0.0) return (cpa_status)(int)h->h_pin[4];
+    if (!(h->h_pin[3] > 0.0)) return CPA_ERR_BOUND;
+    return CPA_OK;
+}
+
+cpa_status cpa_get_coeffs(cpa_handle h, double *c_out, int L, void *stream) {
+    if (!h || !c_out || !h->have_last || L != h->last_L) return CPA_ERR_INVALID_ARG;
+    cpa_status s = set_device(h);
+    if (s != CPA_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(c_out, h->d_coef, (size_t)L * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return CPA_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+cpa_status cpa_profile_enable(cpa_handle h, int enable) {
+    if (!h) return CPA_ERR_INVALID_ARG;
+    h->profiling = enable != 0;
+    return CPA_OK;
+}
+
+cpa_status cpa_profile_read(cpa_handle h, double *ms, int64_t *launches, int reset) {
+    if (!h) return CPA_ERR_INVALID_ARG;
+    cpa_status s = set_device(h);
+    if (s != CPA_OK) return s;
+    CK(cudaDeviceSynchronize());
+    for (auto &p : h->pending) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, p.second.first, p.second.second) == cudaSuccess) h->ms[p.first] += t;
+        h->event_pool.push_back(p.second.first);
+        h->event_pool.push_back(p.second.second);
+    }
+    h->pending.clear();
+    for (int i = 0; i < CPA_NSTAGES; ++i) {
+        if (ms) ms[i] = h->ms[i];
+        if (launches) launches[i] = h->launches[i];
+        if (reset) {
+            h->ms[i] = 0.0;
+            h->launches[i] = 0;
+        }
+    }
+    return CPA_OK;
+}
+
+}  // extern "C"

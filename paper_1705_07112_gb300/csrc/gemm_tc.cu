@@ -1,0 +1,454 @@
+// Blackwell (sm_103a) tensor-core GEMM with the fused CPA epilogue.
+//
+//   out(i,j) = epi( sum_k A(i,k) B(j,k) ),  A: M x K, B: N x K, both BF16
+//   K-major in global memory, FP32 accumulation in tensor memory (TMEM).
+//
+// Structure (one CTA per SM, persistent over output tiles of 128 x BN):
+//   warp 0      TMA producer: cp.async.bulk.tensor 2-D loads of A and B
+//               K-slices (64 elements = one 128-byte swizzle row) into a
+//               ring of shared-memory stages, completion on mbarriers.
+//   warp 1      MMA issuer: allocates TMEM, one elected thread issues
+//               tcgen05.mma kind::f16 (M=128, N=BN, K=16) per 32-byte K step,
+//               tcgen05.commit frees a stage / publishes an accumulator.
+//   warps 2..5  epilogue: tcgen05.ld 32x32b (one accumulator row per thread),
+//               fused  D = s_acc*acc + s_c*C + diag,  H += c_k D,  BF16 hi/lo
+//               copies of D, while the MMA warp fills the other accumulator.
+// Split precision (nsplit = 3) runs the K loop three times over
+// (A_hi,B_hi), (A_hi,B_lo), (A_lo,B_hi) into the same accumulator.
+//
+// Every mbarrier wait is bounded (~2 s of clock); on expiry the CTA raises
+// an error flag, stops issuing work, drains the TMA loads it started, frees
+// its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+#include <mutex>
+
+#include "internal.h"
+
+namespace cpa {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;            // bf16 elements per 128-byte swizzle row
+constexpr int kThreads = 192;
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait; false if the CTA aborted or the wait expired (sets abort).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    long long t0 = clock64();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 0) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > kWaitCycles) {
+                *abort_flag = 1;
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            su32(dst)),
+        "l"(map), "r"(su32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): K-major, 128-byte swizzle,
+// 8-row atoms 1024 bytes apart (stride byte offset), version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
+    d |= (uint64_t)(16 >> 4) << 16;                  // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    d |= (uint64_t)2 << 61;                          // swizzle: 128B
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+struct TileMaps {
+    CUtensorMap a_hi, a_lo, b_hi, b_lo;
+};
+
+template <int BN>
+struct Smem {
+    static constexpr int kStageA = BM * BK * 2;
+    static constexpr int kStageB = BN * BK * 2;
+    static constexpr int kStages = (BN == 256) ? 4 : (BN == 128 ? 6 : 8);
+    static constexpr int kBytes = kStages * (kStageA + kStageB) + 1024 /* align */ + 256 /* barriers */;
+};
+
+__device__ __forceinline__ void epi_scalar(const Epilogue &e, float ck, int i, int j, float acc) {
+    float v = e.s_acc * acc;
+    if (e.C) v = fmaf(e.s_c, e.C[(int64_t)i * e.ldc + j], v);
+    if (i == j) v += e.diag;
+    e.D[(int64_t)i * e.ldd + j] = v;
+    if (e.H) {
+        float *hp = e.H + (int64_t)i * e.ldh + j;
+        *hp = fmaf(ck, v, *hp);
+    }
+    if (e.Dhi) {
+        __nv_bfloat16 h = __float2bfloat16_rn(v);
+        e.Dhi[(int64_t)i * e.ldb + j] = h;
+        if (e.Dlo) e.Dlo[(int64_t)i * e.ldb + j] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
+__device__ __forceinline__ void epi_vec4(const Epilogue &e, float ck, int i, int j, const float *v4, bool vec) {
+    if (vec) {
+        float4 v = make_float4(e.s_acc * v4[0], e.s_acc * v4[1], e.s_acc * v4[2], e.s_acc * v4[3]);
+        if (e.C) {
+            float4 c = *reinterpret_cast<const float4 *>(e.C + (int64_t)i * e.ldc + j);
+            v.x = fmaf(e.s_c, c.x, v.x); v.y = fmaf(e.s_c, c.y, v.y);
+            v.z = fmaf(e.s_c, c.z, v.z); v.w = fmaf(e.s_c, c.w, v.w);
+        }
+        if (i >= j && i < j + 4) (&v.x)[i - j] += e.diag;
+        *reinterpret_cast<float4 *>(e.D + (int64_t)i * e.ldd + j) = v;
+        if (e.H) {
+            float4 *hp = reinterpret_cast<float4 *>(e.H + (int64_t)i * e.ldh + j);
+            float4 h = *hp;
+            h.x = fmaf(ck, v.x, h.x); h.y = fmaf(ck, v.y, h.y);
+            h.z = fmaf(ck, v.z, h.z); h.w = fmaf(ck, v.w, h.w);
+            *hp = h;
+        }
+        if (e.Dhi) {
+            __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+            uint2 hv;
+            hv.x = *reinterpret_cast<uint32_t *>(&h01);
+            hv.y = *reinterpret_cast<uint32_t *>(&h23);
+            *reinterpret_cast<uint2 *>(e.Dhi + (int64_t)i * e.ldb + j) = hv;
+            if (e.Dlo) {
+                float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+                __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+                __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+                uint2 lv;
+                lv.x = *reinterpret_cast<uint32_t *>(&l01);
+                lv.y = *reinterpret_cast<uint32_t *>(&l23);
+                *reinterpret_cast<uint2 *>(e.Dlo + (int64_t)i * e.ldb + j) = lv;
+            }
+        }
+        return;
+    }
+    for (int q = 0; q < 4; ++q) epi_scalar(e, ck, i, j + q, v4[q]);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_tc_kernel(const __grid_constant__ TileMaps maps, int M, int N, int K, int nsplit, Epilogue e, int vec_ok,
+                   int *err) {
+    using S = Smem<BN>;
+    constexpr int kStages = S::kStages;
+    constexpr uint32_t kTmemCols = 2 * BN;   // two accumulators
+    constexpr uint32_t kIdesc = idesc_bf16(BM, BN);
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + kStages * S::kStageA;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + kStages * S::kStageB);
+    uint64_t *full = bars;                 // [kStages]
+    uint64_t *empty = bars + kStages;      // [kStages]
+    uint64_t *tfull = bars + 2 * kStages;  // [2]
+    uint64_t *tempty = tfull + 2;          // [2]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
+    const int ntiles = tiles_m * tiles_n;
+    const int kb_per = (K + BK - 1) / BK;
+    const int nkb = kb_per * nsplit;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t armed_mask = 0, armed_phase = 0;   // per stage: armed at least once / phase it was armed in
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+                const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) break;
+                    const int seg = kb / kb_per, kx = (kb % kb_per) * BK;
+                    const CUtensorMap *ma = (seg < 2) ? &maps.a_hi : &maps.a_lo;
+                    const CUtensorMap *mb = (seg == 1) ? &maps.b_lo : &maps.b_hi;
+                    mbar_expect_tx(&full[stage], S::kStageA + S::kStageB);
+                    tma_load_2d(sA + stage * S::kStageA, ma, &full[stage], kx, m0);
+                    tma_load_2d(sB + stage * S::kStageB, mb, &full[stage], kx, n0);
+                    armed_mask |= 1u << stage;
+                    armed_phase = (armed_phase & ~(1u << stage)) | (phase << stage);
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+            }
+            if (*abort_flag) {
+                // drain: the last load armed on each stage completes the full
+                // barrier phase it was armed in; wait for it (bounded) so no
+                // copy is still writing shared memory when the CTA exits
+                for (int s2 = 0; s2 < kStages; ++s2) {
+                    if (!(armed_mask & (1u << s2))) continue;
+                    const uint32_t ph = (armed_phase >> s2) & 1u;
+                    long long t0 = clock64();
+                    while (!mbar_try_wait(&full[s2], ph) && clock64() - t0 < kWaitCycles) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t tphase[2] = {0, 0};
+            int local = 0;
+            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++local) {
+                const int buf = local & 1;
+                if (!mbar_wait(&tempty[buf], tphase[buf] ^ 1, abort_flag)) break;
+                tphase[buf] ^= 1;
+                fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
+                bool ok = true;
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!mbar_wait(&full[stage], phase, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint64_t da = smem_desc(su32(sA + stage * S::kStageA));
+                    const uint64_t db = smem_desc(su32(sB + stage * S::kStageB));
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk)
+                        mma_bf16(d_tmem, da + 2 * kk, db + 2 * kk, kIdesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                    mma_commit(&empty[stage]);
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(&tfull[buf]);
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int quarter = warp & 3;   // TMEM lanes 32*quarter .. +31
+        const float ck = e.H ? (float)e.coef[e.k] : 0.f;
+        uint32_t tphase[2] = {0, 0};
+        int local = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
+            const int buf = local & 1;
+            if (!mbar_wait(&tfull[buf], tphase[buf], abort_flag)) break;
+            tphase[buf] ^= 1;
+            fence_after();
+            const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
+            const int i = m0 + quarter * 32 + lane;
+            const uint32_t trow = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN);
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                float v[32];
+                tmem_ld32(trow + (uint32_t)(c * 32), v);
+                const int j0 = n0 + c * 32;
+                if (i < M && j0 < N) {
+                    const bool full_chunk = (j0 + 32 <= N);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        int j = j0 + 4 * q;
+                        if (full_chunk) {
+                            epi_vec4(e, ck, i, j, v + 4 * q, vec_ok != 0);
+                        } else {
+                            for (int r = 0; r < 4; ++r)
+                                if (j + r < N) epi_scalar(e, ck, i, j + r, v[4 * q + r]);
+                        }
+                    }
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+        }
+    }
+
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+                     : "memory");
+    }
+    if (threadIdx.x == 0 && *abort_flag) atomicExch(err, CPA_ERR_TIMEOUT);
+}
+
+// ------------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+bool load_encode() {
+    std::call_once(g_encode_once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    return g_encode != nullptr;
+}
+
+bool make_map(CUtensorMap *map, const __nv_bfloat16 *ptr, int64_t ld, int rows, int K, int box_rows) {
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)ptr, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int *g_err_dev = nullptr;
+
+template <int BN>
+cudaError_t launch(int M, int N, int K, const TcOperand &A, const TcOperand &B, int nsplit, const Epilogue &e,
+                   cudaStream_t st, int num_sms) {
+    using S = Smem<BN>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t r = cudaFuncSetAttribute(gemm_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             S::kBytes);
+        if (r != cudaSuccess) return r;
+        attr_set = true;
+    }
+    TileMaps maps;
+    const __nv_bfloat16 *alo = A.lo ? A.lo : A.hi, *blo = B.lo ? B.lo : B.hi;
+    if (!make_map(&maps.a_hi, A.hi, A.ld, A.rows, K, BM) || !make_map(&maps.a_lo, alo, A.ld, A.rows, K, BM) ||
+        !make_map(&maps.b_hi, B.hi, B.ld, B.rows, K, BN) || !make_map(&maps.b_lo, blo, B.ld, B.rows, K, BN))
+        return cudaErrorInvalidValue;
+    const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    const int grid = tiles < num_sms ? tiles : num_sms;
+    bool vec_ok = ((e.ldd | e.ldc | e.ldh) % 4 == 0) && (e.ldb % 4 == 0) && ((uintptr_t)e.D % 16 == 0) &&
+                  ((uintptr_t)e.C % 16 == 0) && ((uintptr_t)e.H % 16 == 0) && ((uintptr_t)e.Dhi % 8 == 0) &&
+                  ((uintptr_t)e.Dlo % 8 == 0);
+    gemm_tc_kernel<BN><<<grid, kThreads, S::kBytes, st>>>(maps, M, N, K, nsplit, e, vec_ok ? 1 : 0, g_err_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t gemm_tc_error_flag(int **flag) {
+    if (!g_err_dev) {
+        cudaError_t r = cudaMalloc(&g_err_dev, sizeof(int));
+        if (r != cudaSuccess) return r;
+        r = cudaMemset(g_err_dev, 0, sizeof(int));
+        if (r != cudaSuccess) return r;
+    }
+    *flag = g_err_dev;
+    return cudaSuccess;
+}
+
+cudaError_t gemm_tc(int M, int N, int K, const TcOperand &A, const TcOperand &B, int nsplit, const Epilogue &e,
+                    cudaStream_t st, int num_sms) {
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    if (!load_encode()) return cudaErrorNotSupported;
+    if ((A.ld % 8) || (B.ld % 8) || ((uintptr_t)A.hi % 16) || ((uintptr_t)B.hi % 16)) return cudaErrorInvalidValue;
+    if (nsplit == 3 && (!A.lo || !B.lo)) return cudaErrorInvalidValue;
+    int *flag;
+    cudaError_t r = gemm_tc_error_flag(&flag);
+    if (r != cudaSuccess) return r;
+    // tile width: the widest whose tile count still fills the SMs
+    const int tm = (M + BM - 1) / BM;
+    if (tm * ((N + 255) / 256) >= num_sms || N > 4096) return launch<256>(M, N, K, A, B, nsplit, e, st, num_sms);
+    if (tm * ((N + 127) / 128) >= num_sms) return launch<128>(M, N, K, A, B, nsplit, e, st, num_sms);
+    return launch<64>(M, N, K, A, B, nsplit, e, st, num_sms);
+}
+
+}  // namespace cpa

@@ -1,0 +1,110 @@
+// Internal declarations shared by the translation units of libcpa.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "../../include/cpa.h"
+
+namespace cpa {
+
+// ---------------------------------------------------------------------------
+// Shrinkage response h(x) of Eq. filter_response_ours, shared by the host
+// coefficient routine and the device coefficient kernel of this library.
+//   h(x) = (sqrt x - W(x)) / sqrt x  if sqrt x > thr(x), else 0,
+//   HARD: W = 0, thr = tau;  SOFT: W = thr = tau;
+//   WSOFT: W = thr = c / (sqrt(max(x - noise, 0)) + eps).
+// ---------------------------------------------------------------------------
+struct ShrinkParams {
+    int kind;
+    double tau, c, eps, noise;
+};
+
+__host__ __device__ inline double response(const ShrinkParams &s, double x) {
+    double r = x > 0.0 ? sqrt(x) : 0.0;
+    double W, thr;
+    if (s.kind == CPA_HARD) {
+        W = 0.0;
+        thr = s.tau;
+    } else if (s.kind == CPA_SOFT) {
+        W = s.tau;
+        thr = s.tau;
+    } else {
+        double s2 = x - s.noise;
+        double sest = s2 > 0.0 ? sqrt(s2) : 0.0;
+        W = s.c / (sest + s.eps);
+        thr = W;
+    }
+    return r > thr ? (r - W) / r : 0.0;
+}
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxTerms = 4096;
+constexpr double kLambdaMargin = 0.01;
+constexpr uint64_t kStartSeed = 0x1705071120000000ULL;
+constexpr int kDefaultPowerIters = 20;
+
+// ---------------------------------------------------------------------------
+// Fused GEMM epilogue used by every dense product of the path:
+//   v = s_acc * acc + s_c * C(i,j) + (i == j ? diag : 0)
+//   D(i,j) = v;   if H: H(i,j) += coef[k] * v
+// D and C may alias (the recurrence overwrites Psi_{k-2} with Psi_k).
+// Optional BF16 hi/lo copies of v (hi = bf16(v), lo = bf16(v - hi)) are
+// written for the tensor-core operand of the next product.
+// ---------------------------------------------------------------------------
+struct Epilogue {
+    float *D = nullptr;
+    int64_t ldd = 0;
+    const float *C = nullptr;
+    int64_t ldc = 0;
+    float s_acc = 1.f, s_c = 0.f, diag = 0.f;
+    float *H = nullptr;
+    int64_t ldh = 0;
+    const double *coef = nullptr;
+    int k = 0;
+    __nv_bfloat16 *Dhi = nullptr, *Dlo = nullptr;
+    int64_t ldb = 0;
+    int symmetric_upper = 0;   // compute only tiles with tile_n >= tile_m, mirror
+};
+
+// SIMT FP32 GEMM: out(i,j) = epi(sum_k A(i,k) B(j,k)),  i < M, j < N, k < K.
+// a_kmajor: A(i,k) = A[i*lda + k], else A[k*lda + i]; likewise B.
+cudaError_t gemm_f32(int M, int N, int K, const float *A, int64_t lda, bool a_kmajor,
+                     const float *B, int64_t ldb, bool b_kmajor, const Epilogue &e,
+                     cudaStream_t st);
+
+// Tensor-core GEMM (tcgen05 + TMA + TMEM).  Operands are BF16 K-major
+// (row-major rows of K contiguous elements), given as hi and optional lo
+// parts.  nsplit = 1: hi*hi.  nsplit = 3: hi*hi + hi*lo + lo*hi.
+struct TcOperand {
+    const __nv_bfloat16 *hi = nullptr, *lo = nullptr;
+    int64_t ld = 0;    // elements
+    int rows = 0;      // M (for A) or N (for B)
+};
+cudaError_t gemm_tc(int M, int N, int K, const TcOperand &A, const TcOperand &B, int nsplit,
+                    const Epilogue &e, cudaStream_t st, int num_sms);
+
+// Elementwise conversion of a row-major FP32 matrix to BF16 hi/lo parts,
+// optionally transposed (out is cols x rows then).
+cudaError_t split_bf16(const float *X, int rows, int cols, int64_t ldx, bool transpose,
+                       __nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t ldo, cudaStream_t st);
+
+}  // namespace cpa
+
+namespace cpa {
+
+// Power-iteration bound (definition in cpa_lambda_bound's comment); out =
+// {theta, r, trace, lambda, status}.  v0, v1: p floats; norm2: iters+2 doubles.
+cudaError_t power_bound(const float *G, int64_t ldg, int p, int iters, float *v0, float *v1, double *norm2,
+                        double *out, cudaStream_t st);
+cudaError_t device_coeffs(const double *lam_dev, double lam_host, int L, const ShrinkParams &s, double *c,
+                          cudaStream_t st);
+cudaError_t shift_init(const float *G, int64_t ldg, int p, const double *lam, const double *c, int L, float *A,
+                       float *Z1, float *H, int64_t ld, __nv_bfloat16 *Ahi, __nv_bfloat16 *Alo, int64_t ldb,
+                       cudaStream_t st, int num_sms);
+cudaError_t check_finite(const float *X, int64_t rows, int64_t cols, int64_t ldx, int *flag, cudaStream_t st,
+                         int num_sms);
+
+}  // namespace cpa

@@ -1,0 +1,269 @@
+// Bandwidth-bound helper kernels of the CPA path: the Lambda_max power
+// iteration, the device-side Chebyshev coefficients, the shift
+// B_hat = (2/Lambda_max) G - Id with the initial sum, and FP32 -> BF16 hi/lo
+// splitting of tensor-core operands.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace cpa {
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide FP64 sum; blockDim.x a multiple of 32, <= 1024.
+__device__ double block_sum(double v) {
+    __shared__ double red[32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    int nw = blockDim.x >> 5;
+    double r = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+    if (w == 0) r = warp_sum(r);
+    return r;   // valid in thread 0
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014), output i of the generator seeded with
+// `seed`: the state after i+1 golden-ratio increments through the finaliser.
+__device__ __forceinline__ uint64_t splitmix64_output(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// v0 and |v0|^2; clears the norm slots used by the iteration.
+__global__ void power_init_kernel(float *v, int p, uint64_t seed, double *norm2, int nslots) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+        uint64_t z = splitmix64_output(seed, (uint64_t)i);
+        float x = (float)((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+        v[i] = x;
+        s += (double)x * (double)x;
+    }
+    for (int i = threadIdx.x + 1; i < nslots; i += blockDim.x) norm2[i] = 0.0;
+    s = block_sum(s);
+    if (threadIdx.x == 0) norm2[0] = s;
+}
+
+// w = G (v / sqrt(norm_in)),  norm_out += |w|^2.  One warp per row of G.
+__global__ void power_matvec_kernel(const float *__restrict__ G, int64_t ldg, int p,
+                                    const float *__restrict__ v, const double *norm_in,
+                                    float *__restrict__ w, double *norm_out) {
+    double nin = *norm_in;
+    float scale = nin > 0.0 ? (float)(1.0 / sqrt(nin)) : 0.f;
+    int lane = threadIdx.x & 31;
+    int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    double contrib = 0.0;
+    if (row < p) {
+        const float *g = G + (int64_t)row * ldg;
+        float s = 0.f;
+        if ((ldg & 3) == 0 && (p & 3) == 0 && ((uintptr_t)G & 15) == 0 && ((uintptr_t)v & 15) == 0) {
+            const float4 *g4 = reinterpret_cast<const float4 *>(g);
+            const float4 *v4 = reinterpret_cast<const float4 *>(v);
+            for (int j = lane; j < (p >> 2); j += 32) {
+                float4 a = __ldg(g4 + j), b = __ldg(v4 + j);
+                s = fmaf(a.x, b.x, s); s = fmaf(a.y, b.y, s);
+                s = fmaf(a.z, b.z, s); s = fmaf(a.w, b.w, s);
+            }
+        } else {
+            for (int j = lane; j < p; j += 32) s = fmaf(g[j], v[j], s);
+        }
+        s = warp_sumf(s) * scale;
+        if (lane == 0) {
+            w[row] = s;
+            contrib = (double)s * (double)s;
+        }
+    }
+    double tot = block_sum(contrib);
+    if (threadIdx.x == 0 && tot != 0.0) atomicAdd(norm_out, tot);
+}
+
+// theta = v.w, r = |w - theta v|, trace, lambda (FP64).  v = vu / sqrt(nv).
+__global__ void power_final_kernel(const float *vu, const double *nv, const float *w, const double *nw,
+                                   const float *G, int64_t ldg, int p, double margin, double *out) {
+    double n = *nv;
+    double sc = n > 0.0 ? 1.0 / sqrt(n) : 0.0;
+    double th = 0.0, tr = 0.0;
+    int nonfinite = 0;
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+        th += (double)vu[i] * sc * (double)w[i];
+        double gii = (double)G[(int64_t)i * ldg + i];
+        tr += gii;
+        if (!isfinite(gii)) nonfinite = 1;
+    }
+    th = block_sum(th);
+    __shared__ double sh_th;
+    if (threadIdx.x == 0) sh_th = th;
+    __syncthreads();
+    th = sh_th;
+    double r2 = 0.0;
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+        double d = (double)w[i] - th * (double)vu[i] * sc;
+        r2 += d * d;
+    }
+    r2 = block_sum(r2);
+    tr = block_sum(tr);
+    nonfinite = __syncthreads_or(nonfinite);
+    if (threadIdx.x == 0) {
+        double r = sqrt(r2);
+        double lam = (th + r) * (1.0 + margin);
+        if (lam > tr) lam = tr;
+        double flag = 0.0;
+        if (nonfinite || !isfinite(lam) || !isfinite(tr)) {
+            flag = (double)CPA_ERR_NONFINITE;
+        } else if (!(lam > 0.0)) {
+            // theta + r = 0 only when X = 0 (trace 0) or v0 lies in the null
+            // space; the trace is then the bound, and any positive value
+            // serves for X = 0, whose shrinkage is 0.
+            lam = tr > 0.0 ? tr : 1.0;
+        }
+        out[0] = th;
+        out[1] = r;
+        out[2] = tr;
+        out[3] = lam;
+        out[4] = flag;
+    }
+    (void)nw;
+}
+
+// Shifted Chebyshev coefficients (Eq. chebychev_coeff_shifted), FP64.
+__global__ void coeffs_kernel(const double *lam_dev, double lam_host, int L, ShrinkParams s, double *c) {
+    double lam = lam_dev ? lam_dev[0] : lam_host;
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+        double acc = 0.0;
+        for (int l = 1; l <= L; ++l) {
+            double th = kPi * ((double)l - 0.5) / (double)L;
+            double x = 0.5 * lam * (cos(th) + 1.0);
+            acc += cos((double)k * th) * response(s, x);
+        }
+        c[k] = 2.0 / (double)L * acc;
+    }
+}
+
+__device__ __forceinline__ void put_split(__nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t idx, float v) {
+    __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[idx] = h;
+    if (lo) lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+// A = (2/lambda) G - Id;  Z1 = A;  H = c0/2 Id + c1 A  (the initial sum of
+// Algorithm 1).  Optional BF16 hi/lo copies of A (tensor-core operand; Z1 is
+// the same matrix and reuses them).
+__global__ void shift_kernel(const float *__restrict__ G, int64_t ldg, int p, const double *lam,
+                             const double *c, int L, float *A, float *Z1, float *H, int64_t ld,
+                             __nv_bfloat16 *Ahi, __nv_bfloat16 *Alo, int64_t ldb) {
+    float s = (float)(2.0 / lam[0]);
+    float c0h = (float)(0.5 * c[0]);
+    float c1 = L > 1 ? (float)c[1] : 0.f;
+    int64_t total = (int64_t)p * p;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int i = (int)(e / p), j = (int)(e % p);
+        float a = s * G[(int64_t)i * ldg + j] - (i == j ? 1.f : 0.f);
+        if (A) A[(int64_t)i * ld + j] = a;
+        if (Z1) Z1[(int64_t)i * ld + j] = a;
+        H[(int64_t)i * ld + j] = c1 * a + (i == j ? c0h : 0.f);
+        if (Ahi) put_split(Ahi, Alo, (int64_t)i * ldb + j, a);
+    }
+}
+
+// hi/lo split of a row-major FP32 matrix, optionally transposed, through a
+// 32 x 32 shared-memory tile so both the read and the write are coalesced.
+__global__ void split_kernel(const float *__restrict__ X, int rows, int cols, int64_t ldx, int transpose,
+                             __nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t ldo) {
+    __shared__ float t[32][33];
+    int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    for (int k = ty; k < 32; k += 8) {
+        int r = r0 + k, c = c0 + tx;
+        t[k][tx] = (r < rows && c < cols) ? X[(int64_t)r * ldx + c] : 0.f;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        if (!transpose) {
+            int r = r0 + k, c = c0 + tx;
+            if (r < rows && c < cols) put_split(hi, lo, (int64_t)r * ldo + c, t[k][tx]);
+        } else {
+            int r = c0 + k, c = r0 + tx;   // out is cols x rows
+            if (r < cols && c < rows) put_split(hi, lo, (int64_t)r * ldo + c, t[tx][k]);
+        }
+    }
+}
+
+__global__ void check_finite_kernel(const float *X, int64_t rows, int64_t cols, int64_t ldx, int *flag) {
+    int bad = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < rows * cols;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        float v = X[(e / cols) * ldx + e % cols];
+        if (!isfinite(v)) bad = 1;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
+}
+
+}  // namespace
+
+cudaError_t power_bound(const float *G, int64_t ldg, int p, int iters, float *v0, float *v1,
+                        double *norm2, double *out, cudaStream_t st) {
+    power_init_kernel<<<1, 1024, 0, st>>>(v0, p, kStartSeed, norm2, iters + 2);
+    float *bufs[2] = {v0, v1};
+    int threads = 256;
+    int blocks = (int)(((int64_t)p * 32 + threads - 1) / threads);
+    for (int t = 0; t < iters; ++t)
+        power_matvec_kernel<<<blocks, threads, 0, st>>>(G, ldg, p, bufs[t & 1], norm2 + t, bufs[(t + 1) & 1],
+                                                        norm2 + t + 1);
+    // final product w = G v with v = bufs[iters&1] / sqrt(norm2[iters])
+    float *vu = bufs[iters & 1], *w = bufs[(iters + 1) & 1];
+    power_matvec_kernel<<<blocks, threads, 0, st>>>(G, ldg, p, vu, norm2 + iters, w, norm2 + iters + 1);
+    // the final kernel needs v unscaled and w: w overwrote the other buffer,
+    // vu is intact
+    power_final_kernel<<<1, 1024, 0, st>>>(vu, norm2 + iters, w, norm2 + iters + 1, G, ldg, p, kLambdaMargin,
+                                           out);
+    return cudaGetLastError();
+}
+
+cudaError_t device_coeffs(const double *lam_dev, double lam_host, int L, const ShrinkParams &s, double *c,
+                          cudaStream_t st) {
+    int threads = L < 1024 ? ((L + 31) / 32) * 32 : 1024;
+    coeffs_kernel<<<1, threads, 0, st>>>(lam_dev, lam_host, L, s, c);
+    return cudaGetLastError();
+}
+
+cudaError_t shift_init(const float *G, int64_t ldg, int p, const double *lam, const double *c, int L, float *A,
+                       float *Z1, float *H, int64_t ld, __nv_bfloat16 *Ahi, __nv_bfloat16 *Alo, int64_t ldb,
+                       cudaStream_t st, int num_sms) {
+    int64_t total = (int64_t)p * p;
+    int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 8);
+    if (blocks < 1) blocks = 1;
+    shift_kernel<<<blocks, 256, 0, st>>>(G, ldg, p, lam, c, L, A, Z1, H, ld, Ahi, Alo, ldb);
+    return cudaGetLastError();
+}
+
+cudaError_t split_bf16(const float *X, int rows, int cols, int64_t ldx, bool transpose, __nv_bfloat16 *hi,
+                       __nv_bfloat16 *lo, int64_t ldo, cudaStream_t st) {
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+    split_kernel<<<grid, dim3(32, 8), 0, st>>>(X, rows, cols, ldx, transpose ? 1 : 0, hi, lo, ldo);
+    return cudaGetLastError();
+}
+
+cudaError_t check_finite(const float *X, int64_t rows, int64_t cols, int64_t ldx, int *flag, cudaStream_t st,
+                         int num_sms) {
+    int64_t total = rows * cols;
+    int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 8);
+    if (blocks < 1) blocks = 1;
+    check_finite_kernel<<<blocks, 256, 0, st>>>(X, rows, cols, ldx, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace cpa

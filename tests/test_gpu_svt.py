@@ -1,0 +1,195 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (relative Frobenius error of the GPU result against the FP64
+oracle at the same L and Lambda_max):
+  fp32    1e-5   plain FP32 CPA
+  bf16x3  2e-3   (measures ~1e-5: every product with the hi/lo split)
+  bf16    2e-3   BF16 recurrence, split Gram and final product
+The interval bound Lambda_max is computed by the oracle and handed to both
+sides, except in the tests of the bound itself, where each side computes it.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1705_07112_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0x1705071120000000
+TOL = {"fp32": 1e-5, "bf16x3": 2e-3, "bf16": 2e-3}
+
+
+@pytest.fixture(scope="module")
+def cpa():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1705_07112_gb300 as cpa
+    return cpa
+
+
+@pytest.fixture(scope="module")
+def handle(cpa):
+    h = cpa.Handle(0)
+    yield h
+    h.close()
+
+
+def to_dev(X):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
+
+
+def oracle_lambda(X64):
+    p = min(X64.shape)
+    return O.lambda_bound(X64, 20, 0.01, O.start_vector(SEED, p))["lam"]
+
+
+def shrink_of(kind, X64):
+    sig = np.sqrt(max(oracle_lambda(X64) / 1.01, 1e-30))
+    if kind == O.HARD:
+        return O.Shrink(O.HARD, 0.3 * sig)
+    if kind == O.SOFT:
+        return O.Shrink(O.SOFT, 0.2 * sig)
+    return O.Shrink(O.WSOFT, 0.0, c=0.05 * sig * sig, eps=1e-8, noise=0.01 * sig * sig)
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def run(cpa, handle, X32, s, L, lam, prec):
+    import torch
+    Y = cpa.cpa_svt(handle, to_dev(X32), {"kind": s.kind, "tau": s.tau, "c": s.c, "eps": s.eps,
+                                          "noise": s.noise}, L, lam, prec)
+    torch.cuda.synchronize()
+    return Y.cpu().numpy().astype(np.float64)
+
+
+SHAPES = [(256, 256), (300, 170), (170, 300), (129, 257), (64, 40), (40, 64), (1, 1), (1, 7), (7, 1),
+          (3, 200), (200, 3), (130, 130)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
+def test_svt_matches_oracle_shapes(cpa, handle, shape, prec):
+    rng = np.random.default_rng(1000 + shape[0] * 7 + shape[1])
+    m, n = shape
+    r = max(1, min(m, n) // 8)
+    X32 = (rng.standard_normal((m, r)) @ rng.standard_normal((r, n)) +
+           0.1 * rng.standard_normal((m, n))).astype(np.float32)
+    X64 = X32.astype(np.float64)
+    s = shrink_of(O.SOFT, X64)
+    lam = oracle_lambda(X64)
+    for L in (1, 2, 3, 17):
+        ref = O.cpa(X64, s, L, lam)
+        got = run(cpa, handle, X32, s, L, lam, prec)
+        assert rel(got, ref) <= TOL[prec], (shape, prec, L, rel(got, ref))
+
+
+@pytest.mark.parametrize("kind", [O.HARD, O.SOFT, O.WSOFT])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
+def test_svt_kinds_single_lowrank(cpa, handle, kind, prec):
+    w = inputs.single_lowrank()
+    X64 = w.X.astype(np.float64)
+    s = O.Shrink(O.SOFT, w.shrink.tau) if kind == O.SOFT else shrink_of(kind, X64)
+    lam = oracle_lambda(X64)
+    ref = O.cpa(X64, s, w.L, lam)
+    got = run(cpa, handle, w.X, s, w.L, lam, prec)
+    assert rel(got, ref) <= TOL[prec], rel(got, ref)
+
+
+def test_lambda_bound_matches_oracle(cpa, handle):
+    for shape in [(256, 256), (300, 170), (170, 300), (1, 5), (64, 40)]:
+        rng = np.random.default_rng(shape[0] + 31 * shape[1])
+        X32 = rng.standard_normal(shape).astype(np.float32)
+        X64 = X32.astype(np.float64)
+        ref = O.lambda_bound(X64, 20, 0.01, O.start_vector(SEED, min(shape)))
+        got = cpa.cpa_lambda_bound(handle, to_dev(X32), 20)
+        assert abs(got - ref["lam"]) <= 1e-4 * ref["lam"], (shape, got, ref)
+        assert got >= np.linalg.norm(X64, 2) ** 2 * (1 - 1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_computed_bound_path_matches_oracle(cpa, handle, prec):
+    # lambda_max <= 0: bound and coefficients formed on the device
+    w = inputs.single_lowrank()
+    X64 = w.X.astype(np.float64)
+    s = O.Shrink(O.SOFT, w.shrink.tau)
+    lam = oracle_lambda(X64)
+    ref = O.cpa(X64, s, w.L, lam)
+    got = run(cpa, handle, w.X, s, w.L, 0.0, prec)
+    assert abs(cpa.cpa_get_lambda(handle) - lam) <= 1e-4 * lam
+    assert rel(got, ref) <= TOL[prec]
+    c_dev = cpa.cpa_get_coeffs(handle, w.L)
+    c_ref = O.coeffs(s, w.L, lam)
+    assert np.allclose(c_dev, c_ref, rtol=1e-4, atol=1e-6 * np.abs(c_ref).max())
+
+
+def test_zero_matrix_and_argument_errors(cpa, handle):
+    import torch
+    X = torch.zeros((50, 30), device="cuda")
+    Y = cpa.cpa_svt(handle, X, {"kind": O.SOFT, "tau": 1.0}, 10, 0.0, "fp32")
+    torch.cuda.synchronize()
+    assert float(Y.abs().max()) == 0.0
+    with pytest.raises(cpa.CpaError):
+        cpa.cpa_svt(handle, X, {"kind": O.SOFT, "tau": 1.0}, 0, 1.0, "fp32")
+    with pytest.raises(cpa.CpaError):
+        cpa.cpa_svt(handle, X, {"kind": O.SOFT, "tau": -1.0}, 5, 1.0, "fp32")
+    with pytest.raises(cpa.CpaError):   # output overlapping the input
+        cpa.cpa_svt(handle, X, {"kind": O.SOFT, "tau": 1.0}, 5, 1.0, "fp32", Y=X)
+    Xn = torch.ones((20, 10), device="cuda")
+    Xn[3, 4] = float("nan")
+    with pytest.raises(cpa.CpaError) as ei:
+        cpa.cpa_lambda_bound(handle, Xn, 20)
+    assert ei.value.status == 4   # CPA_ERR_NONFINITE
+
+
+def test_leading_dimension_views(cpa, handle):
+    import torch
+    rng = np.random.default_rng(5)
+    big = rng.standard_normal((150, 120)).astype(np.float32)
+    Xd = to_dev(big)[10:110, 7:87]          # 100 x 80 view, ld = 120
+    Yd = torch.zeros((100, 96), device="cuda")[:, :80]
+    X64 = big[10:110, 7:87].astype(np.float64)
+    s = O.Shrink(O.SOFT, 2.0)
+    lam = oracle_lambda(X64)
+    for prec in ("fp32", "bf16x3"):
+        cpa.cpa_svt(handle, Xd, {"kind": O.SOFT, "tau": 2.0}, 12, lam, prec, Y=Yd)
+        torch.cuda.synchronize()
+        assert rel(Yd.cpu().numpy().astype(np.float64), O.cpa(X64, s, 12, lam)) <= TOL[prec]
+
+
+# --------------------------------------------------------------- full sizes
+
+def sampled_rows_check(cpa, handle, X32, s, L, prec, idx, tol):
+    """Compare sampled rows (m >= n) or columns (m < n) of the GPU result at
+    full size with the oracle's vector form of the same filter."""
+    X64 = X32.astype(np.float64)
+    m, n = X64.shape
+    lam = oracle_lambda(X64)
+    Y = run(cpa, handle, X32, s, L, lam, prec)
+    scale = np.linalg.norm(Y) / np.sqrt(len(Y) if m >= n else Y.shape[1])
+    for i in idx:
+        if m >= n:
+            want, got = O.cpa_vec(X64, s, L, lam, X64[i]), Y[i]
+        else:
+            want, got = O.cpa_vec(X64, s, L, lam, X64[:, i]), Y[:, i]
+        err = np.linalg.norm(got - want) / max(np.linalg.norm(want), scale)
+        assert err <= tol, (prec, i, err)
+    return lam
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "bf16x3"])
+def test_rpca_frame_full_size_sampled(cpa, handle, prec):
+    w = inputs.rpca_frame()
+    s = O.Shrink(O.SOFT, w.shrink.tau)
+    sampled_rows_check(cpa, handle, w.X, s, w.L, prec, [0, 1, 511, 1022, 1023], TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_video_background_full_size_sampled(cpa, handle, prec):
+    w = inputs.video_background()
+    s = O.Shrink(O.SOFT, w.shrink.tau)
+    sampled_rows_check(cpa, handle, w.X, s, w.L, prec, [0, 8191], TOL[prec])
