@@ -186,6 +186,31 @@ CPA_API cpa_status cpa_profile_enable(cpa_handle h, int enable);
 CPA_API cpa_status cpa_profile_read(cpa_handle h, double *ms, int64_t *launches, int reset);
 
 /* ---------------------------------------------------------------------------
+ * Kernel-level entry points used by the unit tests (no counterpart in the
+ * paper): one tensor-core product with the fused epilogue, and one FP32 ->
+ * BF16 hi/lo split.
+ *   cpa_kernel_gemm_bf16: acc(i,j) = sum_k A(i,k) B(j,k) over the nsplit
+ *   segments (1: hi*hi; 3: hi*hi + hi*lo + lo*hi), A: M x K and B: N x K
+ *   row-major BF16 (ld multiple of 8, 16-byte aligned).
+ *   sym = 0: D(i,j) = s_acc * acc + (i == j ? diag : 0), D: M x N FP32;
+ *            C, C2, H, Dhi, Dlo must be NULL.
+ *   sym = 1 (M == N, the output symmetric; only upper tiles are computed):
+ *            v = s_acc acc + s_c C + s_c2 C2 + diag on the diagonal,
+ *            D = v and H += coef[k] v in the LOWER triangle (row >= col;
+ *            C, C2, H, D share ld = ldd), Dhi/Dlo = BF16 hi/lo of v in
+ *            BOTH triangles (ld = ldh).  This is one recurrence step.
+ *   cpa_kernel_split_bf16: hi = bf16(X), lo = bf16(X - hi), transposed
+ *   (out is cols x rows) when transpose != 0.
+ * ------------------------------------------------------------------------- */
+CPA_API cpa_status cpa_kernel_gemm_bf16(int M, int N, int K, const void *A_hi, const void *A_lo, int64_t lda,
+                                        const void *B_hi, const void *B_lo, int64_t ldb, int nsplit, int sym,
+                                        float s_acc, const float *C, float s_c, const float *C2, float s_c2,
+                                        float diag, float *H, const double *coef, int k, float *D, int64_t ldd,
+                                        void *Dhi, void *Dlo, int64_t ldh, void *stream);
+CPA_API cpa_status cpa_kernel_split_bf16(const float *X, int rows, int cols, int64_t ldx, int transpose, void *hi,
+                                         void *lo, int64_t ldo, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Batched shrinkage of many small independent matrices (patch groups), one
  * persistent launch.  The matrices live packed in one device buffer: matrix
  * i starts at element offset off[i] and is row-major m[i] x n[i] with

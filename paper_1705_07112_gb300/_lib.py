@@ -23,7 +23,7 @@ PREC = {"fp32": FP32, "tf32": TF32, "bf16": BF16, "bf16x3": BF16X3}
 EXPORTS = ["cpa_create", "cpa_destroy", "cpa_status_string", "cpa_last_error", "cpa_coeffs",
            "cpa_lambda_bound", "cpa_svt", "cpa_get_lambda", "cpa_get_coeffs", "cpa_batch_create",
            "cpa_batch_destroy", "cpa_svt_batched", "cpa_batch_lambdas", "cpa_profile_enable",
-           "cpa_profile_read"]
+           "cpa_profile_read", "cpa_kernel_gemm_bf16", "cpa_kernel_split_bf16"]
 STAGES = ["prep", "gram", "bound", "coeff", "shift", "recur", "apply"]
 
 
@@ -74,6 +74,12 @@ def load(path: str = LIB_PATH):
                                                ctypes.c_int, _vp, _vp]),
             "cpa_batch_lambdas": (_vp, [_vp]),
             "cpa_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
+            "cpa_kernel_gemm_bf16": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _i64, _vp,
+                                                    _vp, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_float, _vp,
+                                                    ctypes.c_float, _vp, ctypes.c_float, ctypes.c_float, _vp, _vp,
+                                                    ctypes.c_int, _vp, _i64, _vp, _vp, _i64, _vp]),
+            "cpa_kernel_split_bf16": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, ctypes.c_int, _vp,
+                                                     _vp, _i64, _vp]),
             "cpa_profile_read": (ctypes.c_int, [_vp, _P(_d), _P(_i64), ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
@@ -219,3 +225,26 @@ def cpa_profile_read(h: Handle, reset: bool = True) -> dict:
     n = (ctypes.c_int64 * len(STAGES))()
     _check(load().cpa_profile_read(h.ptr, ms, n, 1 if reset else 0), "cpa_profile_read")
     return {st: {"ms": ms[i], "launches": n[i]} for i, st in enumerate(STAGES)}
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def kernel_gemm_bf16(A_hi, A_lo, B_hi, B_lo, nsplit, D, sym=False, s_acc=1.0, C=None, s_c=0.0, C2=None, s_c2=0.0,
+                     diag=0.0, H=None, coef=None, k=0, Dhi=None, Dlo=None, stream=None):
+    """One tensor-core product with the fused epilogue (diagnostic entry)."""
+    M, K = A_hi.shape
+    N = B_hi.shape[0]
+    _check(load().cpa_kernel_gemm_bf16(M, N, K, _ptr(A_hi), _ptr(A_lo), A_hi.stride(0), _ptr(B_hi), _ptr(B_lo),
+                                       B_hi.stride(0), int(nsplit), 1 if sym else 0, float(s_acc), _ptr(C),
+                                       float(s_c), _ptr(C2), float(s_c2), float(diag), _ptr(H), _ptr(coef), int(k),
+                                       _ptr(D), D.stride(0), _ptr(Dhi), _ptr(Dlo),
+                                       Dhi.stride(0) if Dhi is not None else 0, _stream_ptr(stream)),
+           "cpa_kernel_gemm_bf16")
+
+
+def kernel_split_bf16(X, transpose, hi, lo, stream=None):
+    rows, cols = X.shape
+    _check(load().cpa_kernel_split_bf16(_ptr(X), rows, cols, X.stride(0), 1 if transpose else 0, _ptr(hi),
+                                        _ptr(lo), hi.stride(0), _stream_ptr(stream)), "cpa_kernel_split_bf16")

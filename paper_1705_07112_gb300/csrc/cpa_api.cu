@@ -12,6 +12,11 @@
 
 using namespace cpa;
 
+namespace {
+// below this p the BF16 mode also splits the recurrence operands
+constexpr int64_t kSplitRecBelow = 256;
+}  // namespace
+
 struct cpa_ctx {
     int device = 0;
     int num_sms = 0;
@@ -190,7 +195,7 @@ SvtWs carve(char *base, int64_t m, int64_t n, int L, int iters, int prec) {
         // Gram and final product always use the hi/lo split (their BF16
         // rounding would otherwise dominate the error); the recurrence
         // operands carry a lo part only in the all-split mode.
-        bool split_rec = prec == CPA_BF16X3;
+        bool split_rec = prec == CPA_BF16X3 || p < kSplitRecBelow;
         w.ldn = round_up(n, 8);
         w.ldm = round_up(m, 8);
         w.Ahi = c.take<__nv_bfloat16>(pp);
@@ -315,8 +320,11 @@ cpa_status run_gram(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
             CK(gemm_f32((int)p, (int)p, (int)n, dX, ldx, true, dX, ldx, true, e, st));
         return CPA_OK;
     }
-    // tensor cores: K-major BF16 hi/lo operand of the contraction dimension
+    // tensor cores: K-major BF16 hi/lo operand of the contraction dimension;
+    // upper tiles only, mirrored, so G is exactly symmetric
     const int nsplit = 3;
+    e.symmetric_upper = 1;
+    e.sym_full_d = 1;   // G is read in full by the power iteration and the shift
     TcOperand op;
     if (m >= n) {   // rows of X^T (n x m)
         op.hi = w.Xthi; op.lo = w.Xtlo; op.ld = w.ldm; op.rows = (int)n;
@@ -350,7 +358,8 @@ cpa_status cpa_lambda_bound(cpa_handle h, const float *dX, int64_t m, int64_t n,
     w = carve(h->ws, m, n, 1, iters, CPA_FP32);
     int64_t p = std::min(m, n);
     if ((s = run_gram(h, dX, m, n, ldx, w, CPA_FP32, st)) != CPA_OK) return s;
-    CK(power_bound(w.G, w.ldp, (int)p, iters, w.v0, w.v1, w.norm2, w.out, st));
+    CK(power_bound_persistent(w.G, w.ldp, (int)p, iters, w.v0, w.v1, w.norm2, (unsigned int *)w.flag, w.flag + 1,
+                              w.out, st, h->num_sms));
     CK(cudaMemcpyAsync(h->h_pin, w.out, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (h->h_pin[4] != 0.0) return (cpa_status)(int)h->h_pin[4];
@@ -381,7 +390,11 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
     w = carve(h->ws, m, n, L, iters, prec);
     const int64_t p = std::min(m, n);
     const bool tc = prec != CPA_FP32;
-    const int nsplit_rec = prec == CPA_BF16X3 ? 3 : 1;   // Gram and final product: always 3
+    // Gram and final product: always split.  Recurrence: split in BF16X3
+    // mode, and for small p in BF16 mode too (there the products are
+    // latency-bound, and a single BF16 rounding of a tiny matrix is not
+    // averaged out).
+    const int nsplit_rec = (prec == CPA_BF16X3 || p < kSplitRecBelow) ? 3 : 1;
     ShrinkParams sp_ = to_params(sh);
 
     // operand preparation for the tensor-core path: X and X^T as BF16 hi/lo
@@ -401,8 +414,9 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
         set_scalar2_kernel<<<1, 1, 0, st>>>(w.out + 3, lambda_max, 0.0);
         CK(cudaGetLastError());
     } else {
-        StageScope sc(h, CPA_STAGE_BOUND, st, iters + 3);
-        CK(power_bound(w.G, w.ldp, (int)p, iters, w.v0, w.v1, w.norm2, w.out, st));
+        StageScope sc(h, CPA_STAGE_BOUND, st, 1);
+        CK(power_bound_persistent(w.G, w.ldp, (int)p, iters, w.v0, w.v1, w.norm2, (unsigned int *)w.flag,
+                                  w.flag + 1, w.out, st, h->num_sms));
     }
     // coefficients (FP64, on the device so the call stays asynchronous)
     {
@@ -412,39 +426,42 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
     // shift and initial sum; Psi_1 = B_hat lives in ring slot 1
     {
         StageScope sc(h, CPA_STAGE_SHIFT, st, 1);
-        CK(shift_init(w.G, w.ldp, (int)p, w.out + 3, w.coef, L, w.A, w.Z[1], w.H, w.ldp, tc ? w.Ahi : nullptr,
-                      tc ? w.Alo : nullptr, w.ldp, st, h->num_sms));
+        CK(shift_init(w.G, w.ldp, (int)p, w.out + 3, w.coef, L, tc ? nullptr : w.A, w.Z[1], w.H, w.ldp,
+                      tc ? w.Ahi : nullptr, tc ? w.Alo : nullptr, tc ? w.Zhi[1] : nullptr,
+                      tc ? w.Zlo[1] : nullptr, w.ldp, st, h->num_sms));
     }
-    // recurrence with fused accumulation: Psi_k = 2 B_hat Psi_{k-1} - Psi_{k-2}, H += c_k Psi_k
+    // recurrence with fused accumulation: Psi_k = 2 B_hat Psi_{k-1} - Psi_{k-2}, H += c_k Psi_k.
+    // Ring: Psi_k overwrites Psi_{k-2} in slot k&1; Psi_0 = Id is implicit.
+    // The tensor-core path multiplies by At = (2/lambda) G and applies the
+    // shift exactly in the FP32 epilogue:  Psi_k = 2 At Psi_{k-1} - 2 Psi_{k-1} - Psi_{k-2}.
     for (int k = 2; k < L; ++k) {
         StageScope sc(h, CPA_STAGE_RECUR, st, 1);
         Epilogue e;
         int cur = k & 1, prev = (k - 1) & 1;
         e.D = w.Z[cur];
         e.ldd = w.ldp;
-        e.C = (k == 2) ? nullptr : w.Z[cur];
+        e.C = (k == 2) ? nullptr : w.Z[cur];   // Psi_{k-2}
         e.ldc = w.ldp;
         e.s_acc = 2.f;
         e.s_c = -1.f;
-        e.diag = (k == 2) ? -1.f : 0.f;   // Psi_0 = Id
+        e.diag = (k == 2) ? -1.f : 0.f;        // - Psi_0 = - Id
         e.H = w.H;
         e.ldh = w.ldp;
         e.coef = w.coef;
         e.k = k;
+        e.symmetric_upper = 1;
         if (!tc) {
-            e.symmetric_upper = 1;
             CK(gemm_f32((int)p, (int)p, (int)p, w.A, w.ldp, true, w.Z[prev], w.ldp, true, e, st));
         } else {
+            e.C2 = w.Z[prev];                  // Psi_{k-1}
+            e.ldc2 = w.ldp;
+            e.s_c2 = -2.f;
             e.Dhi = w.Zhi[cur];
             e.Dlo = w.Zlo[cur];
             e.ldb = w.ldp;
             TcOperand a, b;
             a.hi = w.Ahi; a.lo = w.Alo; a.ld = w.ldp; a.rows = (int)p;
-            if (k == 2) {   // Psi_1 = B_hat: its BF16 parts are A's
-                b = a;
-            } else {
-                b.hi = w.Zhi[prev]; b.lo = w.Zlo[prev]; b.ld = w.ldp; b.rows = (int)p;
-            }
+            b.hi = w.Zhi[prev]; b.lo = w.Zlo[prev]; b.ld = w.ldp; b.rows = (int)p;
             CK(gemm_tc((int)p, (int)p, (int)p, a, b, nsplit_rec, e, st, h->num_sms));
         }
     }
@@ -459,7 +476,9 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
         else
             CK(gemm_f32((int)m, (int)n, (int)m, w.H, w.ldp, true, dX, ldx, false, e, st));
     } else {
-        CK(split_bf16(w.H, (int)p, (int)p, w.ldp, false, w.Hhi, w.Hlo, w.ldp, st));
+        // H is valid in its lower triangle (the tensor-core epilogue keeps
+        // the FP32 arrays there); the split writes both triangles
+        CK(split_sym_lower(w.H, (int)p, w.ldp, w.Hhi, w.Hlo, w.ldp, st));
         TcOperand hop, xop;
         hop.hi = w.Hhi; hop.lo = w.Hlo; hop.ld = w.ldp; hop.rows = (int)p;
         if (m >= n) {   // Y(r,j) = sum_l X[r][l] H[j][l]
@@ -530,6 +549,59 @@ cpa_status cpa_profile_read(cpa_handle h, double *ms, int64_t *launches, int res
             h->launches[i] = 0;
         }
     }
+    return CPA_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+cpa_status cpa_kernel_gemm_bf16(int M, int N, int K, const void *A_hi, const void *A_lo, int64_t lda,
+                                const void *B_hi, const void *B_lo, int64_t ldb, int nsplit, int sym, float s_acc,
+                                const float *C, float s_c, const float *C2, float s_c2, float diag, float *H,
+                                const double *coef, int k, float *D, int64_t ldd, void *Dhi, void *Dlo, int64_t ldh,
+                                void *stream) {
+    if (M < 1 || N < 1 || K < 1 || !A_hi || !B_hi || !D || ldd < N || lda < K || ldb < K ||
+        (nsplit != 1 && nsplit != 3) || (sym && M != N) || (H && !coef))
+        return CPA_ERR_INVALID_ARG;
+    if (!sym && (C || C2 || H || Dhi || Dlo)) return CPA_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    TcOperand a, b;
+    a.hi = (const __nv_bfloat16 *)A_hi; a.lo = (const __nv_bfloat16 *)A_lo; a.ld = lda; a.rows = M;
+    b.hi = (const __nv_bfloat16 *)B_hi; b.lo = (const __nv_bfloat16 *)B_lo; b.ld = ldb; b.rows = N;
+    Epilogue e;
+    e.D = D;
+    e.ldd = ldd;
+    e.s_acc = s_acc;
+    e.C = C;
+    e.ldc = ldd;
+    e.s_c = s_c;
+    e.C2 = C2;
+    e.ldc2 = ldd;
+    e.s_c2 = s_c2;
+    e.diag = diag;
+    e.H = H;
+    e.ldh = ldd;
+    e.coef = coef;
+    e.k = k;
+    e.Dhi = (__nv_bfloat16 *)Dhi;
+    e.Dlo = (__nv_bfloat16 *)Dlo;
+    e.ldb = ldh;
+    e.symmetric_upper = sym ? 1 : 0;
+    cudaError_t r = gemm_tc(M, N, K, a, b, nsplit, e, (cudaStream_t)stream, sms);
+    if (r == cudaErrorInvalidValue) return CPA_ERR_INVALID_ARG;
+    if (r != cudaSuccess) return cuda_fail(r, "gemm_tc");
+    return CPA_OK;
+}
+
+cpa_status cpa_kernel_split_bf16(const float *X, int rows, int cols, int64_t ldx, int transpose, void *hi, void *lo,
+                                 int64_t ldo, void *stream) {
+    if (!X || !hi || rows < 1 || cols < 1 || ldx < cols || ldo < (transpose ? rows : cols))
+        return CPA_ERR_INVALID_ARG;
+    CK(split_bf16(X, rows, cols, ldx, transpose != 0, (__nv_bfloat16 *)hi, (__nv_bfloat16 *)lo, ldo,
+                  (cudaStream_t)stream));
     return CPA_OK;
 }
 

@@ -11,8 +11,13 @@
 //               tcgen05.mma kind::f16 (M=128, N=BN, K=16) per 32-byte K step,
 //               tcgen05.commit frees a stage / publishes an accumulator.
 //   warps 2..5  epilogue: tcgen05.ld 32x32b (one accumulator row per thread),
-//               fused  D = s_acc*acc + s_c*C + diag,  H += c_k D,  BF16 hi/lo
-//               copies of D, while the MMA warp fills the other accumulator.
+//               fused  D = s_acc*acc + s_c*C + s_c2*C2 + diag,  H += c_k D,
+//               BF16 hi/lo copies of D, while the MMA warp fills the other
+//               accumulator.  Symmetric outputs: only tiles meeting the upper
+//               triangle are computed; the FP32 arrays are read and written at
+//               the mirrored position (j,i), which is coalesced when each lane
+//               owns one row, and the values for (i,j) go through a per-warp
+//               shared-memory transpose so those stores are coalesced too.
 // Split precision (nsplit = 3) runs the K loop three times over
 // (A_hi,B_hi), (A_hi,B_lo), (A_lo,B_hi) into the same accumulator.
 //
@@ -139,67 +144,120 @@ struct Smem {
     static constexpr int kStageA = BM * BK * 2;
     static constexpr int kStageB = BN * BK * 2;
     static constexpr int kStages = (BN == 256) ? 4 : (BN == 128 ? 6 : 8);
-    static constexpr int kBytes = kStages * (kStageA + kStageB) + 1024 /* align */ + 256 /* barriers */;
+    static constexpr int kBytes =
+        kStages * (kStageA + kStageB) + 4 * 32 * 33 * 4 /* transpose */ + 1024 /* align */ + 256 /* barriers */;
 };
 
-__device__ __forceinline__ void epi_scalar(const Epilogue &e, float ck, int i, int j, float acc) {
-    float v = e.s_acc * acc;
-    if (e.C) v = fmaf(e.s_c, e.C[(int64_t)i * e.ldc + j], v);
-    if (i == j) v += e.diag;
-    e.D[(int64_t)i * e.ldd + j] = v;
-    if (e.H) {
-        float *hp = e.H + (int64_t)i * e.ldh + j;
-        *hp = fmaf(ck, v, *hp);
-    }
-    if (e.Dhi) {
-        __nv_bfloat16 h = __float2bfloat16_rn(v);
-        e.Dhi[(int64_t)i * e.ldb + j] = h;
-        if (e.Dlo) e.Dlo[(int64_t)i * e.ldb + j] = __float2bfloat16_rn(v - __bfloat162float(h));
-    }
+// ------------------------------------------------------------------ epilogue
+
+__device__ __forceinline__ uint32_t pack_hilo(float v) {
+    __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    return (uint32_t)__bfloat16_as_ushort(hi) | ((uint32_t)__bfloat16_as_ushort(lo) << 16);
 }
 
-__device__ __forceinline__ void epi_vec4(const Epilogue &e, float ck, int i, int j, const float *v4, bool vec) {
-    if (vec) {
-        float4 v = make_float4(e.s_acc * v4[0], e.s_acc * v4[1], e.s_acc * v4[2], e.s_acc * v4[3]);
-        if (e.C) {
-            float4 c = *reinterpret_cast<const float4 *>(e.C + (int64_t)i * e.ldc + j);
-            v.x = fmaf(e.s_c, c.x, v.x); v.y = fmaf(e.s_c, c.y, v.y);
-            v.z = fmaf(e.s_c, c.z, v.z); v.w = fmaf(e.s_c, c.w, v.w);
+// One 32 x 32 block of the accumulator held by a warp: lane l owns row
+// i = r0 + l, acc[c] is column j = j0 + c.  tbuf: 32 x 33 words of shared
+// memory private to the warp.
+__device__ __forceinline__ void epilogue_block(const Epilogue &e, float ck, int M, int N, int r0, int j0, int lane,
+                                               const float *acc, uint32_t *tbuf) {
+    const bool sym = e.symmetric_upper != 0;
+    const int i = r0 + lane;
+    uint32_t vbits[32];
+    uint32_t hl[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        const int j = j0 + c;
+        float v = e.s_acc * acc[c];
+        hl[c] = 0u;
+        if (sym) {
+            const bool ok = (i < M) && (j < N) && (j >= i);
+            if (ok) {
+                // mirrored position (j,i): lanes touch consecutive addresses
+                if (e.C) v = fmaf(e.s_c, e.C[(int64_t)j * e.ldc + i], v);
+                if (e.C2) v = fmaf(e.s_c2, e.C2[(int64_t)j * e.ldc2 + i], v);
+                if (i == j) v += e.diag;
+                e.D[(int64_t)j * e.ldd + i] = v;
+                if (e.H) {
+                    float *hp = e.H + (int64_t)j * e.ldh + i;
+                    *hp = fmaf(ck, v, *hp);
+                }
+                if (e.Dhi) {
+                    uint32_t p = pack_hilo(v);
+                    hl[c] = p;
+                    e.Dhi[(int64_t)j * e.ldb + i] = __ushort_as_bfloat16((unsigned short)(p & 0xFFFF));
+                    if (e.Dlo) e.Dlo[(int64_t)j * e.ldb + i] = __ushort_as_bfloat16((unsigned short)(p >> 16));
+                }
+            }
+        } else if (i == j) {
+            v += e.diag;
         }
-        if (i >= j && i < j + 4) (&v.x)[i - j] += e.diag;
-        *reinterpret_cast<float4 *>(e.D + (int64_t)i * e.ldd + j) = v;
-        if (e.H) {
-            float4 *hp = reinterpret_cast<float4 *>(e.H + (int64_t)i * e.ldh + j);
-            float4 h = *hp;
-            h.x = fmaf(ck, v.x, h.x); h.y = fmaf(ck, v.y, h.y);
-            h.z = fmaf(ck, v.z, h.z); h.w = fmaf(ck, v.w, h.w);
-            *hp = h;
-        }
-        if (e.Dhi) {
-            __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
-            uint2 hv;
-            hv.x = *reinterpret_cast<uint32_t *>(&h01);
-            hv.y = *reinterpret_cast<uint32_t *>(&h23);
-            *reinterpret_cast<uint2 *>(e.Dhi + (int64_t)i * e.ldb + j) = hv;
-            if (e.Dlo) {
-                float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
-                __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
-                __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
-                uint2 lv;
-                lv.x = *reinterpret_cast<uint32_t *>(&l01);
-                lv.y = *reinterpret_cast<uint32_t *>(&l23);
-                *reinterpret_cast<uint2 *>(e.Dlo + (int64_t)i * e.ldb + j) = lv;
+        vbits[c] = __float_as_uint(v);
+    }
+    // (i,j) positions through the transpose: pass 0 the FP32 D (general
+    // outputs, or symmetric ones kept in full), pass 1 the BF16 hi/lo copies
+    const bool pass0 = !sym || e.sym_full_d;
+    const bool pass1 = sym && e.Dhi != nullptr;
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 0 && !pass0) continue;
+        if (pass == 1 && !pass1) continue;
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < 32; ++c) tbuf[lane * 33 + c] = pass == 0 ? vbits[c] : hl[c];
+        __syncwarp();
+        const int jj = j0 + lane;
+#pragma unroll 4
+        for (int rr = 0; rr < 32; ++rr) {
+            const int ii = r0 + rr;
+            const bool ok = ii < M && jj < N && (!sym || jj > ii);
+            if (!ok) continue;
+            const uint32_t val = tbuf[rr * 33 + lane];
+            if (pass == 0) {
+                e.D[(int64_t)ii * e.ldd + jj] = __uint_as_float(val);
+            } else {
+                e.Dhi[(int64_t)ii * e.ldb + jj] = __ushort_as_bfloat16((unsigned short)(val & 0xFFFF));
+                if (e.Dlo) e.Dlo[(int64_t)ii * e.ldb + jj] = __ushort_as_bfloat16((unsigned short)(val >> 16));
             }
         }
+    }
+    __syncwarp();
+}
+
+// Output tile t of the persistent schedule.  Symmetric outputs visit only
+// tiles meeting the upper triangle: in tile row tm these start at column
+// tile (tm*BM)/BN.
+__device__ __forceinline__ void tile_of(int t, int tiles_m, int tiles_n, int sym, int bn, int &tm, int &tn) {
+    if (!sym) {
+        tm = t / tiles_n;
+        tn = t % tiles_n;
         return;
     }
-    for (int q = 0; q < 4; ++q) epi_scalar(e, ck, i, j + q, v4[q]);
+    for (tm = 0; tm < tiles_m; ++tm) {
+        const int first = (tm * BM) / bn;
+        const int cnt = tiles_n - first;
+        if (t < cnt) {
+            tn = first + t;
+            return;
+        }
+        t -= cnt;
+    }
+    tn = 0;
+}
+
+__host__ __device__ inline int count_tiles(int tiles_m, int tiles_n, int sym, int bn) {
+    if (!sym) return tiles_m * tiles_n;
+    int c = 0;
+    for (int tm = 0; tm < tiles_m; ++tm) {
+        int first = (tm * BM) / bn;
+        if (first < tiles_n) c += tiles_n - first;
+    }
+    return c;
 }
 
 template <int BN>
 __global__ void __launch_bounds__(kThreads, 1)
-    gemm_tc_kernel(const __grid_constant__ TileMaps maps, int M, int N, int K, int nsplit, Epilogue e, int vec_ok,
-                   int *err) {
+    gemm_tc_kernel(const __grid_constant__ TileMaps maps, int M, int N, int K, int nsplit, Epilogue e, int *err) {
     using S = Smem<BN>;
     constexpr int kStages = S::kStages;
     constexpr uint32_t kTmemCols = 2 * BN;   // two accumulators
@@ -209,7 +267,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = smem;
     uint8_t *sB = smem + kStages * S::kStageA;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + kStages * S::kStageB);
+    uint32_t *tbuf_all = reinterpret_cast<uint32_t *>(sB + kStages * S::kStageB);   // 4 x 32 x 33 words
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tbuf_all + 4 * 32 * 33);
     uint64_t *full = bars;                 // [kStages]
     uint64_t *empty = bars + kStages;      // [kStages]
     uint64_t *tfull = bars + 2 * kStages;  // [2]
@@ -219,7 +278,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
-    const int ntiles = tiles_m * tiles_n;
+    const int sym = e.symmetric_upper;
+    const int ntiles = count_tiles(tiles_m, tiles_n, sym, BN);
     const int kb_per = (K + BK - 1) / BK;
     const int nkb = kb_per * nsplit;
 
@@ -253,7 +313,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t phase = 0;
             uint32_t armed_mask = 0, armed_phase = 0;   // per stage: armed at least once / phase it was armed in
             for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
-                const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
+                int tm, tn;
+                tile_of(t, tiles_m, tiles_n, sym, BN, tm, tn);
+                const int m0 = tm * BM, n0 = tn * BN;
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) break;
                     const int seg = kb / kb_per, kx = (kb % kb_per) * BK;
@@ -321,6 +383,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // ------------------------------------------------------------ epilogue
         const int quarter = warp & 3;   // TMEM lanes 32*quarter .. +31
+        uint32_t *tbuf = tbuf_all + quarter * (32 * 33);
         const float ck = e.H ? (float)e.coef[e.k] : 0.f;
         uint32_t tphase[2] = {0, 0};
         int local = 0;
@@ -329,27 +392,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!mbar_wait(&tfull[buf], tphase[buf], abort_flag)) break;
             tphase[buf] ^= 1;
             fence_after();
-            const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
-            const int i = m0 + quarter * 32 + lane;
+            int tm, tn;
+            tile_of(t, tiles_m, tiles_n, sym, BN, tm, tn);
+            const int r0 = tm * BM + quarter * 32, n0 = tn * BN;
             const uint32_t trow = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN);
 #pragma unroll 1
             for (int c = 0; c < BN / 32; ++c) {
-                float v[32];
-                tmem_ld32(trow + (uint32_t)(c * 32), v);
+                float acc[32];
+                tmem_ld32(trow + (uint32_t)(c * 32), acc);
                 const int j0 = n0 + c * 32;
-                if (i < M && j0 < N) {
-                    const bool full_chunk = (j0 + 32 <= N);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        int j = j0 + 4 * q;
-                        if (full_chunk) {
-                            epi_vec4(e, ck, i, j, v + 4 * q, vec_ok != 0);
-                        } else {
-                            for (int r = 0; r < 4; ++r)
-                                if (j + r < N) epi_scalar(e, ck, i, j + r, v[4 * q + r]);
-                        }
-                    }
-                }
+                if (r0 >= M || j0 >= N) continue;
+                if (sym && j0 + 31 < r0) continue;   // block entirely below the diagonal
+                epilogue_block(e, ck, M, N, r0, j0, lane, acc, tbuf);
             }
             fence_before();
             __syncwarp();
@@ -366,7 +420,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (threadIdx.x == 0 && *abort_flag) atomicExch(err, CPA_ERR_TIMEOUT);
 }
-
 // ------------------------------------------------------------------- host side
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -413,12 +466,9 @@ cudaError_t launch(int M, int N, int K, const TcOperand &A, const TcOperand &B, 
     if (!make_map(&maps.a_hi, A.hi, A.ld, A.rows, K, BM) || !make_map(&maps.a_lo, alo, A.ld, A.rows, K, BM) ||
         !make_map(&maps.b_hi, B.hi, B.ld, B.rows, K, BN) || !make_map(&maps.b_lo, blo, B.ld, B.rows, K, BN))
         return cudaErrorInvalidValue;
-    const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    const int tiles = count_tiles((M + BM - 1) / BM, (N + BN - 1) / BN, e.symmetric_upper, BN);
     const int grid = tiles < num_sms ? tiles : num_sms;
-    bool vec_ok = ((e.ldd | e.ldc | e.ldh) % 4 == 0) && (e.ldb % 4 == 0) && ((uintptr_t)e.D % 16 == 0) &&
-                  ((uintptr_t)e.C % 16 == 0) && ((uintptr_t)e.H % 16 == 0) && ((uintptr_t)e.Dhi % 8 == 0) &&
-                  ((uintptr_t)e.Dlo % 8 == 0);
-    gemm_tc_kernel<BN><<<grid, kThreads, S::kBytes, st>>>(maps, M, N, K, nsplit, e, vec_ok ? 1 : 0, g_err_dev);
+    gemm_tc_kernel<BN><<<grid, kThreads, S::kBytes, st>>>(maps, M, N, K, nsplit, e, g_err_dev);
     return cudaGetLastError();
 }
 
@@ -441,13 +491,18 @@ cudaError_t gemm_tc(int M, int N, int K, const TcOperand &A, const TcOperand &B,
     if (!load_encode()) return cudaErrorNotSupported;
     if ((A.ld % 8) || (B.ld % 8) || ((uintptr_t)A.hi % 16) || ((uintptr_t)B.hi % 16)) return cudaErrorInvalidValue;
     if (nsplit == 3 && (!A.lo || !B.lo)) return cudaErrorInvalidValue;
+    if (e.symmetric_upper && M != N) return cudaErrorInvalidValue;
+    // general outputs carry only D
+    if (!e.symmetric_upper && (e.C || e.C2 || e.H || e.Dhi || e.Dlo)) return cudaErrorInvalidValue;
     int *flag;
     cudaError_t r = gemm_tc_error_flag(&flag);
     if (r != cudaSuccess) return r;
     // tile width: the widest whose tile count still fills the SMs
-    const int tm = (M + BM - 1) / BM;
-    if (tm * ((N + 255) / 256) >= num_sms || N > 4096) return launch<256>(M, N, K, A, B, nsplit, e, st, num_sms);
-    if (tm * ((N + 127) / 128) >= num_sms) return launch<128>(M, N, K, A, B, nsplit, e, st, num_sms);
+    const int tm = (M + BM - 1) / BM, sym = e.symmetric_upper;
+    if (count_tiles(tm, (N + 255) / 256, sym, 256) >= num_sms || N > 4096)
+        return launch<256>(M, N, K, A, B, nsplit, e, st, num_sms);
+    if (count_tiles(tm, (N + 127) / 128, sym, 128) >= num_sms)
+        return launch<128>(M, N, K, A, B, nsplit, e, st, num_sms);
     return launch<64>(M, N, K, A, B, nsplit, e, st, num_sms);
 }
 

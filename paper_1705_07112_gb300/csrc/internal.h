@@ -48,25 +48,35 @@ constexpr int kDefaultPowerIters = 20;
 
 // ---------------------------------------------------------------------------
 // Fused GEMM epilogue used by every dense product of the path:
-//   v = s_acc * acc + s_c * C(i,j) + (i == j ? diag : 0)
+//   v = s_acc * acc + s_c * C(i,j) + s_c2 * C2(i,j) + (i == j ? diag : 0)
 //   D(i,j) = v;   if H: H(i,j) += coef[k] * v
 // D and C may alias (the recurrence overwrites Psi_{k-2} with Psi_k).
 // Optional BF16 hi/lo copies of v (hi = bf16(v), lo = bf16(v - hi)) are
 // written for the tensor-core operand of the next product.
+// symmetric_upper: the output is symmetric and only tiles meeting the upper
+// triangle are computed.  SIMT kernel: every array is written in full.
+// Tensor-core kernel: C, C2, H and D are read/written at the lower-triangle
+// position (j,i), j >= i, so the FP32 arrays are valid in their lower
+// triangle (D in full when sym_full_d), while the BF16 copies Dhi/Dlo are
+// written in full (they are the next product's TMA operand).  General
+// (non-symmetric) tensor-core outputs carry D only.
 // ---------------------------------------------------------------------------
 struct Epilogue {
     float *D = nullptr;
     int64_t ldd = 0;
     const float *C = nullptr;
     int64_t ldc = 0;
-    float s_acc = 1.f, s_c = 0.f, diag = 0.f;
+    const float *C2 = nullptr;
+    int64_t ldc2 = 0;
+    float s_acc = 1.f, s_c = 0.f, s_c2 = 0.f, diag = 0.f;
     float *H = nullptr;
     int64_t ldh = 0;
     const double *coef = nullptr;
     int k = 0;
     __nv_bfloat16 *Dhi = nullptr, *Dlo = nullptr;
     int64_t ldb = 0;
-    int symmetric_upper = 0;   // compute only tiles with tile_n >= tile_m, mirror
+    int symmetric_upper = 0;
+    int sym_full_d = 0;
 };
 
 // SIMT FP32 GEMM: out(i,j) = epi(sum_k A(i,k) B(j,k)),  i < M, j < N, k < K.
@@ -99,11 +109,24 @@ namespace cpa {
 // {theta, r, trace, lambda, status}.  v0, v1: p floats; norm2: iters+2 doubles.
 cudaError_t power_bound(const float *G, int64_t ldg, int p, int iters, float *v0, float *v1, double *norm2,
                         double *out, cudaStream_t st);
+// The same bound with all iterations in one cooperative launch (grid
+// barrier between iterations).  bar, err: device scratch words.
+cudaError_t power_bound_persistent(const float *G, int64_t ldg, int p, int iters, float *v0, float *v1,
+                                   double *norm2, unsigned int *bar, int *err, double *out, cudaStream_t st,
+                                   int num_sms);
 cudaError_t device_coeffs(const double *lam_dev, double lam_host, int L, const ShrinkParams &s, double *c,
                           cudaStream_t st);
+// A = (2/lambda) G - Id, Z1 = A, H = c0/2 Id + c1 A (FP32).  For the
+// tensor-core path also At = (2/lambda) G as BF16 hi/lo (the operand of every
+// recurrence product; the -Id is applied exactly in the FP32 epilogue) and
+// Z1 as BF16 hi/lo.
 cudaError_t shift_init(const float *G, int64_t ldg, int p, const double *lam, const double *c, int L, float *A,
-                       float *Z1, float *H, int64_t ld, __nv_bfloat16 *Ahi, __nv_bfloat16 *Alo, int64_t ldb,
-                       cudaStream_t st, int num_sms);
+                       float *Z1, float *H, int64_t ld, __nv_bfloat16 *Athi, __nv_bfloat16 *Atlo,
+                       __nv_bfloat16 *Z1hi, __nv_bfloat16 *Z1lo, int64_t ldb, cudaStream_t st, int num_sms);
+// hi/lo split of a symmetric p x p matrix valid in its lower triangle, both
+// triangles written.
+cudaError_t split_sym_lower(const float *S, int p, int64_t lds, __nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t ldo,
+                            cudaStream_t st);
 cudaError_t check_finite(const float *X, int64_t rows, int64_t cols, int64_t ldx, int *flag, cudaStream_t st,
                          int num_sms);
 

@@ -138,17 +138,34 @@ __global__ void power_final_kernel(const float *vu, const double *nv, const floa
     (void)nw;
 }
 
-// Shifted Chebyshev coefficients (Eq. chebychev_coeff_shifted), FP64.
+// Shifted Chebyshev coefficients (Eq. chebychev_coeff_shifted), FP64:
+//   c_k = (2/L) sum_l cos(k theta_l) h(lam/2 (cos theta_l + 1)),
+//   theta_l = pi (l - 1/2) / L.
+// k theta_l = pi k (2l - 1) / (2L), so every cosine is cos(pi m / (2L)) for
+// an integer m taken mod 4L: one table of 4L values replaces L^2 cosines
+// (FP64 transcendental throughput is low on this part).
 __global__ void coeffs_kernel(const double *lam_dev, double lam_host, int L, ShrinkParams s, double *c) {
-    double lam = lam_dev ? lam_dev[0] : lam_host;
-    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+    extern __shared__ double sh[];
+    double *tab = sh;            // [4L]
+    double *hs = sh + 4 * L;     // [L]
+    const double lam = lam_dev ? lam_dev[0] : lam_host;
+    for (int m = threadIdx.x; m < 4 * L; m += blockDim.x) tab[m] = cospi((double)m / (2.0 * L));
+    __syncthreads();
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+        // cos theta_l = cos(pi (2l+1) / (2L)) for the 0-based l
+        const double x = 0.5 * lam * (tab[(2 * l + 1) % (4 * L)] + 1.0);
+        hs[l] = response(s, x);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int k = warp; k < L; k += nw) {
         double acc = 0.0;
-        for (int l = 1; l <= L; ++l) {
-            double th = kPi * ((double)l - 0.5) / (double)L;
-            double x = 0.5 * lam * (cos(th) + 1.0);
-            acc += cos((double)k * th) * response(s, x);
+        for (int l = lane; l < L; l += 32) {
+            const int m = (int)(((int64_t)k * (2 * l + 1)) % (4 * L));
+            acc += tab[m] * hs[l];
         }
-        c[k] = 2.0 / (double)L * acc;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) c[k] = 2.0 / (double)L * acc;
     }
 }
 
@@ -159,11 +176,11 @@ __device__ __forceinline__ void put_split(__nv_bfloat16 *hi, __nv_bfloat16 *lo, 
 }
 
 // A = (2/lambda) G - Id;  Z1 = A;  H = c0/2 Id + c1 A  (the initial sum of
-// Algorithm 1).  Optional BF16 hi/lo copies of A (tensor-core operand; Z1 is
-// the same matrix and reuses them).
+// Algorithm 1).  Tensor-core path: At = (2/lambda) G and Z1 as BF16 hi/lo.
 __global__ void shift_kernel(const float *__restrict__ G, int64_t ldg, int p, const double *lam,
                              const double *c, int L, float *A, float *Z1, float *H, int64_t ld,
-                             __nv_bfloat16 *Ahi, __nv_bfloat16 *Alo, int64_t ldb) {
+                             __nv_bfloat16 *Athi, __nv_bfloat16 *Atlo, __nv_bfloat16 *Z1hi, __nv_bfloat16 *Z1lo,
+                             int64_t ldb) {
     float s = (float)(2.0 / lam[0]);
     float c0h = (float)(0.5 * c[0]);
     float c1 = L > 1 ? (float)c[1] : 0.f;
@@ -171,11 +188,13 @@ __global__ void shift_kernel(const float *__restrict__ G, int64_t ldg, int p, co
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         int i = (int)(e / p), j = (int)(e % p);
-        float a = s * G[(int64_t)i * ldg + j] - (i == j ? 1.f : 0.f);
+        float at = s * G[(int64_t)i * ldg + j];
+        float a = at - (i == j ? 1.f : 0.f);
         if (A) A[(int64_t)i * ld + j] = a;
         if (Z1) Z1[(int64_t)i * ld + j] = a;
         H[(int64_t)i * ld + j] = c1 * a + (i == j ? c0h : 0.f);
-        if (Ahi) put_split(Ahi, Alo, (int64_t)i * ldb + j, a);
+        if (Athi) put_split(Athi, Atlo, (int64_t)i * ldb + j, at);
+        if (Z1hi) put_split(Z1hi, Z1lo, (int64_t)i * ldb + j, a);
     }
 }
 
@@ -202,6 +221,32 @@ __global__ void split_kernel(const float *__restrict__ X, int rows, int cols, in
     }
 }
 
+// hi/lo split of a symmetric matrix stored in its lower triangle (row >= col
+// valid): writes both triangles.  Block (bx, by) with by >= bx handles the
+// 32 x 32 tile (by, bx) and its transpose through shared memory.
+__global__ void split_sym_lower_kernel(const float *__restrict__ S, int p, int64_t lds, __nv_bfloat16 *hi,
+                                       __nv_bfloat16 *lo, int64_t ldo) {
+    __shared__ float t[32][33];
+    const int bx = blockIdx.x, by = blockIdx.y;
+    if (by < bx) return;
+    const int r0 = by * 32, c0 = bx * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    for (int k = ty; k < 32; k += 8) {
+        int r = r0 + k, c = c0 + tx;
+        // diagonal tile: take the lower element for both positions
+        float v = 0.f;
+        if (r < p && c < p) v = (r >= c) ? S[(int64_t)r * lds + c] : S[(int64_t)c * lds + r];
+        t[k][tx] = v;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        int r = r0 + k, c = c0 + tx;
+        if (r < p && c < p) put_split(hi, lo, (int64_t)r * ldo + c, t[k][tx]);
+        int rt = c0 + k, ct = r0 + tx;   // transposed tile
+        if (by != bx && rt < p && ct < p) put_split(hi, lo, (int64_t)rt * ldo + ct, t[tx][k]);
+    }
+}
+
 __global__ void check_finite_kernel(const float *X, int64_t rows, int64_t cols, int64_t ldx, int *flag) {
     int bad = 0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < rows * cols;
@@ -212,7 +257,164 @@ __global__ void check_finite_kernel(const float *X, int64_t rows, int64_t cols, 
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
 }
 
+// Software grid barrier for a cooperative launch: a monotone arrival
+// counter (zeroed before the launch); each block's thread 0 adds one and
+// waits for the count of the current round.  The wait is bounded (~2 s);
+// on expiry it records CPA_ERR_TIMEOUT in *err and lets the block go on.
+__device__ __forceinline__ void grid_barrier(unsigned int *count, unsigned int &target, int *err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        target += gridDim.x;
+        __threadfence();
+        atomicAdd(count, 1u);
+        const long long t0 = clock64();
+        while (true) {
+            unsigned int v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+            if (v >= target) break;
+            if (clock64() - t0 > 4000000000LL) {
+                atomicExch(err, (int)CPA_ERR_TIMEOUT);
+                break;
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// All power iterations in one cooperative launch.  Iteration t: w_{t+1} =
+// G (w_t / |w_t|), one warp per row, |w_{t+1}|^2 accumulated in FP64 by
+// atomics into norm2[t+1]; a grid barrier separates iterations.  Block 0
+// then forms theta, r, the trace and lambda as power_final_kernel does.
+__global__ void __launch_bounds__(512) power_persistent_kernel(const float *__restrict__ G, int64_t ldg, int p,
+                                                               int iters, uint64_t seed, float *v0, float *v1,
+                                                               double *norm2, unsigned int *bar, double margin,
+                                                               double *out, int *err) {
+    unsigned int target = 0;
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    // start vector and its norm (block 0), slots cleared
+    if (blockIdx.x == 0) {
+        double sacc = 0.0;
+        for (int i = threadIdx.x; i < p; i += blockDim.x) {
+            uint64_t z = splitmix64_output(seed, (uint64_t)i);
+            float x = (float)((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+            v0[i] = x;
+            sacc += (double)x * (double)x;
+        }
+        for (int i = threadIdx.x + 1; i < iters + 2; i += blockDim.x) norm2[i] = 0.0;
+        sacc = block_sum(sacc);
+        if (threadIdx.x == 0) norm2[0] = sacc;
+    }
+    grid_barrier(bar, target, err);
+    const bool vec = (ldg & 3) == 0 && (p & 3) == 0 && ((uintptr_t)G & 15) == 0;
+    for (int t = 0; t <= iters; ++t) {
+        const float *v = (t & 1) ? v1 : v0;
+        float *w = (t & 1) ? v0 : v1;
+        const double nin = __ldcg(&norm2[t]);   // written by other blocks: read at L2
+        const float scale = nin > 0.0 ? (float)(1.0 / sqrt(nin)) : 0.f;
+        double part = 0.0;
+        for (int row = gwarp; row < p; row += nwarps) {
+            const float *g = G + (int64_t)row * ldg;
+            float acc = 0.f;
+            if (vec) {
+                const float4 *g4 = reinterpret_cast<const float4 *>(g);
+                const float4 *v4 = reinterpret_cast<const float4 *>(v);
+                for (int j = lane; j < (p >> 2); j += 32) {
+                    float4 a = __ldg(g4 + j), b = __ldcg(v4 + j);
+                    acc = fmaf(a.x, b.x, acc); acc = fmaf(a.y, b.y, acc);
+                    acc = fmaf(a.z, b.z, acc); acc = fmaf(a.w, b.w, acc);
+                }
+            } else {
+                for (int j = lane; j < p; j += 32) acc = fmaf(__ldg(g + j), __ldcg(v + j), acc);
+            }
+            acc = warp_sumf(acc) * scale;
+            if (lane == 0) {
+                w[row] = acc;
+                part += (double)acc * (double)acc;
+            }
+        }
+        part = block_sum(part);
+        if (threadIdx.x == 0 && part != 0.0) atomicAdd(&norm2[t + 1], part);
+        grid_barrier(bar, target, err);
+    }
+    // after iters+1 products: v = buffer of step iters (unnormalised, norm2[iters]),
+    // w = G v / |v| in the other buffer
+    if (blockIdx.x != 0) return;
+    const float *vu = (iters & 1) ? v1 : v0;
+    const float *w = (iters & 1) ? v0 : v1;
+    const double n = __ldcg(&norm2[iters]);
+    const double sc = n > 0.0 ? 1.0 / sqrt(n) : 0.0;
+    double th = 0.0, tr = 0.0;
+    int nonfinite = 0;
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+        th += (double)__ldcg(vu + i) * sc * (double)__ldcg(w + i);
+        double gii = (double)G[(int64_t)i * ldg + i];
+        tr += gii;
+        if (!isfinite(gii)) nonfinite = 1;
+    }
+    th = block_sum(th);
+    __shared__ double sh_th;
+    if (threadIdx.x == 0) sh_th = th;
+    __syncthreads();
+    th = sh_th;
+    double r2 = 0.0;
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+        double d = (double)__ldcg(w + i) - th * (double)__ldcg(vu + i) * sc;
+        r2 += d * d;
+    }
+    r2 = block_sum(r2);
+    tr = block_sum(tr);
+    nonfinite = __syncthreads_or(nonfinite);
+    if (threadIdx.x == 0) {
+        double r = sqrt(r2);
+        double lam = (th + r) * (1.0 + margin);
+        if (lam > tr) lam = tr;
+        double flag = 0.0;
+        if (nonfinite || !isfinite(lam) || !isfinite(tr)) {
+            flag = (double)CPA_ERR_NONFINITE;
+        } else if (!(lam > 0.0)) {
+            lam = tr > 0.0 ? tr : 1.0;
+        }
+        const int e2 = __ldcg(err);
+        if (e2) flag = (double)e2;
+        out[0] = th;
+        out[1] = r;
+        out[2] = tr;
+        out[3] = lam;
+        out[4] = flag;
+    }
+}
+
 }  // namespace
+
+cudaError_t power_bound_persistent(const float *G, int64_t ldg, int p, int iters, float *v0, float *v1,
+                                   double *norm2, unsigned int *bar, int *err, double *out, cudaStream_t st,
+                                   int num_sms) {
+    cudaError_t r = cudaMemsetAsync(bar, 0, sizeof(unsigned int), st);
+    if (r != cudaSuccess) return r;
+    r = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (r != cudaSuccess) return r;
+    int grid = num_sms;
+    const int rows_per_block = 16;   // warps per block
+    if (grid > (p + rows_per_block - 1) / rows_per_block) grid = (p + rows_per_block - 1) / rows_per_block;
+    if (grid < 1) grid = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(512);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const double margin = kLambdaMargin;
+    const uint64_t seed = kStartSeed;
+    return cudaLaunchKernelEx(&cfg, power_persistent_kernel, G, ldg, p, iters, seed, v0, v1, norm2, bar, margin, out,
+                              err);
+}
 
 cudaError_t power_bound(const float *G, int64_t ldg, int p, int iters, float *v0, float *v1,
                         double *norm2, double *out, cudaStream_t st) {
@@ -235,18 +437,25 @@ cudaError_t power_bound(const float *G, int64_t ldg, int p, int iters, float *v0
 
 cudaError_t device_coeffs(const double *lam_dev, double lam_host, int L, const ShrinkParams &s, double *c,
                           cudaStream_t st) {
-    int threads = L < 1024 ? ((L + 31) / 32) * 32 : 1024;
-    coeffs_kernel<<<1, threads, 0, st>>>(lam_dev, lam_host, L, s, c);
+    const size_t smem = (size_t)5 * L * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t r = cudaFuncSetAttribute(coeffs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             5 * kMaxTerms * (int)sizeof(double));
+        if (r != cudaSuccess) return r;
+        attr = true;
+    }
+    coeffs_kernel<<<1, 1024, smem, st>>>(lam_dev, lam_host, L, s, c);
     return cudaGetLastError();
 }
 
 cudaError_t shift_init(const float *G, int64_t ldg, int p, const double *lam, const double *c, int L, float *A,
-                       float *Z1, float *H, int64_t ld, __nv_bfloat16 *Ahi, __nv_bfloat16 *Alo, int64_t ldb,
-                       cudaStream_t st, int num_sms) {
+                       float *Z1, float *H, int64_t ld, __nv_bfloat16 *Athi, __nv_bfloat16 *Atlo,
+                       __nv_bfloat16 *Z1hi, __nv_bfloat16 *Z1lo, int64_t ldb, cudaStream_t st, int num_sms) {
     int64_t total = (int64_t)p * p;
     int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 8);
     if (blocks < 1) blocks = 1;
-    shift_kernel<<<blocks, 256, 0, st>>>(G, ldg, p, lam, c, L, A, Z1, H, ld, Ahi, Alo, ldb);
+    shift_kernel<<<blocks, 256, 0, st>>>(G, ldg, p, lam, c, L, A, Z1, H, ld, Athi, Atlo, Z1hi, Z1lo, ldb);
     return cudaGetLastError();
 }
 
@@ -254,6 +463,13 @@ cudaError_t split_bf16(const float *X, int rows, int cols, int64_t ldx, bool tra
                        __nv_bfloat16 *lo, int64_t ldo, cudaStream_t st) {
     dim3 grid((cols + 31) / 32, (rows + 31) / 32);
     split_kernel<<<grid, dim3(32, 8), 0, st>>>(X, rows, cols, ldx, transpose ? 1 : 0, hi, lo, ldo);
+    return cudaGetLastError();
+}
+
+cudaError_t split_sym_lower(const float *S, int p, int64_t lds, __nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t ldo,
+                            cudaStream_t st) {
+    dim3 grid((p + 31) / 32, (p + 31) / 32);
+    split_sym_lower_kernel<<<grid, dim3(32, 8), 0, st>>>(S, p, lds, hi, lo, ldo);
     return cudaGetLastError();
 }
 
