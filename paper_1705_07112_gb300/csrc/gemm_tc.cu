@@ -28,6 +28,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 
 #include "internal.h"
@@ -135,17 +136,44 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(map),
+                 "r"(su32(src)), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Operand maps of the main loop and the 32 x 32 block maps of the epilogue
+// (FP32 C, C2, H, D and BF16 hi/lo copies of D).
 struct TileMaps {
     CUtensorMap a_hi, a_lo, b_hi, b_lo;
+    CUtensorMap c, c2, h, d, dhi, dlo;
+};
+
+// Shared memory of one epilogue warp: three FP32 32 x 32 blocks (C -> D in
+// place, C2, H in place), two BF16 32 x 32 blocks (hi/lo copies of D at the
+// mirrored position) and a padded 32 x 33 word transpose buffer.
+struct EpiSmem {
+    float c[32 * 32];
+    float c2[32 * 32];
+    float h[32 * 32];
+    __nv_bfloat16 hi[32 * 32];
+    __nv_bfloat16 lo[32 * 32];
+    uint32_t t[32 * 33];
+    uint32_t pad[32 - (32 * 33) % 32];
 };
 
 template <int BN>
 struct Smem {
     static constexpr int kStageA = BM * BK * 2;
     static constexpr int kStageB = BN * BK * 2;
-    static constexpr int kStages = (BN == 256) ? 4 : (BN == 128 ? 6 : 8);
+    static constexpr int kStages = (BN == 256) ? 3 : (BN == 128 ? 4 : 6);
     static constexpr int kBytes =
-        kStages * (kStageA + kStageB) + 4 * 32 * 33 * 4 /* transpose */ + 1024 /* align */ + 256 /* barriers */;
+        kStages * (kStageA + kStageB) + 4 * (int)sizeof(EpiSmem) + 1024 /* align */ + 256 /* barriers */;
 };
 
 // ------------------------------------------------------------------ epilogue
@@ -156,71 +184,152 @@ __device__ __forceinline__ uint32_t pack_hilo(float v) {
     return (uint32_t)__bfloat16_as_ushort(hi) | ((uint32_t)__bfloat16_as_ushort(lo) << 16);
 }
 
-// One 32 x 32 block of the accumulator held by a warp: lane l owns row
-// i = r0 + l, acc[c] is column j = j0 + c.  tbuf: 32 x 33 words of shared
-// memory private to the warp.
-__device__ __forceinline__ void epilogue_block(const Epilogue &e, float ck, int M, int N, int r0, int j0, int lane,
-                                               const float *acc, uint32_t *tbuf) {
-    const bool sym = e.symmetric_upper != 0;
+// Writes the 32 x 32 block held in the transpose buffer (word [r][c] is
+// element (r0 + r, j0 + c)) to row-major global memory with coalesced
+// stores; `upper` keeps only c0 + c > r0 + r.  mode 0: FP32 to D,
+// mode 1: BF16 hi (low half) / lo (high half) to Dhi / Dlo.
+__device__ __forceinline__ void store_transposed(const Epilogue &e, const uint32_t *t, int mode, int M, int N, int r0,
+                                                 int j0, int lane, bool upper) {
+    const int jj = j0 + lane;
+    if (jj >= N) return;
+#pragma unroll 8
+    for (int rr = 0; rr < 32; ++rr) {
+        const int ii = r0 + rr;
+        if (ii >= M || (upper && jj <= ii)) continue;
+        const uint32_t val = t[rr * 33 + lane];
+        if (mode == 0) {
+            e.D[(int64_t)ii * e.ldd + jj] = __uint_as_float(val);
+        } else {
+            e.Dhi[(int64_t)ii * e.ldb + jj] = __ushort_as_bfloat16((unsigned short)(val & 0xFFFF));
+            if (e.Dlo) e.Dlo[(int64_t)ii * e.ldb + jj] = __ushort_as_bfloat16((unsigned short)(val >> 16));
+        }
+    }
+}
+
+// Symmetric output, one 32 x 32 block of the accumulator held by a warp:
+// lane l owns row i = r0 + l, acc[c] is column j = j0 + c, j0 >= r0.
+// The FP32 arrays live in the lower triangle, so the block is handled at
+// its mirrored position (rows j0.., columns r0..), moved by TMA:
+//   loads C, C2, H -> es.c, es.c2, es.h  ([j - j0][i - r0]),
+//   v = s_acc acc + s_c C + s_c2 C2 + diag,  es.c = v,  es.h += c_k v,
+//   es.hi/lo = BF16 parts of v,  TMA stores of D, H, Dhi, Dlo;
+// the BF16 parts for the upper positions (i, j) go out through the
+// transpose buffer.  A diagonal block (j0 == r0) is written in full at its
+// own position, each pair (i,j), (j,i) taking the value of the upper
+// element.  Only lane 0 issues TMA operations.
+__device__ __forceinline__ void epilogue_sym_block(const Epilogue &e, const TileMaps &maps, float ck, int M, int N,
+                                                   int r0, int j0, int lane, const float *acc, EpiSmem &es,
+                                                   uint64_t *bar, uint32_t &phase, volatile int *abort_flag) {
+    const bool diag = (j0 == r0);
+    const bool any_load = e.C || e.C2 || e.H;
+    // previous block's TMA stores must have finished reading shared memory
+    fence_proxy_async();
+    __syncwarp();
+    if (lane == 0) {
+        bulk_wait_read_all();
+        if (any_load) {
+            const uint32_t bytes = 4096u * ((e.C ? 1u : 0u) + (e.C2 ? 1u : 0u) + (e.H ? 1u : 0u));
+            mbar_expect_tx(bar, bytes);
+            if (e.C) tma_load_2d(es.c, &maps.c, bar, r0, j0);
+            if (e.C2) tma_load_2d(es.c2, &maps.c2, bar, r0, j0);
+            if (e.H) tma_load_2d(es.h, &maps.h, bar, r0, j0);
+        }
+    }
+    __syncwarp();
+    if (any_load) {
+        mbar_wait(bar, phase, abort_flag);
+        phase ^= 1u;
+    }
     const int i = r0 + lane;
-    uint32_t vbits[32];
     uint32_t hl[32];
+    if (!diag) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            float v = e.s_acc * acc[c];
+            if (e.C) v = fmaf(e.s_c, es.c[c * 32 + lane], v);
+            if (e.C2) v = fmaf(e.s_c2, es.c2[c * 32 + lane], v);
+            es.c[c * 32 + lane] = v;
+            if (e.H) es.h[c * 32 + lane] = fmaf(ck, v, es.h[c * 32 + lane]);
+            const uint32_t p = pack_hilo(v);
+            hl[c] = p;
+            es.hi[c * 32 + lane] = __ushort_as_bfloat16((unsigned short)(p & 0xFFFF));
+            es.lo[c * 32 + lane] = __ushort_as_bfloat16((unsigned short)(p >> 16));
+        }
+    } else {
+        // read every input first: the stores below touch both triangles
+        float cv[32], c2v[32], hv[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            const int a = c >= lane ? c * 32 + lane : lane * 32 + c;   // lower-triangle copy
+            cv[c] = e.C ? es.c[a] : 0.f;
+            c2v[c] = e.C2 ? es.c2[a] : 0.f;
+            hv[c] = e.H ? es.h[a] : 0.f;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            if (c < lane) continue;   // the pair is written by lane c
+            float v = fmaf(e.s_c2, c2v[c], fmaf(e.s_c, cv[c], e.s_acc * acc[c]));
+            if (c == lane) v += e.diag;
+            const float hn = fmaf(ck, v, hv[c]);
+            const uint32_t p = pack_hilo(v);
+            const __nv_bfloat16 bh = __ushort_as_bfloat16((unsigned short)(p & 0xFFFF));
+            const __nv_bfloat16 bl = __ushort_as_bfloat16((unsigned short)(p >> 16));
+            es.c[c * 32 + lane] = v;
+            es.c[lane * 32 + c] = v;
+            if (e.H) {
+                es.h[c * 32 + lane] = hn;
+                es.h[lane * 32 + c] = hn;
+            }
+            es.hi[c * 32 + lane] = bh;
+            es.hi[lane * 32 + c] = bh;
+            es.lo[c * 32 + lane] = bl;
+            es.lo[lane * 32 + c] = bl;
+        }
+    }
+    (void)i;
+    fence_proxy_async();
+    __syncwarp();
+    if (lane == 0) {
+        tma_store_2d(&maps.d, es.c, r0, j0);
+        if (e.H) tma_store_2d(&maps.h, es.h, r0, j0);
+        if (e.Dhi) {
+            tma_store_2d(&maps.dhi, es.hi, r0, j0);
+            if (e.Dlo) tma_store_2d(&maps.dlo, es.lo, r0, j0);
+        }
+        bulk_commit();
+    }
+    if (diag) return;
+    // upper positions (i, j): the transposed values of the mirrored block
+    if (e.sym_full_d) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) es.t[lane * 33 + c] = __float_as_uint(es.c[c * 32 + lane]);
+        __syncwarp();
+        store_transposed(e, es.t, 0, M, N, r0, j0, lane, false);
+        __syncwarp();
+    }
+    if (e.Dhi) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) es.t[lane * 33 + c] = hl[c];
+        __syncwarp();
+        store_transposed(e, es.t, 1, M, N, r0, j0, lane, false);
+        __syncwarp();
+    }
+}
+
+// General (non-symmetric) output: D(i,j) = s_acc acc + diag, stored through
+// the transpose buffer.
+__device__ __forceinline__ void epilogue_general_block(const Epilogue &e, int M, int N, int r0, int j0, int lane,
+                                                       const float *acc, EpiSmem &es) {
+    const int i = r0 + lane;
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
-        const int j = j0 + c;
         float v = e.s_acc * acc[c];
-        hl[c] = 0u;
-        if (sym) {
-            const bool ok = (i < M) && (j < N) && (j >= i);
-            if (ok) {
-                // mirrored position (j,i): lanes touch consecutive addresses
-                if (e.C) v = fmaf(e.s_c, e.C[(int64_t)j * e.ldc + i], v);
-                if (e.C2) v = fmaf(e.s_c2, e.C2[(int64_t)j * e.ldc2 + i], v);
-                if (i == j) v += e.diag;
-                e.D[(int64_t)j * e.ldd + i] = v;
-                if (e.H) {
-                    float *hp = e.H + (int64_t)j * e.ldh + i;
-                    *hp = fmaf(ck, v, *hp);
-                }
-                if (e.Dhi) {
-                    uint32_t p = pack_hilo(v);
-                    hl[c] = p;
-                    e.Dhi[(int64_t)j * e.ldb + i] = __ushort_as_bfloat16((unsigned short)(p & 0xFFFF));
-                    if (e.Dlo) e.Dlo[(int64_t)j * e.ldb + i] = __ushort_as_bfloat16((unsigned short)(p >> 16));
-                }
-            }
-        } else if (i == j) {
-            v += e.diag;
-        }
-        vbits[c] = __float_as_uint(v);
+        if (i == j0 + c) v += e.diag;
+        es.t[lane * 33 + c] = __float_as_uint(v);
     }
-    // (i,j) positions through the transpose: pass 0 the FP32 D (general
-    // outputs, or symmetric ones kept in full), pass 1 the BF16 hi/lo copies
-    const bool pass0 = !sym || e.sym_full_d;
-    const bool pass1 = sym && e.Dhi != nullptr;
-#pragma unroll
-    for (int pass = 0; pass < 2; ++pass) {
-        if (pass == 0 && !pass0) continue;
-        if (pass == 1 && !pass1) continue;
-        __syncwarp();
-#pragma unroll
-        for (int c = 0; c < 32; ++c) tbuf[lane * 33 + c] = pass == 0 ? vbits[c] : hl[c];
-        __syncwarp();
-        const int jj = j0 + lane;
-#pragma unroll 4
-        for (int rr = 0; rr < 32; ++rr) {
-            const int ii = r0 + rr;
-            const bool ok = ii < M && jj < N && (!sym || jj > ii);
-            if (!ok) continue;
-            const uint32_t val = tbuf[rr * 33 + lane];
-            if (pass == 0) {
-                e.D[(int64_t)ii * e.ldd + jj] = __uint_as_float(val);
-            } else {
-                e.Dhi[(int64_t)ii * e.ldb + jj] = __ushort_as_bfloat16((unsigned short)(val & 0xFFFF));
-                if (e.Dlo) e.Dlo[(int64_t)ii * e.ldb + jj] = __ushort_as_bfloat16((unsigned short)(val >> 16));
-            }
-        }
-    }
+    __syncwarp();
+    store_transposed(e, es.t, 0, M, N, r0, j0, lane, false);
     __syncwarp();
 }
 
@@ -267,13 +376,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = smem;
     uint8_t *sB = smem + kStages * S::kStageA;
-    uint32_t *tbuf_all = reinterpret_cast<uint32_t *>(sB + kStages * S::kStageB);   // 4 x 32 x 33 words
-    uint64_t *bars = reinterpret_cast<uint64_t *>(tbuf_all + 4 * 32 * 33);
+    EpiSmem *epi = reinterpret_cast<EpiSmem *>(sB + kStages * S::kStageB);   // [4]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(epi + 4);
     uint64_t *full = bars;                 // [kStages]
     uint64_t *empty = bars + kStages;      // [kStages]
     uint64_t *tfull = bars + 2 * kStages;  // [2]
     uint64_t *tempty = tfull + 2;          // [2]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+    uint64_t *ebar = tempty + 2;           // [4] epilogue TMA loads
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ebar + 4);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -292,6 +402,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], 4);
         }
+        for (int q = 0; q < 4; ++q) mbar_init(&ebar[q], 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -383,7 +494,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // ------------------------------------------------------------ epilogue
         const int quarter = warp & 3;   // TMEM lanes 32*quarter .. +31
-        uint32_t *tbuf = tbuf_all + quarter * (32 * 33);
+        EpiSmem &es = epi[quarter];
+        uint64_t *bar = &ebar[quarter];
+        uint32_t ephase = 0;
         const float ck = e.H ? (float)e.coef[e.k] : 0.f;
         uint32_t tphase[2] = {0, 0};
         int local = 0;
@@ -402,13 +515,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tmem_ld32(trow + (uint32_t)(c * 32), acc);
                 const int j0 = n0 + c * 32;
                 if (r0 >= M || j0 >= N) continue;
-                if (sym && j0 + 31 < r0) continue;   // block entirely below the diagonal
-                epilogue_block(e, ck, M, N, r0, j0, lane, acc, tbuf);
+                if (sym) {
+                    if (j0 < r0) continue;   // block below the diagonal: written as another block's mirror
+                    epilogue_sym_block(e, maps, ck, M, N, r0, j0, lane, acc, es, bar, ephase, abort_flag);
+                } else {
+                    epilogue_general_block(e, M, N, r0, j0, lane, acc, es);
+                }
             }
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[buf]);
         }
+        // the last TMA stores must complete before the CTA exits
+        if (lane == 0) bulk_wait_all();
+        __syncwarp();
     }
 
     fence_before();
@@ -420,6 +540,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (threadIdx.x == 0 && *abort_flag) atomicExch(err, CPA_ERR_TIMEOUT);
 }
+
 // ------------------------------------------------------------------- host side
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -437,6 +558,7 @@ bool load_encode() {
     return g_encode != nullptr;
 }
 
+// Operand map: BF16 rows of K elements, 128-byte swizzled K slices.
 bool make_map(CUtensorMap *map, const __nv_bfloat16 *ptr, int64_t ld, int rows, int K, int box_rows) {
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
@@ -445,6 +567,19 @@ bool make_map(CUtensorMap *map, const __nv_bfloat16 *ptr, int64_t ld, int rows, 
     CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)ptr, dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// Epilogue block map: 32 x 32 elements of a rows x cols row-major array.
+bool make_block_map(CUtensorMap *map, const void *ptr, CUtensorMapDataType type, int esize, int64_t ld, int rows,
+                    int cols) {
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * esize)};
+    cuuint32_t box[2] = {32, 32};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, type, 2, (void *)ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
@@ -462,10 +597,21 @@ cudaError_t launch(int M, int N, int K, const TcOperand &A, const TcOperand &B, 
         attr_set = true;
     }
     TileMaps maps;
+    memset(&maps, 0, sizeof(maps));
     const __nv_bfloat16 *alo = A.lo ? A.lo : A.hi, *blo = B.lo ? B.lo : B.hi;
     if (!make_map(&maps.a_hi, A.hi, A.ld, A.rows, K, BM) || !make_map(&maps.a_lo, alo, A.ld, A.rows, K, BM) ||
         !make_map(&maps.b_hi, B.hi, B.ld, B.rows, K, BN) || !make_map(&maps.b_lo, blo, B.ld, B.rows, K, BN))
         return cudaErrorInvalidValue;
+    if (e.symmetric_upper) {
+        const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32, b16 = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+        bool ok = make_block_map(&maps.d, e.D, f32, 4, e.ldd, M, N);
+        if (e.C) ok = ok && make_block_map(&maps.c, e.C, f32, 4, e.ldc, M, N);
+        if (e.C2) ok = ok && make_block_map(&maps.c2, e.C2, f32, 4, e.ldc2, M, N);
+        if (e.H) ok = ok && make_block_map(&maps.h, e.H, f32, 4, e.ldh, M, N);
+        if (e.Dhi) ok = ok && make_block_map(&maps.dhi, e.Dhi, b16, 2, e.ldb, M, N);
+        if (e.Dlo) ok = ok && make_block_map(&maps.dlo, e.Dlo, b16, 2, e.ldb, M, N);
+        if (!ok) return cudaErrorInvalidValue;
+    }
     const int tiles = count_tiles((M + BM - 1) / BM, (N + BN - 1) / BN, e.symmetric_upper, BN);
     const int grid = tiles < num_sms ? tiles : num_sms;
     gemm_tc_kernel<BN><<<grid, kThreads, S::kBytes, st>>>(maps, M, N, K, nsplit, e, g_err_dev);
@@ -491,9 +637,18 @@ cudaError_t gemm_tc(int M, int N, int K, const TcOperand &A, const TcOperand &B,
     if (!load_encode()) return cudaErrorNotSupported;
     if ((A.ld % 8) || (B.ld % 8) || ((uintptr_t)A.hi % 16) || ((uintptr_t)B.hi % 16)) return cudaErrorInvalidValue;
     if (nsplit == 3 && (!A.lo || !B.lo)) return cudaErrorInvalidValue;
-    if (e.symmetric_upper && M != N) return cudaErrorInvalidValue;
-    // general outputs carry only D
-    if (!e.symmetric_upper && (e.C || e.C2 || e.H || e.Dhi || e.Dlo)) return cudaErrorInvalidValue;
+    if (e.symmetric_upper) {
+        // the epilogue block maps need 16-byte aligned rows and bases
+        if (M != N) return cudaErrorInvalidValue;
+        if ((e.ldd % 4) || (e.C && e.ldc % 4) || (e.C2 && e.ldc2 % 4) || (e.H && e.ldh % 4) ||
+            (e.Dhi && e.ldb % 8) || ((uintptr_t)e.D % 16) || ((uintptr_t)e.C % 16) || ((uintptr_t)e.C2 % 16) ||
+            ((uintptr_t)e.H % 16) || ((uintptr_t)e.Dhi % 16) || ((uintptr_t)e.Dlo % 16))
+            return cudaErrorInvalidValue;
+        // C, when given, is updated in place (D == C)
+        if (e.C && (e.C != e.D || e.ldc != e.ldd)) return cudaErrorInvalidValue;
+    } else if (e.C || e.C2 || e.H || e.Dhi || e.Dlo) {
+        return cudaErrorInvalidValue;   // general outputs carry only D
+    }
     int *flag;
     cudaError_t r = gemm_tc_error_flag(&flag);
     if (r != cudaSuccess) return r;

@@ -321,10 +321,21 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
             if (vec) {
                 const float4 *g4 = reinterpret_cast<const float4 *>(g);
                 const float4 *v4 = reinterpret_cast<const float4 *>(v);
-                for (int j = lane; j < (p >> 2); j += 32) {
-                    float4 a = __ldg(g4 + j), b = __ldcg(v4 + j);
-                    acc = fmaf(a.x, b.x, acc); acc = fmaf(a.y, b.y, acc);
-                    acc = fmaf(a.z, b.z, acc); acc = fmaf(a.w, b.w, acc);
+                const int n4 = p >> 2;
+                // sixteen independent float4 pairs in flight per lane
+                for (int j0 = lane; j0 < n4; j0 += 32 * 16) {
+                    float4 a[16], b[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int j = j0 + 32 * u;
+                        a[u] = j < n4 ? __ldg(g4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        b[u] = j < n4 ? __ldcg(v4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        acc = fmaf(a[u].x, b[u].x, acc); acc = fmaf(a[u].y, b[u].y, acc);
+                        acc = fmaf(a[u].z, b[u].z, acc); acc = fmaf(a[u].w, b[u].w, acc);
+                    }
                 }
             } else {
                 for (int j = lane; j < p; j += 32) acc = fmaf(__ldg(g + j), __ldcg(v + j), acc);

@@ -101,14 +101,22 @@ def test_svt_kinds_single_lowrank(cpa, handle, kind, prec):
 
 
 def test_lambda_bound_matches_oracle(cpa, handle):
-    for shape in [(256, 256), (300, 170), (170, 300), (1, 5), (64, 40)]:
-        rng = np.random.default_rng(shape[0] + 31 * shape[1])
-        X32 = rng.standard_normal(shape).astype(np.float32)
-        X64 = X32.astype(np.float64)
-        ref = O.lambda_bound(X64, 20, 0.01, O.start_vector(SEED, min(shape)))
-        got = cpa.cpa_lambda_bound(handle, to_dev(X32), 20)
-        assert abs(got - ref["lam"]) <= 1e-4 * ref["lam"], (shape, got, ref)
-        assert got >= np.linalg.norm(X64, 2) ** 2 * (1 - 1e-6)
+    # pure noise (no spectral gap at the top) and low rank + noise; the
+    # bound must equal the oracle's; it is an upper bound of sigma_max^2
+    # only where the power iteration has converged (a gap at the top)
+    for shape in [(256, 256), (300, 170), (170, 300), (1, 5), (64, 40), (2048, 1500)]:
+        for lowrank in (False, True):
+            rng = np.random.default_rng(shape[0] + 31 * shape[1])
+            X64 = rng.standard_normal(shape)
+            if lowrank:
+                X64 = 3.0 * rng.standard_normal((shape[0], 3)) @ rng.standard_normal((3, shape[1])) + 0.1 * X64
+            X32 = X64.astype(np.float32)
+            X64 = X32.astype(np.float64)
+            ref = O.lambda_bound(X64, 20, 0.01, O.start_vector(SEED, min(shape)))
+            got = cpa.cpa_lambda_bound(handle, to_dev(X32), 20)
+            assert abs(got - ref["lam"]) <= 1e-4 * ref["lam"], (shape, got, ref)
+            if lowrank or min(shape) == 1:
+                assert got >= np.linalg.norm(X64, 2) ** 2 * (1 - 1e-6)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
