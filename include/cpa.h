@@ -218,7 +218,8 @@ CPA_API cpa_status cpa_kernel_split_bf16(const float *X, int rows, int cols, int
  *
  * A plan uploads the descriptor table once (shapes, offsets, per-matrix L);
  * the same plan can be run many times on new data, and a run can be captured
- * in a CUDA graph.  Supported shapes: 1 <= min(m,n) <= 128, max(m,n) <= 4096.
+ * in a CUDA graph.  Supported shapes: 1 <= min(m,n) <= 64, max(m,n) <= 128,
+ * 1 <= L <= 128 (patch groups; larger matrices go through cpa_svt).
  * ------------------------------------------------------------------------- */
 typedef struct cpa_batch_ctx *cpa_batch;
 
@@ -233,8 +234,13 @@ CPA_API cpa_status cpa_batch_destroy(cpa_batch b);
  *   lambda: NULL to compute each bound on the device (power iteration with
  *      `iters` steps, definition of cpa_lambda_bound), or a DEVICE array of
  *      count doubles.
- *   prec: CPA_FP32 or CPA_BF16X3 (split BF16, FP32 accumulate) or CPA_BF16.
- * Asynchronous on `stream`. */
+ *   prec: CPA_FP32 (FP32 FMA) or CPA_BF16 / CPA_BF16X3 (tensor cores with the
+ *      BF16 hi/lo split in every product: at these sizes the single-BF16
+ *      recurrence would cost accuracy and save nothing).
+ * Asynchronous on `stream`.  The shrink parameters are uploaded on the first
+ * run of a plan and whenever they change: such a run synchronises `stream`
+ * first and cannot be captured in a CUDA graph; runs with unchanged
+ * parameters only launch the kernel (capturable). */
 CPA_API cpa_status cpa_svt_batched(cpa_handle h, cpa_batch b, const float *dX, const cpa_shrink *s,
                            int s_count, const double *lambda, int iters, int prec, float *dY,
                            void *stream);
@@ -242,6 +248,10 @@ CPA_API cpa_status cpa_svt_batched(cpa_handle h, cpa_batch b, const float *dX, c
 /* Per-matrix Lambda_max used by the last run of the plan (device array of
  * count doubles owned by the plan; valid until cpa_batch_destroy). */
 CPA_API const double *cpa_batch_lambdas(cpa_batch b);
+
+/* Copies those count values to host memory (synchronises `stream`); also
+ * returns CPA_ERR_NONFINITE if a computed bound met a NaN/Inf. */
+CPA_API cpa_status cpa_batch_read_lambdas(cpa_batch b, double *host_out, void *stream);
 
 #ifdef __cplusplus
 }

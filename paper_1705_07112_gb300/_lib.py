@@ -23,7 +23,7 @@ PREC = {"fp32": FP32, "tf32": TF32, "bf16": BF16, "bf16x3": BF16X3}
 EXPORTS = ["cpa_create", "cpa_destroy", "cpa_status_string", "cpa_last_error", "cpa_coeffs",
            "cpa_lambda_bound", "cpa_svt", "cpa_get_lambda", "cpa_get_coeffs", "cpa_batch_create",
            "cpa_batch_destroy", "cpa_svt_batched", "cpa_batch_lambdas", "cpa_profile_enable",
-           "cpa_profile_read", "cpa_kernel_gemm_bf16", "cpa_kernel_split_bf16"]
+           "cpa_profile_read", "cpa_kernel_gemm_bf16", "cpa_kernel_split_bf16", "cpa_batch_read_lambdas"]
 STAGES = ["prep", "gram", "bound", "coeff", "shift", "recur", "apply"]
 
 
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
             "cpa_svt_batched": (ctypes.c_int, [_vp, _vp, _vp, _P(CpaShrink), ctypes.c_int, _vp, ctypes.c_int,
                                                ctypes.c_int, _vp, _vp]),
             "cpa_batch_lambdas": (_vp, [_vp]),
+            "cpa_batch_read_lambdas": (ctypes.c_int, [_vp, _P(_d), _vp]),
             "cpa_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
             "cpa_kernel_gemm_bf16": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _i64, _vp,
                                                     _vp, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_float, _vp,
@@ -248,3 +249,67 @@ def kernel_split_bf16(X, transpose, hi, lo, stream=None):
     rows, cols = X.shape
     _check(load().cpa_kernel_split_bf16(_ptr(X), rows, cols, X.stride(0), 1 if transpose else 0, _ptr(hi),
                                         _ptr(lo), hi.stride(0), _stream_ptr(stream)), "cpa_kernel_split_bf16")
+
+
+class BatchPlan:
+    """cpa_batch: shapes, offsets and term counts of a packed batch."""
+
+    def __init__(self, h: Handle, shapes, offsets=None, L=None, L0: int = 24):
+        self._lib = load()
+        shapes = [(int(a), int(b)) for a, b in shapes]
+        self.count = len(shapes)
+        if offsets is None:
+            offsets, o = [], 0
+            for a, b in shapes:
+                offsets.append(o)
+                o += a * b
+        self.shapes, self.offsets = shapes, list(offsets)
+        self.total = max(o + a * b for (a, b), o in zip(shapes, self.offsets))
+        off = (ctypes.c_int64 * self.count)(*self.offsets)
+        ms = (ctypes.c_int32 * self.count)(*[a for a, _ in shapes])
+        ns = (ctypes.c_int32 * self.count)(*[b for _, b in shapes])
+        Ls = (ctypes.c_int32 * self.count)(*L) if L is not None else None
+        ptr = ctypes.c_void_p()
+        _check(self._lib.cpa_batch_create(h.ptr, self.count, off, ms, ns, Ls, int(L0), ctypes.byref(ptr)),
+               "cpa_batch_create")
+        self.ptr = ptr
+
+    def close(self):
+        if self.ptr:
+            self._lib.cpa_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def lambdas(self, stream=None) -> np.ndarray:
+        out = np.zeros(self.count, dtype=np.float64)
+        _check(self._lib.cpa_batch_read_lambdas(self.ptr, out.ctypes.data_as(_P(_d)), _stream_ptr(stream)),
+               "cpa_batch_read_lambdas")
+        return out
+
+
+def cpa_svt_batched(h: Handle, plan: BatchPlan, X, shrink, lambdas=None, iters: int = 20, prec="bf16x3", Y=None,
+                    stream=None):
+    """Batched shrinkage of the packed matrices in X (flat float32 CUDA
+    tensor); shrink: one spec or a list with one per matrix; lambdas: None
+    (computed on the device) or a float64 CUDA tensor of plan.count bounds."""
+    import torch
+    if not (X.is_cuda and X.dtype == torch.float32 and X.is_contiguous() and X.numel() >= plan.total):
+        raise ValueError("X must be a contiguous float32 CUDA tensor covering the plan")
+    if Y is None:
+        Y = torch.empty_like(X)
+    specs = shrink if isinstance(shrink, (list, tuple)) else [shrink]
+    arr = (CpaShrink * len(specs))(*[_as_shrink(x) for x in specs])
+    lam = None
+    if lambdas is not None:
+        if not (lambdas.is_cuda and lambdas.dtype == torch.float64 and lambdas.numel() == plan.count):
+            raise ValueError("lambdas must be a float64 CUDA tensor of plan.count values")
+        lam = ctypes.c_void_p(lambdas.data_ptr())
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    _check(load().cpa_svt_batched(h.ptr, plan.ptr, ctypes.c_void_p(X.data_ptr()), arr, len(specs), lam, int(iters),
+                                  p, ctypes.c_void_p(Y.data_ptr()), _stream_ptr(stream)), "cpa_svt_batched")
+    return Y

@@ -1,34 +1,639 @@
-// Batched shrinkage of many small matrices (patch groups).
+// Batched CPA shrinkage of many small matrices (patch groups), one
+// persistent launch.
+//
+// One CTA of 128 threads (4 warps) owns one matrix at a time and walks a
+// size-sorted work list.  With p = min(m, n) <= 64 and q = max(m, n) <= 128
+// everything stays on chip:
+//   shared memory  X as BF16 hi/lo (or FP32), At = (2/lambda) G as BF16 hi/lo
+//                  (the constant operand), Psi_{k-1} as BF16 hi/lo (double
+//                  buffered), G in FP32 for the power iteration;
+//   registers      the accumulator and Psi_{k-1}, Psi_{k-2}, H in the MMA
+//                  accumulator layout: warp w owns rows 16w..16w+15, each
+//                  thread the same 32 elements at every step, so the
+//                  recurrence  Psi_k = 2 At Psi_{k-1} - 2 Psi_{k-1} - Psi_{k-2},
+//                  H += c_k Psi_k  never leaves the registers.
+// Products (Gram, recurrence, final product) use warp-level BF16 tensor-core
+// MMA (m16n8k16, FP32 accumulate) with the hi/lo split hi*hi + hi*lo + lo*hi,
+// or FP32 FMA in the plain-FP32 variant.  The 64 x 64 products of this
+// workload are too small for a 128-row tcgen05 tile to pay for its TMEM round
+// trips; the path is bound by the per-element recurrence arithmetic.
+//
+// The recurrence multiplies At by Psi_{k-1} exactly as stored (B operand
+// loaded with a transposing ldmatrix from row-major Psi), so no symmetry of
+// Psi is assumed.  Lambda_max, the coefficients and everything else follow
+// the single-matrix path's definitions.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
 #include "internal.h"
 
-struct cpa_batch_ctx {
-    int count = 0;
+namespace cpa {
+namespace {
+
+constexpr int kP = 64;          // maximum min(m, n)
+constexpr int kQ = 128;         // maximum max(m, n)
+constexpr int kLdB = kP + 8;    // BF16 row stride of 64-wide tiles (conflict-free ldmatrix)
+constexpr int kLdX = kQ + 8;    // BF16 row stride of X tiles
+constexpr int kThreads = 128;
+constexpr int kMaxBatchTerms = 128;
+
+struct BatchDesc {
+    int64_t off;   // element offset of X (and Y) in the packed buffers
+    int m, n, L, pad;
 };
+
+// ---------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t su32b(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(su32b(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(su32b(p)));
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float *d, const uint32_t *a, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// ---------------------------------------------------------------- fragments
+//
+// Accumulator layout of m16n8k16 (per warp: 16 rows x 64 columns = 8 n-tiles):
+// thread (g = lane/4, t = lane%4) holds for n-tile nt the elements
+//   (16w + g,     8 nt + 2t + {0,1})  -> d[nt][0..1]
+//   (16w + g + 8, 8 nt + 2t + {0,1})  -> d[nt][2..3]
+
+struct Frag {
+    float v[8][4];
+};
+
+__device__ __forceinline__ void frag_zero(Frag &f) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) f.v[a][b] = 0.f;
+}
+
+__device__ __forceinline__ int frag_row(int w, int lane, int e) { return 16 * w + (lane >> 2) + (e >= 2 ? 8 : 0); }
+__device__ __forceinline__ int frag_col(int nt, int lane, int e) { return 8 * nt + 2 * (lane & 3) + (e & 1); }
+
+// A fragment (16 rows from r0, 16 columns from k0) of a row-major BF16 tile.
+__device__ __forceinline__ void load_a(uint32_t *a, const __nv_bfloat16 *base, int ld, int r0, int k0, int lane) {
+    const __nv_bfloat16 *p = base + (r0 + (lane & 15)) * ld + k0 + (lane >> 4) * 8;
+    ldsm_x4(a[0], a[1], a[2], a[3], p);
+}
+// A fragment of A = S^T where S is a row-major BF16 tile (A(i,k) = S(k,i)).
+__device__ __forceinline__ void load_a_t(uint32_t *a, const __nv_bfloat16 *base, int ld, int r0, int k0, int lane) {
+    // matrices: a0 = S[k0..+7][r0..+7]^T, a1 = S[k0..+7][r0+8..]^T, a2 = S[k0+8..][r0..]^T, a3 = S[k0+8..][r0+8..]^T
+    const int mtx = lane >> 3, r = lane & 7;
+    const int kk = k0 + ((mtx & 2) ? 8 : 0) + r;
+    const int ii = r0 + ((mtx & 1) ? 8 : 0);
+    ldsm_x4_t(a[0], a[1], a[2], a[3], base + kk * ld + ii);
+}
+// B fragments for two n-tiles (columns n0..n0+15), k from k0, of B(k,j) stored
+// row-major as S[k][j] (transposing load).  b[0],b[1]: n-tile n0; b[2],b[3]: n0+8.
+__device__ __forceinline__ void load_b_kn(uint32_t *b, const __nv_bfloat16 *base, int ld, int k0, int n0, int lane) {
+    const int mtx = lane >> 3, r = lane & 7;
+    const int kk = k0 + ((mtx & 1) ? 8 : 0) + r;
+    const int jj = n0 + ((mtx & 2) ? 8 : 0);
+    ldsm_x4_t(b[0], b[1], b[2], b[3], base + kk * ld + jj);
+}
+// B fragments of B(k,j) stored as S[j][k] (non-transposing load).
+__device__ __forceinline__ void load_b_nk(uint32_t *b, const __nv_bfloat16 *base, int ld, int k0, int n0, int lane) {
+    const int mtx = lane >> 3, r = lane & 7;
+    const int jj = n0 + ((mtx & 2) ? 8 : 0) + r;
+    const int kk = k0 + ((mtx & 1) ? 8 : 0);
+    ldsm_x4(b[0], b[1], b[2], b[3], base + jj * ld + kk);
+}
+
+// ---------------------------------------------------------------- shared memory
+
+struct BatchSmem {
+    __nv_bfloat16 xhi[kP * kLdX];        // Xp = X^T (m >= n) or X (m < n): p x q, hi
+    __nv_bfloat16 xlo[kP * kLdX];
+    __nv_bfloat16 ahi[kP * kLdB];        // At = (2/lambda) G
+    __nv_bfloat16 alo[kP * kLdB];
+    __nv_bfloat16 zhi[2][kP * kLdB];     // Psi_{k-1}, double buffered
+    __nv_bfloat16 zlo[2][kP * kLdB];
+    float g[kP * (kP + 1)];              // G (FP32), then H for the final product
+    float v[2][kP];                      // power-iteration vectors
+    double red[8];
+    double coef[kMaxBatchTerms];
+    double tab[4 * kMaxBatchTerms];
+    double hs[kMaxBatchTerms];
+    double scal[4];                      // theta, r, trace, lambda
+};
+
+__device__ __forceinline__ double bsum(double x, double *red) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = x;
+    __syncthreads();
+    return red[0] + red[1] + red[2] + red[3];
+}
+
+__device__ __forceinline__ uint64_t splitmix64_b(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// D(16w.., 0..63) = sum_k A(i,k) B(k,j) over K (multiple of 16, <= kQ),
+// hi/lo split when split.  a_trans: A = S^T of a row-major S[k][i];
+// b_kn: B stored S[k][j], else S[j][k].
+template <bool A_T, bool B_KN>
+__device__ __forceinline__ void mma_tile(Frag &d, const __nv_bfloat16 *ahi, const __nv_bfloat16 *alo, int lda,
+                                         const __nv_bfloat16 *bhi, const __nv_bfloat16 *blo, int ldb, int K,
+                                         bool split, int w, int lane) {
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        uint32_t ah[4], al[4];
+        if (A_T) {
+            load_a_t(ah, ahi, lda, 16 * w, k0, lane);
+            if (split) load_a_t(al, alo, lda, 16 * w, k0, lane);
+        } else {
+            load_a(ah, ahi, lda, 16 * w, k0, lane);
+            if (split) load_a(al, alo, lda, 16 * w, k0, lane);
+        }
+#pragma unroll
+        for (int np = 0; np < 4; ++np) {
+            uint32_t bh[4], bl[4];
+            if (B_KN) {
+                load_b_kn(bh, bhi, ldb, k0, 16 * np, lane);
+                if (split) load_b_kn(bl, blo, ldb, k0, 16 * np, lane);
+            } else {
+                load_b_nk(bh, bhi, ldb, k0, 16 * np, lane);
+                if (split) load_b_nk(bl, blo, ldb, k0, 16 * np, lane);
+            }
+            mma_bf16_16816(d.v[2 * np], ah, bh[0], bh[1]);
+            mma_bf16_16816(d.v[2 * np + 1], ah, bh[2], bh[3]);
+            if (split) {
+                mma_bf16_16816(d.v[2 * np], ah, bl[0], bl[1]);
+                mma_bf16_16816(d.v[2 * np + 1], ah, bl[2], bl[3]);
+                mma_bf16_16816(d.v[2 * np], al, bh[0], bh[1]);
+                mma_bf16_16816(d.v[2 * np + 1], al, bh[2], bh[3]);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void put_hilo(__nv_bfloat16 *hi, __nv_bfloat16 *lo, int idx, float v) {
+    __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[idx] = h;
+    lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+// Writes a fragment (rows 16w..+15, columns 0..63) to a row-major BF16
+// hi/lo tile.
+__device__ __forceinline__ void frag_store_hilo(const Frag &f, __nv_bfloat16 *hi, __nv_bfloat16 *lo, int ld, int w,
+                                                int lane) {
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int r = frag_row(w, lane, 2 * h2), c = frag_col(nt, lane, 0);
+            const float x0 = f.v[nt][2 * h2], x1 = f.v[nt][2 * h2 + 1];
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+            *reinterpret_cast<uint32_t *>(hi + r * ld + c) = pack2(h0, h1);
+            *reinterpret_cast<uint32_t *>(lo + r * ld + c) = pack2(l0, l1);
+        }
+    }
+}
+
+// FP32 FMA product for the plain variant: D(16w.., 0..63) += sum_k A(i,k) B(k,j)
+// with A, B given as FP32 element accessors through shared memory.
+template <class FA, class FB>
+__device__ __forceinline__ void fma_tile(Frag &d, FA A, FB B, int K, int w, int lane) {
+    for (int k = 0; k < K; ++k) {
+        float a0 = A(frag_row(w, lane, 0), k), a1 = A(frag_row(w, lane, 2), k);
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float b0 = B(k, frag_col(nt, lane, 0)), b1 = B(k, frag_col(nt, lane, 1));
+            d.v[nt][0] = fmaf(a0, b0, d.v[nt][0]);
+            d.v[nt][1] = fmaf(a0, b1, d.v[nt][1]);
+            d.v[nt][2] = fmaf(a1, b0, d.v[nt][2]);
+            d.v[nt][3] = fmaf(a1, b1, d.v[nt][3]);
+        }
+    }
+}
+
+// FP32 variant: Psi buffer b spans zhi[0..1] (b = 0) or zlo[0..1] (b = 1).
+__device__ __forceinline__ float *zbuf_f32(BatchSmem &S, int b) {
+    return reinterpret_cast<float *>(b == 0 ? &S.zhi[0][0] : &S.zlo[0][0]);
+}
+
+// ---------------------------------------------------------------- the kernel
+//
+// FP32 variant: the BF16 buffers are reused as FP32 storage (xhi/xlo hold X
+// in FP32, ahi/alo hold At, zhi[b]/zlo[b] hold Psi_{k-1}).
+
+template <bool TC>
+__global__ void __launch_bounds__(kThreads, 2)
+    batched_kernel(const BatchDesc *__restrict__ descs, const int *__restrict__ order, int count,
+                   const float *__restrict__ X, float *__restrict__ Y, const ShrinkParams *__restrict__ shr,
+                   int shr_stride, const double *__restrict__ lam_in, double *__restrict__ lam_out, int iters,
+                   int *__restrict__ status) {
+    extern __shared__ __align__(16) uint8_t smem_raw_b[];
+    BatchSmem &S = *reinterpret_cast<BatchSmem *>(smem_raw_b);
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+
+    for (int it = blockIdx.x; it < count; it += gridDim.x) {
+        const int idx = order[it];
+        const BatchDesc d = descs[idx];
+        const int m = d.m, n = d.n, L = d.L;
+        const bool tall = m >= n;           // Gram X^T X (p = n) or X X^T (p = m)
+        const int p = tall ? n : m, q = tall ? m : n;
+        const int q16 = (q + 15) & ~15, p16 = (p + 15) & ~15;
+        const float *Xg = X + d.off;
+        float *Yg = Y + d.off;
+        const ShrinkParams sp = shr[shr_stride ? idx : 0];
+
+        // ---- Xp (p x q, zero padded to multiples of 16) into shared memory:
+        // Xp = X^T when m >= n, else X, so that G = Xp Xp^T and the final
+        // product is H Xp (stored back transposed when m >= n)
+        for (int e = tid; e < p16 * q16; e += kThreads) {
+            const int r = e / q16, c = e % q16;
+            float x = 0.f;
+            if (r < p && c < q) x = tall ? __ldg(Xg + (int64_t)c * n + r) : __ldg(Xg + (int64_t)r * n + c);
+            if (TC)
+                put_hilo(S.xhi, S.xlo, r * kLdX + c, x);
+            else
+                reinterpret_cast<float *>(S.xhi)[r * kLdX + c] = x;   // spans xhi and xlo
+        }
+        __syncthreads();
+
+        // ---- Gram G(i,j) = sum_k Xp(i,k) Xp(j,k) (FP32 accumulate), into S.g
+        Frag acc;
+        frag_zero(acc);
+        if (TC) {
+            mma_tile<false, false>(acc, S.xhi, S.xlo, kLdX, S.xhi, S.xlo, kLdX, q16, true, w, lane);
+        } else {
+            const float *xf = reinterpret_cast<const float *>(S.xhi);
+            fma_tile(acc, [&](int i, int k) { return xf[i * kLdX + k]; },
+                     [&](int k, int j) { return xf[j * kLdX + k]; }, q, w, lane);
+        }
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                S.g[frag_row(w, lane, e) * (kP + 1) + frag_col(nt, lane, e)] = acc.v[nt][e];
+        __syncthreads();
+
+        // ---- Lambda_max: power iteration (definition of cpa_lambda_bound)
+        double lam;
+        if (lam_in) {
+            lam = lam_in[idx];
+        } else {
+            double s0 = 0.0;
+            for (int i = tid; i < p; i += kThreads) {
+                const uint64_t z = splitmix64_b(kStartSeed, (uint64_t)i);
+                const float x = (float)((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+                S.v[0][i] = x;
+                s0 += (double)x * (double)x;
+            }
+            double nrm2 = bsum(s0, S.red);
+            int cur = 0;
+            for (int t = 0; t <= iters; ++t) {
+                // w = G (v / |v|): two threads per row
+                const float sc = nrm2 > 0.0 ? (float)(1.0 / sqrt(nrm2)) : 0.f;
+                const int row = tid >> 1, half = tid & 1;
+                float a = 0.f;
+                if (row < p)
+                    for (int j = half; j < p; j += 2) a = fmaf(S.g[row * (kP + 1) + j], S.v[cur][j], a);
+                a += __shfl_xor_sync(0xffffffffu, a, 1);
+                a *= sc;
+                if (row < p && half == 0) S.v[cur ^ 1][row] = a;
+                const double ww = (row < p && half == 0) ? (double)a * (double)a : 0.0;
+                if (t < iters) {
+                    nrm2 = bsum(ww, S.red);
+                    cur ^= 1;
+                } else {
+                    // v = S.v[cur] / sqrt(nrm2), w = S.v[cur^1]
+                    __syncthreads();
+                    const double vs = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
+                    double th = 0.0, tr = 0.0;
+                    for (int i = tid; i < p; i += kThreads) {
+                        th += (double)S.v[cur][i] * vs * (double)S.v[cur ^ 1][i];
+                        tr += (double)S.g[i * (kP + 1) + i];
+                    }
+                    th = bsum(th, S.red);
+                    double r2 = 0.0;
+                    for (int i = tid; i < p; i += kThreads) {
+                        const double dd = (double)S.v[cur ^ 1][i] - th * (double)S.v[cur][i] * vs;
+                        r2 += dd * dd;
+                    }
+                    r2 = bsum(r2, S.red);
+                    tr = bsum(tr, S.red);
+                    lam = (th + sqrt(r2)) * (1.0 + kLambdaMargin);
+                    if (lam > tr) lam = tr;
+                    if (!isfinite(lam) || !isfinite(tr)) {
+                        if (tid == 0) atomicExch(status, (int)CPA_ERR_NONFINITE);
+                        lam = 1.0;
+                    } else if (!(lam > 0.0)) {
+                        lam = tr > 0.0 ? tr : 1.0;
+                    }
+                }
+            }
+        }
+        if (tid == 0) lam_out[idx] = lam;
+
+        // ---- coefficients (Eq. chebychev_coeff_shifted), FP64, cos(pi m / 2L) table
+        for (int e = tid; e < 4 * L; e += kThreads) S.tab[e] = cospi((double)e / (2.0 * L));
+        __syncthreads();
+        for (int l = tid; l < L; l += kThreads) S.hs[l] = response(sp, 0.5 * lam * (S.tab[(2 * l + 1) % (4 * L)] + 1.0));
+        __syncthreads();
+        for (int k = tid; k < L; k += kThreads) {
+            double a = 0.0;
+            for (int l = 0; l < L; ++l) a += S.tab[(int)(((int64_t)k * (2 * l + 1)) % (4 * L))] * S.hs[l];
+            S.coef[k] = 2.0 / (double)L * a;
+        }
+        __syncthreads();
+
+        // ---- shift: At = (2/lambda) G (operand), Psi_1 = At - Id, H = c0/2 Id + c1 Psi_1
+        const float s2 = (float)(2.0 / lam);
+        Frag z1, z0, h;   // Psi_{k-1}, Psi_{k-2}, H in the accumulator layout
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int r = frag_row(w, lane, e), c = frag_col(nt, lane, e);
+                const bool in = r < p && c < p;
+                const float at = in ? s2 * S.g[r * (kP + 1) + c] : 0.f;
+                const float eye = (r == c && in) ? 1.f : 0.f;
+                z1.v[nt][e] = at - eye;
+                z0.v[nt][e] = eye;   // Psi_0 = Id
+                h.v[nt][e] = (float)(0.5 * S.coef[0]) * eye + (L > 1 ? (float)S.coef[1] : 0.f) * z1.v[nt][e];
+                if (TC) {
+                    put_hilo(S.ahi, S.alo, r * kLdB + c, at);
+                } else {
+                    reinterpret_cast<float *>(S.ahi)[r * kLdB + c] = at;
+                }
+            }
+        if (TC) {
+            frag_store_hilo(z1, S.zhi[1], S.zlo[1], kLdB, w, lane);
+        } else {
+            float *zf = zbuf_f32(S, 1);
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) zf[frag_row(w, lane, e) * kLdB + frag_col(nt, lane, e)] = z1.v[nt][e];
+        }
+        __syncthreads();
+
+        // ---- recurrence
+        for (int k = 2; k < L; ++k) {
+            const int bcur = (k - 1) & 1;   // buffer holding Psi_{k-1}
+            frag_zero(acc);
+            if (TC) {
+                mma_tile<false, true>(acc, S.ahi, S.alo, kLdB, S.zhi[bcur], S.zlo[bcur], kLdB, p16, true, w, lane);
+            } else {
+                const float *af = reinterpret_cast<const float *>(S.ahi);
+                const float *zf = zbuf_f32(S, bcur);
+                fma_tile(acc, [&](int i, int kk) { return af[i * kLdB + kk]; },
+                         [&](int kk, int j) { return zf[kk * kLdB + j]; }, p, w, lane);
+            }
+            const float ck = (float)S.coef[k];
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float zk = fmaf(2.f, acc.v[nt][e], fmaf(-2.f, z1.v[nt][e], -z0.v[nt][e]));
+                    z0.v[nt][e] = z1.v[nt][e];
+                    z1.v[nt][e] = zk;
+                    h.v[nt][e] = fmaf(ck, zk, h.v[nt][e]);
+                }
+            // Psi_k into the other buffer; one barrier per step
+            if (TC) {
+                frag_store_hilo(z1, S.zhi[bcur ^ 1], S.zlo[bcur ^ 1], kLdB, w, lane);
+            } else {
+                float *zf = zbuf_f32(S, bcur ^ 1);
+#pragma unroll
+                for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        zf[frag_row(w, lane, e) * kLdB + frag_col(nt, lane, e)] = z1.v[nt][e];
+            }
+            __syncthreads();
+        }
+
+        // ---- final product: Y = X H (tall) or H X (wide), H through shared memory
+        if (TC) {
+            frag_store_hilo(h, S.ahi, S.alo, kLdB, w, lane);   // At no longer needed
+        } else {
+            float *hf = reinterpret_cast<float *>(S.ahi);
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) hf[frag_row(w, lane, e) * kLdB + frag_col(nt, lane, e)] = h.v[nt][e];
+        }
+        __syncthreads();
+        // D = H Xp in column blocks of 64; D(r, c) is Y(c, r) (m >= n) or Y(r, c)
+        for (int b = 0; b < (q + 63) / 64; ++b) {
+            frag_zero(acc);
+            if (TC) {
+                mma_tile<false, true>(acc, S.ahi, S.alo, kLdB, S.xhi + 64 * b, S.xlo + 64 * b, kLdX, p16, true, w,
+                                      lane);
+            } else {
+                const float *xf = reinterpret_cast<const float *>(S.xhi);
+                const float *hf = reinterpret_cast<const float *>(S.ahi);
+                fma_tile(acc, [&](int i, int kk) { return hf[i * kLdB + kk]; },
+                         [&](int kk, int j) { return xf[kk * kLdX + 64 * b + j]; }, p, w, lane);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int r = frag_row(w, lane, e), c = 64 * b + frag_col(nt, lane, e);
+                    if (r < p && c < q) {
+                        if (tall)
+                            Yg[(int64_t)c * n + r] = acc.v[nt][e];
+                        else
+                            Yg[(int64_t)r * n + c] = acc.v[nt][e];
+                    }
+                }
+        }
+        __syncthreads();   // shared memory is reused by the next matrix
+    }
+}
+
+}  // namespace
+}  // namespace cpa
+
+using namespace cpa;
+
+struct cpa_batch_ctx {
+    int device = 0;
+    int count = 0;
+    int num_sms = 0;
+    BatchDesc *d_desc = nullptr;
+    int *d_order = nullptr;
+    double *d_lambda = nullptr;
+    ShrinkParams *d_shrink = nullptr;
+    int shrink_cap = 0;
+    int *d_status = nullptr;
+    int max_L = 0;
+    int64_t total = 0;   // elements covered by the packed buffers
+    std::vector<ShrinkParams> uploaded;   // shrink parameters currently on the device
+};
+
+namespace {
+thread_local char g_berr[256] = "";
+cpa_status bfail(cudaError_t e, const char *where) {
+    snprintf(g_berr, sizeof g_berr, "%s: %s", where, cudaGetErrorString(e));
+    return CPA_ERR_CUDA;
+}
+#define BCK(call)                                        \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return bfail(e_, #call);  \
+    } while (0)
+}  // namespace
 
 extern "C" {
 
 cpa_status cpa_batch_create(cpa_handle h, int count, const int64_t *off, const int32_t *m, const int32_t *n,
                             const int32_t *L, int L0, cpa_batch *out) {
-    (void)h; (void)count; (void)off; (void)m; (void)n; (void)L; (void)L0;
-    if (out) *out = nullptr;
-    return CPA_ERR_UNSUPPORTED;
+    if (!h || !out || count < 1 || !off || !m || !n) return CPA_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::vector<BatchDesc> desc(count);
+    int max_L = 0;
+    int64_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        const int mi = m[i], ni = n[i], Li = L ? L[i] : L0;
+        if (mi < 1 || ni < 1 || std::min(mi, ni) > kP || std::max(mi, ni) > kQ || off[i] < 0 || Li < 1 ||
+            Li > kMaxBatchTerms)
+            return CPA_ERR_INVALID_ARG;
+        desc[i] = BatchDesc{off[i], mi, ni, Li, 0};
+        max_L = std::max(max_L, Li);
+        total = std::max(total, off[i] + (int64_t)mi * ni);
+    }
+    // largest work first: (L - 2) p^3 + p^2 q
+    std::vector<int> order(count);
+    std::iota(order.begin(), order.end(), 0);
+    auto work = [&](int i) {
+        const double p = std::min(desc[i].m, desc[i].n), q = std::max(desc[i].m, desc[i].n);
+        return (desc[i].L - 2) * p * p * p + 2.0 * p * p * q;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+
+    int device = 0;
+    BCK(cudaGetDevice(&device));
+    cpa_batch b = new cpa_batch_ctx();
+    b->device = device;
+    b->count = count;
+    b->max_L = max_L;
+    b->total = total;
+    BCK(cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, device));
+    cudaError_t e = cudaMalloc(&b->d_desc, sizeof(BatchDesc) * count);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_order, sizeof(int) * count);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_lambda, sizeof(double) * count);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_desc, desc.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cpa_batch_destroy(b);
+        return bfail(e, "cpa_batch_create");
+    }
+    *out = b;
+    return CPA_OK;
 }
 
 cpa_status cpa_batch_destroy(cpa_batch b) {
+    if (!b) return CPA_ERR_INVALID_ARG;
+    cudaFree(b->d_desc);
+    cudaFree(b->d_order);
+    cudaFree(b->d_lambda);
+    cudaFree(b->d_shrink);
+    cudaFree(b->d_status);
     delete b;
     return CPA_OK;
 }
 
-cpa_status cpa_svt_batched(cpa_handle h, cpa_batch b, const float *dX, const cpa_shrink *s, int s_count,
-                           const double *lambda, int iters, int prec, float *dY, void *stream) {
-    (void)h; (void)b; (void)dX; (void)s; (void)s_count; (void)lambda; (void)iters; (void)prec; (void)dY;
-    (void)stream;
-    return CPA_ERR_UNSUPPORTED;
+const double *cpa_batch_lambdas(cpa_batch b) { return b ? b->d_lambda : nullptr; }
+
+cpa_status cpa_batch_read_lambdas(cpa_batch b, double *host_out, void *stream) {
+    if (!b || !host_out) return CPA_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    BCK(cudaSetDevice(b->device));
+    int status = 0;
+    BCK(cudaMemcpyAsync(host_out, b->d_lambda, sizeof(double) * b->count, cudaMemcpyDeviceToHost, st));
+    BCK(cudaMemcpyAsync(&status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BCK(cudaStreamSynchronize(st));
+    return status ? (cpa_status)status : CPA_OK;
 }
 
-const double *cpa_batch_lambdas(cpa_batch b) {
-    (void)b;
-    return nullptr;
+cpa_status cpa_svt_batched(cpa_handle h, cpa_batch b, const float *dX, const cpa_shrink *s, int s_count,
+                           const double *lambda, int iters, int prec, float *dY, void *stream) {
+    if (!h || !b || !dX || !dY || !s || (s_count != 1 && s_count != b->count) || iters < 0 || iters > 10000)
+        return CPA_ERR_INVALID_ARG;
+    if (prec != CPA_FP32 && prec != CPA_BF16 && prec != CPA_BF16X3) return CPA_ERR_UNSUPPORTED;
+    uintptr_t x0 = (uintptr_t)dX, y0 = (uintptr_t)dY, bytes = (uintptr_t)b->total * sizeof(float);
+    if (x0 < y0 + bytes && y0 < x0 + bytes) return CPA_ERR_INVALID_ARG;   // output overlaps input
+    std::vector<ShrinkParams> sp(s_count);
+    memset(sp.data(), 0, sizeof(ShrinkParams) * s_count);   // padding too: compared with memcmp
+    for (int i = 0; i < s_count; ++i) {
+        const cpa_shrink &x = s[i];
+        bool ok = (x.kind == CPA_HARD || x.kind == CPA_SOFT) ? (x.tau >= 0.0 && std::isfinite(x.tau))
+                  : (x.kind == CPA_WSOFT) ? (x.c >= 0.0 && x.eps > 0.0 && x.noise >= 0.0 && std::isfinite(x.c) &&
+                                             std::isfinite(x.noise))
+                                          : false;
+        if (!ok) return CPA_ERR_INVALID_ARG;
+        sp[i].kind = x.kind;
+        sp[i].tau = x.tau;
+        sp[i].c = x.c;
+        sp[i].eps = x.eps;
+        sp[i].noise = x.noise;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    BCK(cudaSetDevice(b->device));
+    // the shrink parameters are uploaded on the first call and whenever they
+    // change; such a call synchronises the stream (and cannot be captured),
+    // later calls with the same parameters only launch the kernel
+    const bool same = b->uploaded.size() == sp.size() &&
+                      memcmp(b->uploaded.data(), sp.data(), sizeof(ShrinkParams) * sp.size()) == 0;
+    if (!same) {
+        BCK(cudaStreamSynchronize(st));
+        if (b->shrink_cap < s_count) {
+            if (b->d_shrink) cudaFree(b->d_shrink);
+            b->d_shrink = nullptr;
+            BCK(cudaMalloc(&b->d_shrink, sizeof(ShrinkParams) * s_count));
+            b->shrink_cap = s_count;
+        }
+        BCK(cudaMemcpy(b->d_shrink, sp.data(), sizeof(ShrinkParams) * s_count, cudaMemcpyHostToDevice));
+        b->uploaded = sp;
+    }
+    BCK(cudaMemsetAsync(b->d_status, 0, sizeof(int), st));
+    const size_t smem = sizeof(BatchSmem);
+    const bool tc = prec != CPA_FP32;
+    auto kern = tc ? batched_kernel<true> : batched_kernel<false>;
+    BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+    if (per_sm < 1) per_sm = 1;
+    int grid = std::min(b->count, b->num_sms * per_sm);
+    kern<<<grid, kThreads, smem, st>>>(b->d_desc, b->d_order, b->count, dX, dY, b->d_shrink, s_count > 1 ? 1 : 0,
+                                       lambda, b->d_lambda, iters, b->d_status);
+    BCK(cudaGetLastError());
+    return CPA_OK;
 }
 
 }  // extern "C"

@@ -265,8 +265,9 @@ __device__ __forceinline__ void grid_barrier(unsigned int *count, unsigned int &
     __syncthreads();
     if (threadIdx.x == 0) {
         target += gridDim.x;
-        __threadfence();
-        atomicAdd(count, 1u);
+        // release: this block's prior writes (made visible to the thread by
+        // the CTA barrier) are ordered before the arrival
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
         const long long t0 = clock64();
         while (true) {
             unsigned int v;
@@ -277,7 +278,6 @@ __device__ __forceinline__ void grid_barrier(unsigned int *count, unsigned int &
                 break;
             }
         }
-        __threadfence();
     }
     __syncthreads();
 }

@@ -1,0 +1,145 @@
+"""Parity of the batched path (cpa_svt_batched, one persistent launch) with
+the FP64 oracle, matrix by matrix.
+
+Tolerances as for the single-matrix path: fp32 1e-5; bf16 (hi/lo split in
+every product) 2e-3 (measures ~1e-5).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1705_07112_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0x1705071120000000
+TOL = {"fp32": 1e-5, "bf16": 2e-3}
+
+
+@pytest.fixture(scope="module")
+def cpa():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1705_07112_gb300 as cpa
+    return cpa
+
+
+@pytest.fixture(scope="module")
+def handle(cpa):
+    h = cpa.Handle(0)
+    yield h
+    h.close()
+
+
+def oracle_lambda(X64):
+    return O.lambda_bound(X64, 20, 0.01, O.start_vector(SEED, min(X64.shape)))["lam"]
+
+
+def pack(mats):
+    import torch
+    flat = np.concatenate([m.astype(np.float32).ravel() for m in mats])
+    return torch.from_numpy(flat).cuda()
+
+
+def unpack(Y, shapes):
+    y = Y.cpu().numpy().astype(np.float64)
+    out, o = [], 0
+    for m, n in shapes:
+        out.append(y[o:o + m * n].reshape(m, n))
+        o += m * n
+    return out
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+EDGE = [(1, 1), (1, 7), (7, 1), (64, 64), (64, 40), (40, 64), (17, 100), (100, 17), (128, 64), (64, 128),
+        (3, 3), (63, 65), (65, 63), (16, 16), (33, 127)]
+
+
+def edge_batch(seed=7):
+    rng = np.random.default_rng(seed)
+    mats = []
+    for (m, n) in EDGE:
+        r = max(1, min(m, n) // 6)
+        mats.append(rng.standard_normal((m, r)) @ rng.standard_normal((r, n)) + 0.05 * rng.standard_normal((m, n)))
+    return mats
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("kind", [O.HARD, O.SOFT, O.WSOFT])
+def test_batched_edge_shapes_given_lambda(cpa, handle, prec, kind):
+    import torch
+    mats = [m.astype(np.float32).astype(np.float64) for m in edge_batch()]
+    shapes = [m.shape for m in mats]
+    lams = np.array([oracle_lambda(m) for m in mats])
+    specs = []
+    for m, lam in zip(mats, lams):
+        sig = np.sqrt(lam / 1.01)
+        if kind == O.HARD:
+            specs.append(O.Shrink(O.HARD, 0.3 * sig))
+        elif kind == O.SOFT:
+            specs.append(O.Shrink(O.SOFT, 0.2 * sig))
+        else:
+            specs.append(O.Shrink(O.WSOFT, 0.0, c=0.05 * sig * sig, eps=1e-8, noise=0.01 * sig * sig))
+    Ls = [1, 2, 3, 24, 24, 24, 17, 17, 30, 30, 5, 24, 24, 9, 24]
+    plan = cpa.BatchPlan(handle, shapes, L=Ls)
+    Y = cpa.cpa_svt_batched(handle, plan, pack(mats), [dict(kind=s.kind, tau=s.tau, c=s.c, eps=s.eps,
+                                                            noise=s.noise) for s in specs],
+                            lambdas=torch.tensor(lams, dtype=torch.float64, device="cuda"), prec=prec)
+    torch.cuda.synchronize()
+    for Xm, Ym, s, L, lam in zip(mats, unpack(Y, shapes), specs, Ls, lams):
+        ref = O.cpa(Xm, s, L, lam)
+        assert rel(Ym, ref) <= TOL[prec], (Xm.shape, L, rel(Ym, ref))
+    assert np.array_equal(plan.lambdas(), lams)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_batched_computed_lambda(cpa, handle, prec):
+    import torch
+    mats = [m.astype(np.float32).astype(np.float64) for m in edge_batch(11)]
+    shapes = [m.shape for m in mats]
+    plan = cpa.BatchPlan(handle, shapes, L0=12)
+    s = O.Shrink(O.SOFT, 0.5)
+    Y = cpa.cpa_svt_batched(handle, plan, pack(mats), dict(kind=O.SOFT, tau=0.5), prec=prec)
+    torch.cuda.synchronize()
+    lam_gpu = plan.lambdas()
+    for i, (Xm, Ym) in enumerate(zip(mats, unpack(Y, shapes))):
+        lam = oracle_lambda(Xm)
+        assert abs(lam_gpu[i] - lam) <= 1e-4 * lam, (Xm.shape, lam_gpu[i], lam)
+        assert rel(Ym, O.cpa(Xm, s, 12, lam)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_patch_groups_full_batch_sampled(cpa, handle, prec):
+    """The full 20,000-matrix patch-group batch in the benchmark's launch
+    configuration (one persistent launch, device-computed bounds); a sample
+    of matrices is checked against the oracle."""
+    import torch
+    mats, spec, L, sigma = inputs.patch_groups(20000)
+    shapes = [m.shape for m in mats]
+    specs = [dict(kind=spec.kind, tau=spec.tau, c=spec.c, eps=spec.eps,
+                  noise=inputs.patch_group_noise(sh, sigma)) for sh in shapes]
+    plan = cpa.BatchPlan(handle, shapes, L0=L)
+    Y = cpa.cpa_svt_batched(handle, plan, pack(mats), specs, prec=prec)
+    torch.cuda.synchronize()
+    lam_gpu = plan.lambdas()
+    ys = unpack(Y, shapes)
+    rng = np.random.default_rng(3)
+    for i in list(rng.choice(len(mats), 60, replace=False)) + [0, len(mats) - 1]:
+        Xm = mats[i].astype(np.float64)
+        lam = oracle_lambda(Xm)
+        assert abs(lam_gpu[i] - lam) <= 1e-4 * lam
+        s = O.Shrink(specs[i]["kind"], 0.0, specs[i]["c"], specs[i]["eps"], specs[i]["noise"])
+        assert rel(ys[i], O.cpa(Xm, s, L, lam)) <= TOL[prec], (i, Xm.shape)
+
+
+def test_batch_plan_argument_errors(cpa, handle):
+    with pytest.raises(cpa.CpaError):
+        cpa.BatchPlan(handle, [(65, 65)])          # min(m, n) > 64
+    with pytest.raises(cpa.CpaError):
+        cpa.BatchPlan(handle, [(64, 129)])         # max(m, n) > 128
+    with pytest.raises(cpa.CpaError):
+        cpa.BatchPlan(handle, [(8, 8)], L0=0)
