@@ -211,6 +211,29 @@ CPA_API cpa_status cpa_kernel_split_bf16(const float *X, int rows, int cols, int
                                          void *lo, int64_t ldo, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Allocation-free Lambda_max bound.  The paper has no counterpart: this is a
+ * deployment variant of cpa_lambda_bound for callers that cannot allocate
+ * device memory (latency-critical loops that cannot pay for the device-wide
+ * synchronisation of cudaMalloc/cudaFree, services held to a fixed device
+ * memory budget, processes whose device memory belongs to another
+ * allocator).  It takes no handle and allocates nothing: its scratch lives in
+ * one fixed array of a little over 1 MB in device global memory that every
+ * GPU loading the library holds until the process exits.
+ *   Same definition and result as cpa_lambda_bound (same kernels), on the
+ *   current device; dX as there; writes the bound to *lambda_out (host) and
+ *   synchronises `stream`.
+ *   Limits: min(m, n) <= 512, iters <= 1000; larger sizes return
+ *   CPA_ERR_INVALID_ARG.
+ *   The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   Every call shares the one array: calls whose work overlaps on the GPU
+ *   (other host threads, other streams) race on it and must be serialised
+ *   by the caller.
+ * ------------------------------------------------------------------------- */
+CPA_API cpa_status cpa_lambda_bound_noalloc(const float *dX, int64_t m, int64_t n, int64_t ldx, int iters,
+                                            double *lambda_out, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Batched shrinkage of many small independent matrices (patch groups), one
  * persistent launch.  The matrices live packed in one device buffer: matrix
  * i starts at element offset off[i] and is row-major m[i] x n[i] with

@@ -23,7 +23,8 @@ PREC = {"fp32": FP32, "tf32": TF32, "bf16": BF16, "bf16x3": BF16X3}
 EXPORTS = ["cpa_create", "cpa_destroy", "cpa_status_string", "cpa_last_error", "cpa_coeffs",
            "cpa_lambda_bound", "cpa_svt", "cpa_get_lambda", "cpa_get_coeffs", "cpa_batch_create",
            "cpa_batch_destroy", "cpa_svt_batched", "cpa_batch_lambdas", "cpa_profile_enable",
-           "cpa_profile_read", "cpa_kernel_gemm_bf16", "cpa_kernel_split_bf16", "cpa_batch_read_lambdas"]
+           "cpa_profile_read", "cpa_kernel_gemm_bf16", "cpa_kernel_split_bf16", "cpa_batch_read_lambdas",
+           "cpa_lambda_bound_noalloc"]
 STAGES = ["prep", "gram", "bound", "coeff", "shift", "recur", "apply"]
 
 
@@ -74,6 +75,7 @@ def load(path: str = LIB_PATH):
                                                ctypes.c_int, _vp, _vp]),
             "cpa_batch_lambdas": (_vp, [_vp]),
             "cpa_batch_read_lambdas": (ctypes.c_int, [_vp, _P(_d), _vp]),
+            "cpa_lambda_bound_noalloc": (ctypes.c_int, [_vp, _i64, _i64, _i64, ctypes.c_int, _P(_d), _vp]),
             "cpa_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
             "cpa_kernel_gemm_bf16": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _i64, _vp,
                                                     _vp, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_float, _vp,
@@ -180,6 +182,17 @@ def cpa_lambda_bound(h: Handle, X, iters: int = 20, stream=None) -> float:
     out = ctypes.c_double()
     _check(load().cpa_lambda_bound(h.ptr, ctypes.c_void_p(ptr), m, n, ld, int(iters), ctypes.byref(out),
                                    _stream_ptr(stream)), "cpa_lambda_bound")
+    return out.value
+
+
+def cpa_lambda_bound_noalloc(X, iters: int = 20, stream=None) -> float:
+    """The Lambda_max bound of cpa_lambda_bound computed without a handle
+    and without allocating device memory (fixed scratch array inside the
+    library; min(m, n) <= 512), for callers that must not allocate."""
+    ptr, m, n, ld = _matrix(X, "X")
+    out = ctypes.c_double()
+    _check(load().cpa_lambda_bound_noalloc(ctypes.c_void_p(ptr), m, n, ld, int(iters), ctypes.byref(out),
+                                           _stream_ptr(stream)), "cpa_lambda_bound_noalloc")
     return out.value
 
 
