@@ -434,7 +434,28 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
     // Ring: Psi_k overwrites Psi_{k-2} in slot k&1; Psi_0 = Id is implicit.
     // The tensor-core path multiplies by At = (2/lambda) G and applies the
     // shift exactly in the FP32 epilogue:  Psi_k = 2 At Psi_{k-1} - 2 Psi_{k-1} - Psi_{k-2}.
-    for (int k = 2; k < L; ++k) {
+    if (tc && L > 2) {
+        // every step in one cooperative launch (grid barrier between steps)
+        StageScope sc(h, CPA_STAGE_RECUR, st, 1);
+        Epilogue e;
+        e.D = w.Z[0];
+        e.ldd = w.ldp;
+        e.ldc = w.ldp;
+        e.ldc2 = w.ldp;
+        e.s_acc = 2.f;
+        e.s_c = -1.f;
+        e.s_c2 = -2.f;
+        e.H = w.H;
+        e.ldh = w.ldp;
+        e.coef = w.coef;
+        e.ldb = w.ldp;
+        e.symmetric_upper = 1;
+        TcOperand a;
+        a.hi = w.Ahi; a.lo = w.Alo; a.ld = w.ldp; a.rows = (int)p;
+        CK(gemm_tc_recurrence((int)p, a, nsplit_rec, e, 2, L, w.Z, w.Zhi, w.Zlo, (unsigned int *)(w.flag + 2), st,
+                              h->num_sms));
+    }
+    for (int k = 2; k < L && !tc; ++k) {
         StageScope sc(h, CPA_STAGE_RECUR, st, 1);
         Epilogue e;
         int cur = k & 1, prev = (k - 1) & 1;

@@ -29,6 +29,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <mutex>
 
 #include "internal.h"
@@ -149,10 +150,33 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 
 // Operand maps of the main loop and the 32 x 32 block maps of the epilogue
 // (FP32 C, C2, H, D and BF16 hi/lo copies of D).
-struct TileMaps {
-    CUtensorMap a_hi, a_lo, b_hi, b_lo;
-    CUtensorMap c, c2, h, d, dhi, dlo;
+// Per ring parity of the recurrence (a single product uses parity 0): the B
+// operand and the epilogue block maps (C = D updated in place, C2, D hi/lo).
+struct StepMaps {
+    CUtensorMap b_hi, b_lo;
+    CUtensorMap c, c2, d, dhi, dlo;
 };
+struct TileMaps {
+    CUtensorMap a_hi, a_lo, h;
+    StepMaps s[2];
+};
+
+// Several recurrence steps in one cooperative launch.  Step k uses ring slot
+// k & 1: D = C = z[k&1] (Psi_{k-2} overwritten by Psi_k), C2 = z[(k&1)^1]
+// (Psi_{k-1}), BF16 copies zhi/zlo[k&1], B operand zhi/zlo[(k&1)^1]; step 2
+// has no C and subtracts Id on the diagonal.  A grid barrier (counter *bar,
+// zeroed before the launch) separates the steps.
+struct MultiStep {
+    int multi = 0;
+    int k_first = 0, k_end = 1;
+    float *z[2] = {nullptr, nullptr};
+    __nv_bfloat16 *zhi[2] = {nullptr, nullptr}, *zlo[2] = {nullptr, nullptr};
+    unsigned int *bar = nullptr;
+};
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
 
 // Shared memory of one epilogue warp: three FP32 32 x 32 blocks (C -> D in
 // place, C2, H in place), two BF16 32 x 32 blocks (hi/lo copies of D at the
@@ -171,7 +195,7 @@ template <int BN>
 struct Smem {
     static constexpr int kStageA = BM * BK * 2;
     static constexpr int kStageB = BN * BK * 2;
-    static constexpr int kStages = (BN == 256) ? 3 : (BN == 128 ? 4 : 6);
+    static constexpr int kStages = (BN == 256) ? 3 : (BN == 128 ? 4 : 6);   // BN 64: 6 x 24 KB, 32: 6 x 20 KB
     static constexpr int kBytes =
         kStages * (kStageA + kStageB) + 4 * (int)sizeof(EpiSmem) + 1024 /* align */ + 256 /* barriers */;
 };
@@ -217,25 +241,34 @@ __device__ __forceinline__ void store_transposed(const Epilogue &e, const uint32
 // transpose buffer.  A diagonal block (j0 == r0) is written in full at its
 // own position, each pair (i,j), (j,i) taking the value of the upper
 // element.  Only lane 0 issues TMA operations.
-__device__ __forceinline__ void epilogue_sym_block(const Epilogue &e, const TileMaps &maps, float ck, int M, int N,
-                                                   int r0, int j0, int lane, const float *acc, EpiSmem &es,
-                                                   uint64_t *bar, uint32_t &phase, volatile int *abort_flag) {
-    const bool diag = (j0 == r0);
-    const bool any_load = e.C || e.C2 || e.H;
-    // previous block's TMA stores must have finished reading shared memory
+// Issues the TMA loads of one block's inputs (C, C2, H at the mirrored
+// position) into the warp's buffers, once the previous block's TMA stores
+// have finished reading them.
+__device__ __forceinline__ void epilogue_issue_loads(const Epilogue &e, const StepMaps &maps, const CUtensorMap &hmap,
+                                                     int r0, int j0, int lane, EpiSmem &es, uint64_t *bar) {
     fence_proxy_async();
     __syncwarp();
     if (lane == 0) {
         bulk_wait_read_all();
-        if (any_load) {
+        if (e.C || e.C2 || e.H) {
             const uint32_t bytes = 4096u * ((e.C ? 1u : 0u) + (e.C2 ? 1u : 0u) + (e.H ? 1u : 0u));
             mbar_expect_tx(bar, bytes);
             if (e.C) tma_load_2d(es.c, &maps.c, bar, r0, j0);
             if (e.C2) tma_load_2d(es.c2, &maps.c2, bar, r0, j0);
-            if (e.H) tma_load_2d(es.h, &maps.h, bar, r0, j0);
+            if (e.H) tma_load_2d(es.h, &hmap, bar, r0, j0);
         }
     }
     __syncwarp();
+}
+
+__device__ __forceinline__ void epilogue_sym_block(const Epilogue &e, const StepMaps &maps, const CUtensorMap &hmap,
+                                                   float ck, int M, int N,
+                                                   int r0, int j0, int lane, const float *acc, EpiSmem &es,
+                                                   uint64_t *bar, uint32_t &phase, volatile int *abort_flag,
+                                                   bool preloaded) {
+    const bool diag = (j0 == r0);
+    const bool any_load = e.C || e.C2 || e.H;
+    if (!preloaded) epilogue_issue_loads(e, maps, hmap, r0, j0, lane, es, bar);
     if (any_load) {
         mbar_wait(bar, phase, abort_flag);
         phase ^= 1u;
@@ -292,7 +325,7 @@ __device__ __forceinline__ void epilogue_sym_block(const Epilogue &e, const Tile
     __syncwarp();
     if (lane == 0) {
         tma_store_2d(&maps.d, es.c, r0, j0);
-        if (e.H) tma_store_2d(&maps.h, es.h, r0, j0);
+        if (e.H) tma_store_2d(&hmap, es.h, r0, j0);
         if (e.Dhi) {
             tma_store_2d(&maps.dhi, es.hi, r0, j0);
             if (e.Dlo) tma_store_2d(&maps.dlo, es.lo, r0, j0);
@@ -366,7 +399,8 @@ __host__ __device__ inline int count_tiles(int tiles_m, int tiles_n, int sym, in
 
 template <int BN>
 __global__ void __launch_bounds__(kThreads, 1)
-    gemm_tc_kernel(const __grid_constant__ TileMaps maps, int M, int N, int K, int nsplit, Epilogue e, int *err) {
+    gemm_tc_kernel(const __grid_constant__ TileMaps maps, int M, int N, int K, int nsplit, Epilogue e, MultiStep ms,
+                   int *err) {
     using S = Smem<BN>;
     constexpr int kStages = S::kStages;
     constexpr uint32_t kTmemCols = 2 * BN;   // two accumulators
@@ -383,7 +417,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *tfull = bars + 2 * kStages;  // [2]
     uint64_t *tempty = tfull + 2;          // [2]
     uint64_t *ebar = tempty + 2;           // [4] epilogue TMA loads
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ebar + 4);
+    uint64_t *stepbar = ebar + 4;          // next step may load (multi-step)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(stepbar + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -403,6 +438,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&tempty[b], 4);
         }
         for (int q = 0; q < 4; ++q) mbar_init(&ebar[q], 1);
+        mbar_init(stepbar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -421,25 +457,34 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             int stage = 0;
-            uint32_t phase = 0;
+            uint32_t phase = 0, sphase = 0;
             uint32_t armed_mask = 0, armed_phase = 0;   // per stage: armed at least once / phase it was armed in
-            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
-                int tm, tn;
-                tile_of(t, tiles_m, tiles_n, sym, BN, tm, tn);
-                const int m0 = tm * BM, n0 = tn * BN;
-                for (int kb = 0; kb < nkb; ++kb) {
-                    if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) break;
-                    const int seg = kb / kb_per, kx = (kb % kb_per) * BK;
-                    const CUtensorMap *ma = (seg < 2) ? &maps.a_hi : &maps.a_lo;
-                    const CUtensorMap *mb = (seg == 1) ? &maps.b_lo : &maps.b_hi;
-                    mbar_expect_tx(&full[stage], S::kStageA + S::kStageB);
-                    tma_load_2d(sA + stage * S::kStageA, ma, &full[stage], kx, m0);
-                    tma_load_2d(sB + stage * S::kStageB, mb, &full[stage], kx, n0);
-                    armed_mask |= 1u << stage;
-                    armed_phase = (armed_phase & ~(1u << stage)) | (phase << stage);
-                    if (++stage == kStages) {
-                        stage = 0;
-                        phase ^= 1;
+            for (int k = ms.k_first; k < ms.k_end && !*abort_flag; ++k) {
+                if (ms.multi && k > ms.k_first) {
+                    // the previous step's outputs are complete in every CTA
+                    if (!mbar_wait(stepbar, sphase, abort_flag)) break;
+                    sphase ^= 1;
+                    fence_proxy_async_global();
+                }
+                const StepMaps &sm = maps.s[ms.multi ? (k & 1) : 0];
+                for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+                    int tm, tn;
+                    tile_of(t, tiles_m, tiles_n, sym, BN, tm, tn);
+                    const int m0 = tm * BM, n0 = tn * BN;
+                    for (int kb = 0; kb < nkb; ++kb) {
+                        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) break;
+                        const int seg = kb / kb_per, kx = (kb % kb_per) * BK;
+                        const CUtensorMap *ma = (seg < 2) ? &maps.a_hi : &maps.a_lo;
+                        const CUtensorMap *mb = (seg == 1) ? &sm.b_lo : &sm.b_hi;
+                        mbar_expect_tx(&full[stage], S::kStageA + S::kStageB);
+                        tma_load_2d(sA + stage * S::kStageA, ma, &full[stage], kx, m0);
+                        tma_load_2d(sB + stage * S::kStageB, mb, &full[stage], kx, n0);
+                        armed_mask |= 1u << stage;
+                        armed_phase = (armed_phase & ~(1u << stage)) | (phase << stage);
+                        if (++stage == kStages) {
+                            stage = 0;
+                            phase ^= 1;
+                        }
                     }
                 }
             }
@@ -463,32 +508,37 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t phase = 0;
             uint32_t tphase[2] = {0, 0};
             int local = 0;
-            for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++local) {
-                const int buf = local & 1;
-                if (!mbar_wait(&tempty[buf], tphase[buf] ^ 1, abort_flag)) break;
-                tphase[buf] ^= 1;
-                fence_after();
-                const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
-                bool ok = true;
-                for (int kb = 0; kb < nkb; ++kb) {
-                    if (!mbar_wait(&full[stage], phase, abort_flag)) {
+            bool ok = true;
+            for (int k = ms.k_first; k < ms.k_end && ok && !*abort_flag; ++k) {
+                for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++local) {
+                    const int buf = local & 1;
+                    if (!mbar_wait(&tempty[buf], tphase[buf] ^ 1, abort_flag)) {
                         ok = false;
                         break;
                     }
+                    tphase[buf] ^= 1;
                     fence_after();
-                    const uint64_t da = smem_desc(su32(sA + stage * S::kStageA));
-                    const uint64_t db = smem_desc(su32(sB + stage * S::kStageB));
+                    const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
+                    for (int kb = 0; kb < nkb; ++kb) {
+                        if (!mbar_wait(&full[stage], phase, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                        const uint64_t da = smem_desc(su32(sA + stage * S::kStageA));
+                        const uint64_t db = smem_desc(su32(sB + stage * S::kStageB));
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk)
-                        mma_bf16(d_tmem, da + 2 * kk, db + 2 * kk, kIdesc, (kb > 0 || kk > 0) ? 1u : 0u);
-                    mma_commit(&empty[stage]);
-                    if (++stage == kStages) {
-                        stage = 0;
-                        phase ^= 1;
+                        for (int kk = 0; kk < BK / 16; ++kk)
+                            mma_bf16(d_tmem, da + 2 * kk, db + 2 * kk, kIdesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                        mma_commit(&empty[stage]);
+                        if (++stage == kStages) {
+                            stage = 0;
+                            phase ^= 1;
+                        }
                     }
+                    if (!ok) break;
+                    mma_commit(&tfull[buf]);
                 }
-                if (!ok) break;
-                mma_commit(&tfull[buf]);
             }
         }
     } else {
@@ -497,34 +547,95 @@ __global__ void __launch_bounds__(kThreads, 1)
         EpiSmem &es = epi[quarter];
         uint64_t *bar = &ebar[quarter];
         uint32_t ephase = 0;
-        const float ck = e.H ? (float)e.coef[e.k] : 0.f;
         uint32_t tphase[2] = {0, 0};
         int local = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
-            const int buf = local & 1;
-            if (!mbar_wait(&tfull[buf], tphase[buf], abort_flag)) break;
-            tphase[buf] ^= 1;
-            fence_after();
-            int tm, tn;
-            tile_of(t, tiles_m, tiles_n, sym, BN, tm, tn);
-            const int r0 = tm * BM + quarter * 32, n0 = tn * BN;
-            const uint32_t trow = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN);
-#pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
-                float acc[32];
-                tmem_ld32(trow + (uint32_t)(c * 32), acc);
-                const int j0 = n0 + c * 32;
-                if (r0 >= M || j0 >= N) continue;
-                if (sym) {
-                    if (j0 < r0) continue;   // block below the diagonal: written as another block's mirror
-                    epilogue_sym_block(e, maps, ck, M, N, r0, j0, lane, acc, es, bar, ephase, abort_flag);
-                } else {
-                    epilogue_general_block(e, M, N, r0, j0, lane, acc, es);
-                }
+        unsigned int target = 0;
+        bool alive = true;
+        for (int k = ms.k_first; k < ms.k_end && alive; ++k) {
+            Epilogue es_e = e;
+            const int par = ms.multi ? (k & 1) : 0;
+            if (ms.multi) {
+                es_e.D = ms.z[par];
+                es_e.C = (k == 2) ? nullptr : ms.z[par];
+                es_e.C2 = ms.z[par ^ 1];
+                es_e.Dhi = ms.zhi[par];
+                es_e.Dlo = ms.zlo[par];
+                es_e.diag = (k == 2) ? -1.f : 0.f;
+                es_e.k = k;
             }
-            fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[buf]);
+            const float ck = es_e.H ? (float)es_e.coef[es_e.k] : 0.f;
+            for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
+                const int buf = local & 1;
+                int tm, tn;
+                tile_of(t, tiles_m, tiles_n, sym, BN, tm, tn);
+                const int r0 = tm * BM + quarter * 32, n0 = tn * BN;
+                // the first block's inputs do not depend on the accumulator:
+                // load them while the MMAs of this tile are still running
+                int c_pre = -1;
+                if (sym && r0 < M) {
+                    for (int c = 0; c < BN / 32; ++c) {
+                        const int j0 = n0 + c * 32;
+                        if (j0 < N && j0 >= r0) {
+                            c_pre = c;
+                            break;
+                        }
+                    }
+                    if (c_pre >= 0) epilogue_issue_loads(es_e, maps.s[par], maps.h, r0, n0 + c_pre * 32, lane, es, bar);
+                }
+                if (!mbar_wait(&tfull[buf], tphase[buf], abort_flag)) {
+                    alive = false;
+                    break;
+                }
+                tphase[buf] ^= 1;
+                fence_after();
+                const uint32_t trow = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN);
+#pragma unroll 1
+                for (int c = 0; c < BN / 32; ++c) {
+                    float acc[32];
+                    tmem_ld32(trow + (uint32_t)(c * 32), acc);
+                    const int j0 = n0 + c * 32;
+                    if (r0 >= M || j0 >= N) continue;
+                    if (sym) {
+                        if (j0 < r0) continue;   // block below the diagonal: written as another block's mirror
+                        epilogue_sym_block(es_e, maps.s[par], maps.h, ck, M, N, r0, j0, lane, acc, es, bar, ephase,
+                                           abort_flag, c == c_pre);
+                    } else {
+                        epilogue_general_block(es_e, M, N, r0, j0, lane, acc, es);
+                    }
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[buf]);
+            }
+            if (ms.multi && k + 1 < ms.k_end && alive) {
+                // step k done in this CTA: stores complete and ordered for the
+                // async proxy, then one grid-wide barrier, then the producer
+                // may load step k+1's operands
+                if (lane == 0) bulk_wait_all();
+                __syncwarp();
+                fence_proxy_async_global();
+                __threadfence();
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (threadIdx.x == 64) {
+                    target += gridDim.x;
+                    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ms.bar) : "memory");
+                    const long long t0 = clock64();
+                    while (true) {
+                        unsigned int v;
+                        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ms.bar) : "memory");
+                        if (v >= target) break;
+                        if (clock64() - t0 > kWaitCycles) {
+                            *abort_flag = 1;
+                            break;
+                        }
+                    }
+                    fence_proxy_async_global();
+                    mbar_arrive(stepbar);
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                fence_proxy_async_global();
+                if (*abort_flag) alive = false;
+            }
         }
         // the last TMA stores must complete before the CTA exits
         if (lane == 0) bulk_wait_all();
@@ -587,7 +698,7 @@ int *g_err_dev = nullptr;
 
 template <int BN>
 cudaError_t launch(int M, int N, int K, const TcOperand &A, const TcOperand &B, int nsplit, const Epilogue &e,
-                   cudaStream_t st, int num_sms) {
+                   const MultiStep &ms, cudaStream_t st, int num_sms) {
     using S = Smem<BN>;
     static bool attr_set = false;
     if (!attr_set) {
@@ -598,24 +709,56 @@ cudaError_t launch(int M, int N, int K, const TcOperand &A, const TcOperand &B, 
     }
     TileMaps maps;
     memset(&maps, 0, sizeof(maps));
-    const __nv_bfloat16 *alo = A.lo ? A.lo : A.hi, *blo = B.lo ? B.lo : B.hi;
-    if (!make_map(&maps.a_hi, A.hi, A.ld, A.rows, K, BM) || !make_map(&maps.a_lo, alo, A.ld, A.rows, K, BM) ||
-        !make_map(&maps.b_hi, B.hi, B.ld, B.rows, K, BN) || !make_map(&maps.b_lo, blo, B.ld, B.rows, K, BN))
+    const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32, b16 = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const __nv_bfloat16 *alo = A.lo ? A.lo : A.hi;
+    if (!make_map(&maps.a_hi, A.hi, A.ld, A.rows, K, BM) || !make_map(&maps.a_lo, alo, A.ld, A.rows, K, BM))
         return cudaErrorInvalidValue;
-    if (e.symmetric_upper) {
-        const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32, b16 = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-        bool ok = make_block_map(&maps.d, e.D, f32, 4, e.ldd, M, N);
-        if (e.C) ok = ok && make_block_map(&maps.c, e.C, f32, 4, e.ldc, M, N);
-        if (e.C2) ok = ok && make_block_map(&maps.c2, e.C2, f32, 4, e.ldc2, M, N);
-        if (e.H) ok = ok && make_block_map(&maps.h, e.H, f32, 4, e.ldh, M, N);
-        if (e.Dhi) ok = ok && make_block_map(&maps.dhi, e.Dhi, b16, 2, e.ldb, M, N);
-        if (e.Dlo) ok = ok && make_block_map(&maps.dlo, e.Dlo, b16, 2, e.ldb, M, N);
+    if (e.H && !make_block_map(&maps.h, e.H, f32, 4, e.ldh, M, N)) return cudaErrorInvalidValue;
+    for (int par = 0; par < (ms.multi ? 2 : 1); ++par) {
+        StepMaps &sm = maps.s[par];
+        const __nv_bfloat16 *bhi = ms.multi ? ms.zhi[par ^ 1] : B.hi;
+        const __nv_bfloat16 *blo = ms.multi ? ms.zlo[par ^ 1] : B.lo;
+        if (!blo) blo = bhi;
+        bool ok = make_map(&sm.b_hi, bhi, B.ld, B.rows, K, BN) && make_map(&sm.b_lo, blo, B.ld, B.rows, K, BN);
+        if (e.symmetric_upper) {
+            const float *D = ms.multi ? ms.z[par] : e.D;
+            const float *C2 = ms.multi ? ms.z[par ^ 1] : e.C2;
+            __nv_bfloat16 *Dhi = ms.multi ? ms.zhi[par] : e.Dhi;
+            __nv_bfloat16 *Dlo = ms.multi ? ms.zlo[par] : e.Dlo;
+            ok = ok && make_block_map(&sm.d, D, f32, 4, e.ldd, M, N);
+            if (e.C || ms.multi) ok = ok && make_block_map(&sm.c, D, f32, 4, e.ldd, M, N);
+            if (C2) ok = ok && make_block_map(&sm.c2, C2, f32, 4, ms.multi ? e.ldd : e.ldc2, M, N);
+            if (Dhi) ok = ok && make_block_map(&sm.dhi, Dhi, b16, 2, e.ldb, M, N);
+            if (Dlo) ok = ok && make_block_map(&sm.dlo, Dlo, b16, 2, e.ldb, M, N);
+        }
         if (!ok) return cudaErrorInvalidValue;
     }
     const int tiles = count_tiles((M + BM - 1) / BM, (N + BN - 1) / BN, e.symmetric_upper, BN);
     const int grid = tiles < num_sms ? tiles : num_sms;
-    gemm_tc_kernel<BN><<<grid, kThreads, S::kBytes, st>>>(maps, M, N, K, nsplit, e, g_err_dev);
-    return cudaGetLastError();
+    if (!ms.multi) {
+        gemm_tc_kernel<BN><<<grid, kThreads, S::kBytes, st>>>(maps, M, N, K, nsplit, e, ms, g_err_dev);
+        return cudaGetLastError();
+    }
+    cudaError_t r = cudaMemsetAsync(ms.bar, 0, sizeof(unsigned int), st);
+    if (r != cudaSuccess) return r;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = S::kBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<BN>, maps, M, N, K, nsplit, e, ms, g_err_dev);
+}
+
+template <int BN>
+cudaError_t launch(int M, int N, int K, const TcOperand &A, const TcOperand &B, int nsplit, const Epilogue &e,
+                   cudaStream_t st, int num_sms) {
+    MultiStep ms;
+    return launch<BN>(M, N, K, A, B, nsplit, e, ms, st, num_sms);
 }
 
 }  // namespace
@@ -629,6 +772,69 @@ cudaError_t gemm_tc_error_flag(int **flag) {
     }
     *flag = g_err_dev;
     return cudaSuccess;
+}
+
+// Tile width by a small cost model: waves of CTAs times the tile's cost,
+// which grows with BN plus a fixed per-tile overhead of about 64 columns.
+int choose_bn(int M, int N, int sym, int num_sms) {
+    const int cands[4] = {256, 128, 64, 32};
+    int best = 256;
+    long best_cost = -1;
+    const int tm = (M + BM - 1) / BM;
+    for (int bn : cands) {
+        if (bn < 256 && N > 4096 * 2) continue;
+        const int tiles = count_tiles(tm, (N + bn - 1) / bn, sym, bn);
+        const long waves = (tiles + num_sms - 1) / num_sms;
+        const long cost = waves * (bn + 64);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = bn;
+        }
+    }
+    return best;
+}
+
+template <class F>
+cudaError_t dispatch_bn(int bn, F f) {
+    switch (bn) {
+        case 256: return f(std::integral_constant<int, 256>());
+        case 128: return f(std::integral_constant<int, 128>());
+        case 64: return f(std::integral_constant<int, 64>());
+        default: return f(std::integral_constant<int, 32>());
+    }
+}
+
+cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epilogue &e, int k_first, int k_end,
+                               float *const z[2], __nv_bfloat16 *const zhi[2], __nv_bfloat16 *const zlo[2],
+                               unsigned int *bar, cudaStream_t st, int num_sms) {
+    if (p <= 0 || k_end <= k_first) return cudaSuccess;
+    if (!load_encode()) return cudaErrorNotSupported;
+    if ((A.ld % 8) || ((uintptr_t)A.hi % 16) || !e.symmetric_upper || !e.H || !bar) return cudaErrorInvalidValue;
+    if (nsplit == 3 && (!A.lo || !zlo[0] || !zlo[1])) return cudaErrorInvalidValue;
+    if ((e.ldd % 4) || (e.ldh % 4) || (e.ldb % 8)) return cudaErrorInvalidValue;
+    for (int i = 0; i < 2; ++i)
+        if (((uintptr_t)z[i] % 16) || ((uintptr_t)zhi[i] % 16) || (zlo[i] && ((uintptr_t)zlo[i] % 16)))
+            return cudaErrorInvalidValue;
+    int *flag;
+    cudaError_t r = gemm_tc_error_flag(&flag);
+    if (r != cudaSuccess) return r;
+    MultiStep ms;
+    ms.multi = 1;
+    ms.k_first = k_first;
+    ms.k_end = k_end;
+    for (int i = 0; i < 2; ++i) {
+        ms.z[i] = z[i];
+        ms.zhi[i] = zhi[i];
+        ms.zlo[i] = zlo[i];
+    }
+    ms.bar = bar;
+    TcOperand B;
+    B.ld = A.ld;
+    B.rows = p;
+    B.hi = zhi[0];   // per-step operands come from the ring
+    return dispatch_bn(choose_bn(p, p, 1, num_sms), [&](auto bn) {
+        return launch<decltype(bn)::value>(p, p, p, A, B, nsplit, e, ms, st, num_sms);
+    });
 }
 
 cudaError_t gemm_tc(int M, int N, int K, const TcOperand &A, const TcOperand &B, int nsplit, const Epilogue &e,
@@ -652,13 +858,9 @@ cudaError_t gemm_tc(int M, int N, int K, const TcOperand &A, const TcOperand &B,
     int *flag;
     cudaError_t r = gemm_tc_error_flag(&flag);
     if (r != cudaSuccess) return r;
-    // tile width: the widest whose tile count still fills the SMs
-    const int tm = (M + BM - 1) / BM, sym = e.symmetric_upper;
-    if (count_tiles(tm, (N + 255) / 256, sym, 256) >= num_sms || N > 4096)
-        return launch<256>(M, N, K, A, B, nsplit, e, st, num_sms);
-    if (count_tiles(tm, (N + 127) / 128, sym, 128) >= num_sms)
-        return launch<128>(M, N, K, A, B, nsplit, e, st, num_sms);
-    return launch<64>(M, N, K, A, B, nsplit, e, st, num_sms);
+    return dispatch_bn(choose_bn(M, N, e.symmetric_upper, num_sms), [&](auto bn) {
+        return launch<decltype(bn)::value>(M, N, K, A, B, nsplit, e, st, num_sms);
+    });
 }
 
 }  // namespace cpa

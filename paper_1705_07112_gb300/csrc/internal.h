@@ -96,6 +96,15 @@ struct TcOperand {
 cudaError_t gemm_tc(int M, int N, int K, const TcOperand &A, const TcOperand &B, int nsplit,
                     const Epilogue &e, cudaStream_t st, int num_sms);
 
+// All recurrence steps k_first <= k < k_end in one cooperative launch (grid
+// barrier between steps).  A: the At operand.  e: the step-independent
+// epilogue fields (s_acc, s_c, s_c2, H, ldh, coef, ldd, ldb, symmetric_upper).
+// Step k writes Psi_k over Psi_{k-2} in z[k&1] and its BF16 copies in
+// zhi/zlo[k&1]; it reads Psi_{k-1} from slot (k&1)^1.  bar: one device word.
+cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epilogue &e, int k_first, int k_end,
+                               float *const z[2], __nv_bfloat16 *const zhi[2], __nv_bfloat16 *const zlo[2],
+                               unsigned int *bar, cudaStream_t st, int num_sms);
+
 // Elementwise conversion of a row-major FP32 matrix to BF16 hi/lo parts,
 // optionally transposed (out is cols x rows then).
 cudaError_t split_bf16(const float *X, int rows, int cols, int64_t ldx, bool transpose,

@@ -289,7 +289,10 @@ __device__ __forceinline__ void grid_barrier(unsigned int *count, unsigned int &
 __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__restrict__ G, int64_t ldg, int p,
                                                                int iters, uint64_t seed, float *v0, float *v1,
                                                                double *norm2, unsigned int *bar, double margin,
-                                                               double *out, int *err) {
+                                                               double *out, int *err, int cache) {
+    // cache != 0: every warp owns at most one row of G and keeps it in
+    // shared memory for all iterations (row stride p rounded up to 4)
+    extern __shared__ __align__(16) float grow[];
     unsigned int target = 0;
     const int lane = threadIdx.x & 31;
     const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -297,6 +300,10 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
     // start vector and its norm (block 0), slots cleared
     if (blockIdx.x == 0) {
         double sacc = 0.0;
+        for (int i = p + threadIdx.x; i < ((p + 3) & ~3); i += blockDim.x) {
+            v0[i] = 0.f;   // float4 padding of both vectors
+            v1[i] = 0.f;
+        }
         for (int i = threadIdx.x; i < p; i += blockDim.x) {
             uint64_t z = splitmix64_output(seed, (uint64_t)i);
             float x = (float)((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
@@ -306,6 +313,12 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
         for (int i = threadIdx.x + 1; i < iters + 2; i += blockDim.x) norm2[i] = 0.0;
         sacc = block_sum(sacc);
         if (threadIdx.x == 0) norm2[0] = sacc;
+    }
+    const int p4 = (p + 3) & ~3;
+    float *myrow = grow + (threadIdx.x >> 5) * p4;
+    if (cache && gwarp < p) {
+        const float *g = G + (int64_t)gwarp * ldg;
+        for (int j = lane; j < p4; j += 32) myrow[j] = j < p ? __ldg(g + j) : 0.f;
     }
     grid_barrier(bar, target, err);
     const bool vec = (ldg & 3) == 0 && (p & 3) == 0 && ((uintptr_t)G & 15) == 0;
@@ -318,7 +331,25 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
         for (int row = gwarp; row < p; row += nwarps) {
             const float *g = G + (int64_t)row * ldg;
             float acc = 0.f;
-            if (vec) {
+            if (cache) {
+                const float4 *g4 = reinterpret_cast<const float4 *>(myrow);
+                const float4 *v4 = reinterpret_cast<const float4 *>(v);
+                const int n4 = p4 >> 2;
+                for (int j0 = lane; j0 < n4; j0 += 32 * 8) {
+                    float4 a[8], b[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int j = j0 + 32 * u;
+                        a[u] = j < n4 ? g4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        b[u] = j < n4 ? __ldcg(v4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        acc = fmaf(a[u].x, b[u].x, acc); acc = fmaf(a[u].y, b[u].y, acc);
+                        acc = fmaf(a[u].z, b[u].z, acc); acc = fmaf(a[u].w, b[u].w, acc);
+                    }
+                }
+            } else if (vec) {
                 const float4 *g4 = reinterpret_cast<const float4 *>(g);
                 const float4 *v4 = reinterpret_cast<const float4 *>(v);
                 const int n4 = p >> 2;
@@ -411,10 +442,22 @@ cudaError_t power_bound_persistent(const float *G, int64_t ldg, int p, int iters
     const int rows_per_block = 16;   // warps per block
     if (grid > (p + rows_per_block - 1) / rows_per_block) grid = (p + rows_per_block - 1) / rows_per_block;
     if (grid < 1) grid = 1;
+    const int p4 = (p + 3) & ~3;
+    const size_t cache_bytes = (size_t)16 * p4 * sizeof(float);
+    const int cache = ((int64_t)grid * 16 >= p && cache_bytes <= 200 * 1024) ? 1 : 0;
+    if (cache) {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t ra = cudaFuncSetAttribute(power_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  200 * 1024);
+            if (ra != cudaSuccess) return ra;
+            attr = true;
+        }
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(512);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = cache ? cache_bytes : 0;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -424,7 +467,7 @@ cudaError_t power_bound_persistent(const float *G, int64_t ldg, int p, int iters
     const double margin = kLambdaMargin;
     const uint64_t seed = kStartSeed;
     return cudaLaunchKernelEx(&cfg, power_persistent_kernel, G, ldg, p, iters, seed, v0, v1, norm2, bar, margin, out,
-                              err);
+                              err, cache);
 }
 
 cudaError_t power_bound(const float *G, int64_t ldg, int p, int iters, float *v0, float *v1,
