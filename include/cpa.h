@@ -84,7 +84,17 @@ typedef struct {
 
 /* Optional sparsity-based reduction (Eqs. sing_shrink_exact_sparse and
  * threshold_components): Phi = T G T^T, entries with |Phi_ij| < eps set to 0,
- * result X T^T H_hat(Phi_) T.  Pass NULL for "off" (T = Id, no threshold). */
+ * result X T^T H_hat(Phi_) T (T^T H_hat T X for m < n).  Pass NULL for "off"
+ * (T = Id, no threshold).  Transforms (p x p):
+ *   HAAR1_LOWPASS: row i < floor(p/2) holds 1/sqrt2 at columns 2i, 2i+1; for
+ *     odd p row floor(p/2) holds 1 at column p-1; the high band rows are 0.
+ *   BLOCK_DCT8: block-diagonal orthonormal DCT-II, 8 x 8 blocks (the last
+ *     block p mod 8 wide when that is not 0).
+ *   DCT: orthonormal DCT-II, T[k][j] = s_k cos(pi (2j+1) k / 2p), s_0 =
+ *     sqrt(1/p), s_k = sqrt(2/p).
+ * Modes: ABS keeps |Phi_ij| >= eps_or_frac (>= 0); TOPK sets eps to the k-th
+ * largest |Phi_ij|, k = ceil(frac p^2) in [1, p^2] (0 < frac <= 1), and keeps
+ * the entries >= eps.  Phi, T and T^T H T are formed in FP32 on the device. */
 typedef enum {
     CPA_T_IDENTITY = 0,
     CPA_T_HAAR1_LOWPASS = 1,   /* one-level Haar DWT, high band set to zero     */
@@ -176,7 +186,8 @@ typedef enum {
     CPA_STAGE_SHIFT = 4,   /* B_hat, Psi_1 and the initial sum               */
     CPA_STAGE_RECUR = 5,   /* recurrence products with fused accumulation    */
     CPA_STAGE_APPLY = 6,   /* final product                                  */
-    CPA_NSTAGES = 7
+    CPA_STAGE_SPARSE = 7,  /* transform, entry threshold, T^T H T            */
+    CPA_NSTAGES = 8
 } cpa_stage;
 
 CPA_API cpa_status cpa_profile_enable(cpa_handle h, int enable);

@@ -14,6 +14,7 @@ Functions and the passage each follows:
 * ``series_cos`` / ``series_rec``  truncated series, Eqs. chebychev_series,
                           chebychev_polynomial and chebyche2
 * ``gram``                Gram matrix of the smaller side (Algorithm 1, T = Id)
+* ``phi``                 T G T^T (Eq. sing_shrink_exact_sparse), no threshold
 * ``cpa``                 Algorithm 1, dense, optional transform T and entry
                           threshold (Eqs. sing_shrink_exact_sparse,
                           threshold_components, recurrence_our_method, SVD_fil)
@@ -74,6 +75,7 @@ def _load():
                 "orc_series_rec": (_d, [_P, _i, _d]),
                 "orc_cheb_T": (_d, [_i, _d]),
                 "orc_gram": (None, [_P, _i, _i, _P]),
+                "orc_phi": (None, [_P, _i, _i, _P, _P]),
                 "orc_cpa": (_i, [_P, _i, _i, _i, _d, _d, _d, _d, _i, _d, _P, _d, _P, _P]),
                 "orc_cpa_vec": (_i, [_P, _i, _i, _i, _d, _d, _d, _d, _i, _d, _P, _P]),
                 "orc_lambda_bound": (_i, [_P, _i, _i, _i, _d, _P, _P]),
@@ -161,6 +163,17 @@ def gram(X) -> np.ndarray:
     G = np.zeros((p, p))
     _load().orc_gram(_p(X), m, n, _p(G))
     return G
+
+
+def phi(X, T=None) -> np.ndarray:
+    """Phi = T G T^T before thresholding (Eq. sing_shrink_exact_sparse)."""
+    X = _arr(X)
+    m, n = X.shape
+    p = min(m, n)
+    Tm = _arr(T, (p, p)) if T is not None else None
+    out = np.zeros((p, p))
+    _load().orc_phi(_p(X), m, n, _p(Tm), _p(out))
+    return out
 
 
 def cpa(X, s: Shrink, alpha: int, lam: float, T=None, eps_thr: float = -1.0,

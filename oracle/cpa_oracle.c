@@ -209,6 +209,24 @@ void orc_gram(const double *X, int m, int n, double *G)
     }
 }
 
+/* Transformed Gram matrix Phi = T G T^T of the smaller side (Eq.
+ * sing_shrink_exact_sparse), before any entry threshold; T NULL = Id. */
+void orc_phi(const double *X, int m, int n, const double *T, double *Phi)
+{
+    int p = m < n ? m : n;
+    size_t pp = (size_t)p * p;
+    orc_gram(X, m, n, Phi);
+    if (T) {
+        double *Tt = malloc(pp * sizeof(double));
+        double *tmp = malloc(pp * sizeof(double));
+        transpose(T, Tt, p, p);
+        matmul(T, Phi, tmp, p, p, p);
+        matmul(tmp, Tt, Phi, p, p, p);
+        free(Tt);
+        free(tmp);
+    }
+}
+
 /* ------------------------------------------------------------------------- */
 /* Algorithm 1: CPA-based singular value shrinkage, dense.                   */
 /*                                                                           */

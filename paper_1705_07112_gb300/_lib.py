@@ -25,7 +25,9 @@ EXPORTS = ["cpa_create", "cpa_destroy", "cpa_status_string", "cpa_last_error", "
            "cpa_batch_destroy", "cpa_svt_batched", "cpa_batch_lambdas", "cpa_profile_enable",
            "cpa_profile_read", "cpa_kernel_gemm_bf16", "cpa_kernel_split_bf16", "cpa_batch_read_lambdas",
            "cpa_lambda_bound_noalloc"]
-STAGES = ["prep", "gram", "bound", "coeff", "shift", "recur", "apply"]
+STAGES = ["prep", "gram", "bound", "coeff", "shift", "recur", "apply", "sparse"]
+T_IDENTITY, T_HAAR1_LOWPASS, T_BLOCK_DCT8, T_DCT = 0, 1, 2, 3
+SPARSE_OFF, SPARSE_ABS, SPARSE_TOPK = 0, 1, 2
 
 
 class CpaShrink(ctypes.Structure):

@@ -164,6 +164,9 @@ bool ranges_overlap(const void *a, size_t abytes, const void *b, size_t bbytes) 
 // Workspace pieces of one single-matrix shrinkage.
 struct SvtWs {
     int64_t ldp = 0;
+    float *T = nullptr;                 // sparsify transform (when requested)
+    float *eps = nullptr;
+    unsigned long long *counts = nullptr;
     float *G = nullptr, *A = nullptr, *Z[2] = {nullptr, nullptr}, *H = nullptr, *v0 = nullptr, *v1 = nullptr;
     double *out = nullptr, *norm2 = nullptr, *coef = nullptr;
     int *flag = nullptr;
@@ -174,7 +177,7 @@ struct SvtWs {
     size_t bytes = 0;
 };
 
-SvtWs carve(char *base, int64_t m, int64_t n, int L, int iters, int prec) {
+SvtWs carve(char *base, int64_t m, int64_t n, int L, int iters, int prec, bool sparse = false) {
     SvtWs w;
     int64_t p = std::min(m, n);
     w.ldp = round_up(p, 8);
@@ -183,7 +186,7 @@ SvtWs carve(char *base, int64_t m, int64_t n, int L, int iters, int prec) {
     w.out = c.take<double>(8);
     w.norm2 = c.take<double>(iters + 2);
     w.coef = c.take<double>(std::max(L, 2));
-    w.flag = c.take<int>(4);
+    w.flag = c.take<int>(8);
     w.G = c.take<float>(pp);
     w.A = c.take<float>(pp);
     w.Z[0] = c.take<float>(pp);
@@ -191,6 +194,11 @@ SvtWs carve(char *base, int64_t m, int64_t n, int L, int iters, int prec) {
     w.H = c.take<float>(pp);
     w.v0 = c.take<float>(round_up(p, 4));
     w.v1 = c.take<float>(round_up(p, 4));
+    if (sparse) {
+        w.T = c.take<float>(pp);
+        w.eps = c.take<float>(4);
+        w.counts = c.take<unsigned long long>(32);
+    }
     if (prec != CPA_FP32) {
         // Gram and final product always use the hi/lo split (their BF16
         // rounding would otherwise dominate the error); the recurrence
@@ -376,7 +384,15 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
     if ((s = check_shrink(sh)) != CPA_OK) return s;
     if (!std::isfinite(lambda_max)) return CPA_ERR_INVALID_ARG;
     if (prec < CPA_FP32 || prec > CPA_BF16X3) return CPA_ERR_INVALID_ARG;
-    if (sp && (sp->transform != CPA_T_IDENTITY || sp->mode != CPA_SPARSE_OFF)) return CPA_ERR_UNSUPPORTED;
+    const bool sparse = sp && (sp->transform != CPA_T_IDENTITY || sp->mode != CPA_SPARSE_OFF);
+    if (sp) {
+        if (sp->transform < CPA_T_IDENTITY || sp->transform > CPA_T_DCT || sp->mode < CPA_SPARSE_OFF ||
+            sp->mode > CPA_SPARSE_TOPK || !std::isfinite(sp->eps_or_frac))
+            return CPA_ERR_INVALID_ARG;
+        if (sp->mode == CPA_SPARSE_ABS && !(sp->eps_or_frac >= 0.0)) return CPA_ERR_INVALID_ARG;
+        if (sp->mode == CPA_SPARSE_TOPK && !(sp->eps_or_frac > 0.0 && sp->eps_or_frac <= 1.0))
+            return CPA_ERR_INVALID_ARG;
+    }
     if (ranges_overlap(dX, (size_t)((m - 1) * ldx + n) * sizeof(float), dY,
                        (size_t)((m - 1) * ldy + n) * sizeof(float)))
         return CPA_ERR_INVALID_ARG;
@@ -385,9 +401,9 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
     if ((s = set_device(h)) != CPA_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     const int iters = kDefaultPowerIters;
-    SvtWs w = carve(nullptr, m, n, L, iters, prec);
+    SvtWs w = carve(nullptr, m, n, L, iters, prec, sparse);
     if ((s = ensure_ws(h, w.bytes, st)) != CPA_OK) return s;
-    w = carve(h->ws, m, n, L, iters, prec);
+    w = carve(h->ws, m, n, L, iters, prec, sparse);
     const int64_t p = std::min(m, n);
     const bool tc = prec != CPA_FP32;
     // Gram and final product: always split.  Recurrence: split in BF16X3
@@ -407,6 +423,33 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
     {
         StageScope sc(h, CPA_STAGE_GRAM, st, 1);
         if ((s = run_gram(h, dX, m, n, ldx, w, prec, st)) != CPA_OK) return s;
+    }
+    // sparsity-based reduction: Phi = T G T^T, entries below eps set to zero
+    if (sparse) {
+        StageScope sc(h, CPA_STAGE_SPARSE, st, 0);
+        CK(make_transform(sp->transform, (int)p, w.T, w.ldp, st, h->num_sms));
+        Epilogue e1;
+        e1.D = w.A;   // T G (w.A is free until the shift)
+        e1.ldd = w.ldp;
+        CK(gemm_f32((int)p, (int)p, (int)p, w.T, w.ldp, true, w.G, w.ldp, true, e1, st));
+        Epilogue e2;
+        e2.D = w.G;   // (T G) T^T, exactly symmetric
+        e2.ldd = w.ldp;
+        e2.symmetric_upper = 1;
+        CK(gemm_f32((int)p, (int)p, (int)p, w.A, w.ldp, true, w.T, w.ldp, true, e2, st));
+        h->launches[CPA_STAGE_SPARSE] += 3;
+        if (sp->mode == CPA_SPARSE_ABS) {
+            CK(threshold_entries(w.G, (int)p, w.ldp, nullptr, (float)sp->eps_or_frac, st, h->num_sms));
+            h->launches[CPA_STAGE_SPARSE] += 1;
+        } else if (sp->mode == CPA_SPARSE_TOPK) {
+            const double pp2 = (double)p * (double)p;
+            long long k = (long long)std::ceil(sp->eps_or_frac * pp2);
+            k = std::max(1LL, std::min(k, (long long)pp2));
+            CK(topk_eps(w.G, (int)p, w.ldp, k, w.counts, (unsigned int *)(w.flag + 3), w.flag + 4, w.eps, st,
+                        h->num_sms));
+            CK(threshold_entries(w.G, (int)p, w.ldp, w.eps, 0.f, st, h->num_sms));
+            h->launches[CPA_STAGE_SPARSE] += 2;
+        }
     }
     // interval bound
     if (lambda_max > 0.0) {
@@ -486,6 +529,22 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
             CK(gemm_tc((int)p, (int)p, (int)p, a, b, nsplit_rec, e, st, h->num_sms));
         }
     }
+    // with the sparsity option the filter applied to X is T^T H T (Eq. SVD_fil)
+    float *Hf = w.H;
+    if (sparse) {
+        StageScope sc(h, CPA_STAGE_SPARSE, st, 2 + (tc ? 1 : 0));
+        if (tc) CK(symmetrize_lower(w.H, (int)p, w.ldp, st, h->num_sms));
+        Epilogue e1;
+        e1.D = w.Z[0];   // T^T H
+        e1.ldd = w.ldp;
+        CK(gemm_f32((int)p, (int)p, (int)p, w.T, w.ldp, false, w.H, w.ldp, true, e1, st));
+        Epilogue e2;
+        e2.D = w.Z[1];   // (T^T H) T
+        e2.ldd = w.ldp;
+        e2.symmetric_upper = 1;
+        CK(gemm_f32((int)p, (int)p, (int)p, w.Z[0], w.ldp, true, w.T, w.ldp, false, e2, st));
+        Hf = w.Z[1];
+    }
     // final product: Y = X H (m >= n) or H X (m < n)
     StageScope sc(h, CPA_STAGE_APPLY, st, tc ? 2 : 1);
     Epilogue e;
@@ -493,13 +552,17 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
     e.ldd = ldy;
     if (!tc) {
         if (m >= n)
-            CK(gemm_f32((int)m, (int)n, (int)n, dX, ldx, true, w.H, w.ldp, true, e, st));
+            CK(gemm_f32((int)m, (int)n, (int)n, dX, ldx, true, Hf, w.ldp, true, e, st));
         else
-            CK(gemm_f32((int)m, (int)n, (int)m, w.H, w.ldp, true, dX, ldx, false, e, st));
+            CK(gemm_f32((int)m, (int)n, (int)m, Hf, w.ldp, true, dX, ldx, false, e, st));
     } else {
         // H is valid in its lower triangle (the tensor-core epilogue keeps
-        // the FP32 arrays there); the split writes both triangles
-        CK(split_sym_lower(w.H, (int)p, w.ldp, w.Hhi, w.Hlo, w.ldp, st));
+        // the FP32 arrays there); the split writes both triangles.  The
+        // transformed filter is full and split as it is.
+        if (sparse)
+            CK(split_bf16(Hf, (int)p, (int)p, w.ldp, false, w.Hhi, w.Hlo, w.ldp, st));
+        else
+            CK(split_sym_lower(w.H, (int)p, w.ldp, w.Hhi, w.Hlo, w.ldp, st));
         TcOperand hop, xop;
         hop.hi = w.Hhi; hop.lo = w.Hlo; hop.ld = w.ldp; hop.rows = (int)p;
         if (m >= n) {   // Y(r,j) = sum_l X[r][l] H[j][l]

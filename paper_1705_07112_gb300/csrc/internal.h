@@ -105,6 +105,14 @@ cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epil
                                float *const z[2], __nv_bfloat16 *const zhi[2], __nv_bfloat16 *const zlo[2],
                                unsigned int *bar, cudaStream_t st, int num_sms);
 
+// Sparsity-based reduction helpers (sparsify.cu).
+cudaError_t make_transform(int type, int p, float *T, int64_t ld, cudaStream_t st, int num_sms);
+cudaError_t threshold_entries(float *Phi, int p, int64_t ld, const float *eps_dev, float eps_host, cudaStream_t st,
+                              int num_sms);
+cudaError_t symmetrize_lower(float *S, int p, int64_t ld, cudaStream_t st, int num_sms);
+cudaError_t topk_eps(const float *Phi, int p, int64_t ld, long long k, unsigned long long *counts, unsigned int *bar,
+                     int *err, float *eps_out, cudaStream_t st, int num_sms);
+
 // Elementwise conversion of a row-major FP32 matrix to BF16 hi/lo parts,
 // optionally transposed (out is cols x rows then).
 cudaError_t split_bf16(const float *X, int rows, int cols, int64_t ldx, bool transpose,

@@ -311,3 +311,11 @@ def test_start_vector_is_splitmix64():
     first = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
     want = [(z >> 11) / 2.0 ** 53 - 0.5 for z in first]
     assert np.allclose(O.start_vector(0, 3), want, atol=0)
+
+
+def test_phi_is_the_transformed_gram():
+    X = RNG.standard_normal((11, 7))
+    T = rand_orth(RNG, 7)
+    assert np.allclose(O.phi(X), X.T @ X, atol=1e-12)
+    assert np.allclose(O.phi(X, T), T @ X.T @ X @ T.T, atol=1e-12)
+    assert np.allclose(O.phi(X.T, T), T @ X.T @ X @ T.T, atol=1e-12)
