@@ -245,6 +245,38 @@ CPA_API cpa_status cpa_lambda_bound_noalloc(const float *dX, int64_t m, int64_t 
                                             double *lambda_out, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Learned predictor network (no counterpart in the paper: it chooses
+ * Lambda_max and L for Algorithm 1 from cheap features).  A fully connected
+ * in -> h1 -> h2 -> out network, ReLU hidden layers, FP32, widths <= 128.
+ * Parameters, one FP32 array: W1[h1][in], b1[h1], W2[h2][h1], b2[h2],
+ * W3[out][h2], b3[out].  Loss of a batch of B samples:
+ *   (1/2B) sum_b sum_o (y_bo - t_bo)^2.
+ * Training updates with Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias
+ * corrected, step t counted from 1 per network) and decoupled weight decay:
+ *   m <- b1 m + (1-b1) g,  v <- b2 v + (1-b2) g^2,
+ *   P <- P - lr (m/(1-b1^t) / (sqrt(v/(1-b2^t)) + eps) + weight_decay P).
+ * dX: device [B][in], dY / dT: device [B][out].
+ * ------------------------------------------------------------------------- */
+typedef struct cpa_mlp_ctx *cpa_mlp;
+
+/* Creates the network on the current device; weights uniform with variance
+ * 2/fan_in from SplitMix64(seed), biases 0. */
+CPA_API cpa_status cpa_mlp_create(cpa_mlp *out, int in, int h1, int h2, int out_dim, uint64_t seed);
+CPA_API cpa_status cpa_mlp_destroy(cpa_mlp m);
+CPA_API int64_t cpa_mlp_param_count(cpa_mlp m);
+CPA_API cpa_status cpa_mlp_set_params(cpa_mlp m, const float *host, int64_t count);
+CPA_API cpa_status cpa_mlp_get_params(cpa_mlp m, float *host, int64_t count);
+CPA_API cpa_status cpa_mlp_forward(cpa_mlp m, const float *dX, int batch, float *dY, void *stream);
+/* Loss gradient with respect to every parameter (host copy) and the loss;
+ * synchronises `stream`. */
+CPA_API cpa_status cpa_mlp_gradients(cpa_mlp m, const float *dX, const float *dT, int batch, float *host_grad,
+                                     int64_t count, float *host_loss, void *stream);
+/* One Adam step on a batch (lr > 0, weight_decay >= 0); host_loss
+ * (optional, synchronises) receives the batch loss before the step. */
+CPA_API cpa_status cpa_mlp_train_step(cpa_mlp m, const float *dX, const float *dT, int batch, float lr,
+                                      float weight_decay, float *host_loss, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Batched shrinkage of many small independent matrices (patch groups), one
  * persistent launch.  The matrices live packed in one device buffer: matrix
  * i starts at element offset off[i] and is row-major m[i] x n[i] with
@@ -286,6 +318,43 @@ CPA_API const double *cpa_batch_lambdas(cpa_batch b);
 /* Copies those count values to host memory (synchronises `stream`); also
  * returns CPA_ERR_NONFINITE if a computed bound met a NaN/Inf. */
 CPA_API cpa_status cpa_batch_read_lambdas(cpa_batch b, double *host_out, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned choice of (Lambda_max, L) for a batch (no counterpart in the
+ * paper).  Features of matrix i (12 floats, dF[i][0..11]), with G its Gram
+ * matrix, E = trace G = |X|_F^2, theta_t the Rayleigh quotient of the power
+ * iterate after t-1 steps from the SplitMix64 start vector (t products with
+ * G, so theta_t <= Lambda_max), r_4 = |G v - theta_4 v| for that unit
+ * iterate, lambda_min the Rayleigh quotient after 4 steps
+ * u <- (theta_4 I - G) u / |.| from the SplitMix64 vector of seed
+ * (0x1705071120000000 xor 0x5EED), thr the threshold on sigma (weighted
+ * soft: w at sigma^2 = theta_4), each of theta_4, lambda_min, thr^2 and
+ * |G|_F^2 clamped below by 1e-30 E (1e-30 E^2):
+ *   log p, log(q/p), log(E/theta_4), log(thr^2/theta_4),
+ *   log(lambda_min/theta_4), log(thr^2/lambda_min), log(|G|_F^2/theta_4^2),
+ *   log(E/(p thr^2)), log(theta_4/theta_2), log((theta_4 + r_4)/theta_4),
+ *   [kind == HARD], [kind == WSOFT];   dTheta[i] = theta_4.
+ * cpa_svt_batched_learned is one persistent launch that, per matrix,
+ * computes the same features, runs the 12 -> 64 -> 64 -> 2 network `net`
+ * (outputs y0 ~ log(sigma_max^2/theta_4), y1 ~ log L*; same FP32 results as
+ * cpa_mlp_forward on the features) and shrinks with
+ *   L = ceil(exp(y1) L_scale), at least L_min; L_fallback above L_max;
+ *   Lambda_max = the 20-step power-iteration bound of cpa_lambda_bound, or,
+ *     with use_lambda != 0, the prediction theta_4 exp(max(y0, 0))
+ *     (1 + margin) (a prediction below sigma_max^2 makes the series
+ *     diverge: opt in only with a network whose errors are known to be
+ *     small); a non-finite prediction falls back to the bound and
+ *     L_fallback.
+ * L_scale > 0, margin >= 0, 1 <= L_min <= L_max <= 128, 1 <= L_fallback <=
+ * 128, else CPA_ERR_INVALID_ARG.  cpa_batch_read_choices returns the L used
+ * per matrix and the number of fallbacks of the last learned run. */
+CPA_API cpa_status cpa_batch_features(cpa_handle h, cpa_batch b, const float *dX, const cpa_shrink *s, int s_count,
+                                      float *dF, double *dTheta, void *stream);
+CPA_API cpa_status cpa_svt_batched_learned(cpa_handle h, cpa_batch b, cpa_mlp net, const float *dX,
+                                           const cpa_shrink *s, int s_count, double L_scale, int L_min, int L_max,
+                                           int L_fallback, int use_lambda, double margin, int prec, float *dY,
+                                           void *stream);
+CPA_API cpa_status cpa_batch_read_choices(cpa_batch b, int *host_L, int *host_fallbacks, void *stream);
 
 #ifdef __cplusplus
 }

@@ -24,7 +24,9 @@ EXPORTS = ["cpa_create", "cpa_destroy", "cpa_status_string", "cpa_last_error", "
            "cpa_lambda_bound", "cpa_svt", "cpa_get_lambda", "cpa_get_coeffs", "cpa_batch_create",
            "cpa_batch_destroy", "cpa_svt_batched", "cpa_batch_lambdas", "cpa_profile_enable",
            "cpa_profile_read", "cpa_kernel_gemm_bf16", "cpa_kernel_split_bf16", "cpa_batch_read_lambdas",
-           "cpa_lambda_bound_noalloc"]
+           "cpa_lambda_bound_noalloc", "cpa_mlp_create", "cpa_mlp_destroy", "cpa_mlp_param_count",
+           "cpa_mlp_set_params", "cpa_mlp_get_params", "cpa_mlp_forward", "cpa_mlp_gradients",
+           "cpa_mlp_train_step", "cpa_batch_features", "cpa_svt_batched_learned", "cpa_batch_read_choices"]
 STAGES = ["prep", "gram", "bound", "coeff", "shift", "recur", "apply", "sparse"]
 T_IDENTITY, T_HAAR1_LOWPASS, T_BLOCK_DCT8, T_DCT = 0, 1, 2, 3
 SPARSE_OFF, SPARSE_ABS, SPARSE_TOPK = 0, 1, 2
@@ -78,6 +80,22 @@ def load(path: str = LIB_PATH):
             "cpa_batch_lambdas": (_vp, [_vp]),
             "cpa_batch_read_lambdas": (ctypes.c_int, [_vp, _P(_d), _vp]),
             "cpa_lambda_bound_noalloc": (ctypes.c_int, [_vp, _i64, _i64, _i64, ctypes.c_int, _P(_d), _vp]),
+            "cpa_mlp_create": (ctypes.c_int, [_P(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_uint64]),
+            "cpa_mlp_destroy": (ctypes.c_int, [_vp]),
+            "cpa_batch_features": (ctypes.c_int, [_vp, _vp, _vp, _P(CpaShrink), ctypes.c_int, _vp, _vp, _vp]),
+            "cpa_svt_batched_learned": (ctypes.c_int, [_vp, _vp, _vp, _vp, _P(CpaShrink), ctypes.c_int, _d,
+                                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _d,
+                                                       ctypes.c_int, _vp, _vp]),
+            "cpa_batch_read_choices": (ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_int), _vp]),
+            "cpa_mlp_param_count": (_i64, [_vp]),
+            "cpa_mlp_set_params": (ctypes.c_int, [_vp, _P(ctypes.c_float), _i64]),
+            "cpa_mlp_get_params": (ctypes.c_int, [_vp, _P(ctypes.c_float), _i64]),
+            "cpa_mlp_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp]),
+            "cpa_mlp_gradients": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _P(ctypes.c_float), _i64,
+                                                 _P(ctypes.c_float), _vp]),
+            "cpa_mlp_train_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                                                  _P(ctypes.c_float), _vp]),
             "cpa_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
             "cpa_kernel_gemm_bf16": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _i64, _vp,
                                                     _vp, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_float, _vp,
@@ -317,14 +335,128 @@ def cpa_svt_batched(h: Handle, plan: BatchPlan, X, shrink, lambdas=None, iters: 
         raise ValueError("X must be a contiguous float32 CUDA tensor covering the plan")
     if Y is None:
         Y = torch.empty_like(X)
-    specs = shrink if isinstance(shrink, (list, tuple)) else [shrink]
-    arr = (CpaShrink * len(specs))(*[_as_shrink(x) for x in specs])
+    arr, k = _shrink_array(shrink)
     lam = None
     if lambdas is not None:
         if not (lambdas.is_cuda and lambdas.dtype == torch.float64 and lambdas.numel() == plan.count):
             raise ValueError("lambdas must be a float64 CUDA tensor of plan.count values")
         lam = ctypes.c_void_p(lambdas.data_ptr())
     p = PREC[prec] if isinstance(prec, str) else int(prec)
-    _check(load().cpa_svt_batched(h.ptr, plan.ptr, ctypes.c_void_p(X.data_ptr()), arr, len(specs), lam, int(iters),
+    _check(load().cpa_svt_batched(h.ptr, plan.ptr, ctypes.c_void_p(X.data_ptr()), arr, k, lam, int(iters),
                                   p, ctypes.c_void_p(Y.data_ptr()), _stream_ptr(stream)), "cpa_svt_batched")
     return Y
+
+
+class MLP:
+    """The predictor network (cpa_mlp): forward, gradients and Adam steps
+    run in the library's kernels."""
+
+    def __init__(self, sizes=(12, 64, 64, 2), seed: int = 1):
+        self._lib = load()
+        self.sizes = tuple(int(x) for x in sizes)
+        ptr = ctypes.c_void_p()
+        _check(self._lib.cpa_mlp_create(ctypes.byref(ptr), *self.sizes, ctypes.c_uint64(seed)), "cpa_mlp_create")
+        self.ptr = ptr
+        self.count = int(self._lib.cpa_mlp_param_count(self.ptr))
+
+    def close(self):
+        if self.ptr:
+            self._lib.cpa_mlp_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.count, dtype=np.float32)
+        _check(self._lib.cpa_mlp_get_params(self.ptr, out.ctypes.data_as(_P(ctypes.c_float)), self.count),
+               "cpa_mlp_get_params")
+        return out
+
+    def set_params(self, params):
+        arr = np.ascontiguousarray(params, dtype=np.float32)
+        _check(self._lib.cpa_mlp_set_params(self.ptr, arr.ctypes.data_as(_P(ctypes.c_float)), self.count),
+               "cpa_mlp_set_params")
+
+    def forward(self, X, Y=None, stream=None):
+        import torch
+        if Y is None:
+            Y = torch.empty((X.shape[0], self.sizes[-1]), dtype=torch.float32, device=X.device)
+        _check(self._lib.cpa_mlp_forward(self.ptr, ctypes.c_void_p(X.data_ptr()), X.shape[0],
+                                         ctypes.c_void_p(Y.data_ptr()), _stream_ptr(stream)), "cpa_mlp_forward")
+        return Y
+
+    def gradients(self, X, T, stream=None):
+        g = np.zeros(self.count, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(self._lib.cpa_mlp_gradients(self.ptr, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+                                           X.shape[0], g.ctypes.data_as(_P(ctypes.c_float)), self.count,
+                                           ctypes.byref(loss), _stream_ptr(stream)), "cpa_mlp_gradients")
+        return g, loss.value
+
+    def train_step(self, X, T, lr, weight_decay=0.0, want_loss=False, stream=None):
+        loss = ctypes.c_float()
+        _check(self._lib.cpa_mlp_train_step(self.ptr, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+                                            X.shape[0], float(lr), float(weight_decay),
+                                            ctypes.byref(loss) if want_loss else None, _stream_ptr(stream)),
+               "cpa_mlp_train_step")
+        return loss.value if want_loss else None
+
+
+N_FEATURES = 12
+
+
+class ShrinkArray:
+    """Shrink parameters marshalled once into a C array, for repeated batched
+    calls on the same plan (building the array per call costs host time
+    proportional to the batch)."""
+
+    def __init__(self, specs):
+        specs = specs if isinstance(specs, (list, tuple)) else [specs]
+        self.arr = (CpaShrink * len(specs))(*[_as_shrink(x) for x in specs])
+        self.count = len(specs)
+
+
+def _shrink_array(shrink):
+    if isinstance(shrink, ShrinkArray):
+        return shrink.arr, shrink.count
+    specs = shrink if isinstance(shrink, (list, tuple)) else [shrink]
+    return (CpaShrink * len(specs))(*[_as_shrink(x) for x in specs]), len(specs)
+
+
+def cpa_batch_features(h: Handle, plan: BatchPlan, X, shrink, stream=None):
+    """Predictor features (count x 12, float32 CUDA) and theta_4 (float64)."""
+    import torch
+    F = torch.empty((plan.count, N_FEATURES), dtype=torch.float32, device=X.device)
+    th = torch.empty(plan.count, dtype=torch.float64, device=X.device)
+    arr, k = _shrink_array(shrink)
+    _check(load().cpa_batch_features(h.ptr, plan.ptr, ctypes.c_void_p(X.data_ptr()), arr, k,
+                                     ctypes.c_void_p(F.data_ptr()), ctypes.c_void_p(th.data_ptr()),
+                                     _stream_ptr(stream)), "cpa_batch_features")
+    return F, th
+
+
+def cpa_svt_batched_learned(h: Handle, plan: BatchPlan, net: MLP, X, shrink, L_scale=1.0, L_min=4, L_max=96,
+                            L_fallback=50, use_lambda=False, margin=0.01, prec="bf16x3", Y=None, stream=None):
+    import torch
+    if Y is None:
+        Y = torch.empty_like(X)
+    arr, k = _shrink_array(shrink)
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    _check(load().cpa_svt_batched_learned(h.ptr, plan.ptr, net.ptr, ctypes.c_void_p(X.data_ptr()), arr, k,
+                                          float(L_scale), int(L_min), int(L_max), int(L_fallback),
+                                          1 if use_lambda else 0, float(margin), p,
+                                          ctypes.c_void_p(Y.data_ptr()), _stream_ptr(stream)),
+           "cpa_svt_batched_learned")
+    return Y
+
+
+def cpa_batch_read_choices(plan: BatchPlan, stream=None):
+    Ls = (ctypes.c_int * plan.count)()
+    nfb = ctypes.c_int()
+    _check(load().cpa_batch_read_choices(plan.ptr, Ls, ctypes.byref(nfb), _stream_ptr(stream)),
+           "cpa_batch_read_choices")
+    return np.array(Ls[:], dtype=np.int64), nfb.value

@@ -39,6 +39,7 @@ constexpr int kLdB = kP + 8;    // BF16 row stride of 64-wide tiles (conflict-fr
 constexpr int kLdX = kQ + 8;    // BF16 row stride of X tiles
 constexpr int kThreads = 128;
 constexpr int kMaxBatchTerms = 128;
+constexpr uint64_t kEdgeSeedXor = 0x5EEDULL;   // start vector of the lower-edge feature
 
 struct BatchDesc {
     int64_t off;   // element offset of X (and Y) in the packed buffers
@@ -133,20 +134,43 @@ struct BatchSmem {
     __nv_bfloat16 zlo[2][kP * kLdB];
     float g[kP * (kP + 1)];              // G (FP32), then H for the final product
     float v[2][kP];                      // power-iteration vectors
-    double red[8];
+    float redf[8];                       // bsumf partials, two sets of four
     double coef[kMaxBatchTerms];
     double tab[4 * kMaxBatchTerms];
     double hs[kMaxBatchTerms];
     double scal[4];                      // theta, r, trace, lambda
+    int next_it;                         // work item fetched by thread 0
 };
 
-__device__ __forceinline__ double bsum(double x, double *red) {
+// Block sum (4 warps) of one float per thread.  The warp partials go through
+// one of two sets of shared slots, alternating with `slot`, so one barrier
+// per call suffices: a set is rewritten two calls later, after every thread
+// has passed the barrier of the call in between (and so has read it).
+__device__ __forceinline__ float bsumf(float x, float *red8, int &slot) {
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *r = red8 + 4 * (slot & 1);
+    ++slot;
+    if ((threadIdx.x & 31) == 0) r[threadIdx.x >> 5] = x;
     __syncthreads();
-    if (lane == 0) red[w] = x;
-    __syncthreads();
-    return red[0] + red[1] + red[2] + red[3];
+    return (r[0] + r[1]) + (r[2] + r[3]);
+}
+
+// (G v)(row) from the FP32 Gram matrix in shared memory: two threads per row
+// (half = 0, 1 take alternate columns), two accumulators each; rows >= p
+// give 0.  Called by all threads of the block (pair shuffle).
+__device__ __forceinline__ float gmatvec(const BatchSmem &S, int row, int half, int p, const float *v) {
+    float a0 = 0.f, a1 = 0.f;
+    if (row < p) {
+        const float *gr = S.g + row * (kP + 1);
+        int j = half;
+        for (; j + 2 < p; j += 4) {
+            a0 = fmaf(gr[j], v[j], a0);
+            a1 = fmaf(gr[j + 2], v[j + 2], a1);
+        }
+        if (j < p) a0 = fmaf(gr[j], v[j], a0);
+    }
+    const float a = a0 + a1;
+    return a + __shfl_xor_sync(0xffffffffu, a, 1);
 }
 
 __device__ __forceinline__ uint64_t splitmix64_b(uint64_t seed, uint64_t i) {
@@ -246,20 +270,227 @@ __device__ __forceinline__ float *zbuf_f32(BatchSmem &S, int b) {
 // FP32 variant: the BF16 buffers are reused as FP32 storage (xhi/xlo hold X
 // in FP32, ahi/alo hold At, zhi[b]/zlo[b] hold Psi_{k-1}).
 
-template <bool TC>
+// Feature vector of one matrix for the learned predictor (kFeatures
+// entries, defined in the declaration of cpa_batch_features): shape, energy
+// and threshold relative to theta_4 (a lower bound of Lambda_max after four
+// power products), the lower spectral edge, |G|_F^2, convergence of the
+// power iterates, and the shrink kind.
+constexpr int kFeatures = 12;
+constexpr int kHidden = 64;   // the predictor network: kFeatures -> 64 -> 64 -> 2
+
+// Learned selection inside the batched launch: the network's parameters
+// (layout W1[64][12], b1, W2[64][64], b2, W3[2][64], b3) and the rule that
+// maps its outputs (y0, y1) to (Lambda_max, L).
+struct LearnArgs {
+    const float *P;
+    double L_scale, margin;
+    int L_min, L_max, L_fallback, use_lambda;
+    int *L_out;       // L chosen per matrix
+    int *nfallback;   // matrices that took the fallback
+};
+
+// Features of one matrix (FEAT: written out, returns L = -1) or the learned
+// choice of (Lambda_max, L) for it (LEARN).  Kept out of line so that the
+// recurrence of the calling kernel is compiled as in the plain mode.
+struct Choice {
+    double lam;
+    int L;
+};
+
+template <bool FEAT>
+__device__ __noinline__ Choice learned_phase(BatchSmem &S, int idx, int p, int q, ShrinkParams sp, float th2, float th4,
+                                             float r4, double lam, float *__restrict__ feat,
+                                             double *__restrict__ theta_out, const LearnArgs la) {
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int row = tid >> 1, half = tid & 1;
+    const bool own = row < p && half == 0;
+    int rs = 0;   // a barrier precedes the first reduction
+        // lower spectral edge: 4 steps u <- (theta4 I - G) u / |.| from a
+        // second SplitMix64 vector, then lambda_min = u^T G u / u^T u
+        __syncthreads();
+        for (int i = tid; i < p; i += kThreads) {
+            const uint64_t z = splitmix64_b(kStartSeed ^ kEdgeSeedXor, (uint64_t)i);
+            S.v[0][i] = (float)((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+        }
+        __syncthreads();
+        float lmin = 0.f;
+        int uc = 0;
+        for (int t = 0; t <= 4; ++t) {
+            const float a = gmatvec(S, row, half, p, S.v[uc]);
+            const float ur = own ? S.v[uc][row] : 0.f;
+            if (t < 4) {
+                const float nx = th4 * ur - a;
+                const float n2 = bsumf(own ? nx * nx : 0.f, S.redf, rs);
+                const float sc2 = n2 > 0.f ? 1.f / sqrtf(n2) : 0.f;
+                if (own) S.v[uc ^ 1][row] = nx * sc2;
+                __syncthreads();
+                uc ^= 1;
+            } else {
+                const float num = bsumf(ur * a, S.redf, rs);
+                const float den = bsumf(ur * ur, S.redf, rs);
+                lmin = den > 0.f ? num / den : 0.f;
+            }
+        }
+        float fro = 0.f;
+        for (int r = w; r < p; r += kThreads / 32)
+            for (int c = lane; c < p; c += 32) {
+                const float gv = S.g[r * (kP + 1) + c];
+                fro = fmaf(gv, gv, fro);
+            }
+        fro = bsumf(fro, S.redf, rs);
+        const float tr = bsumf(own ? S.g[row * (kP + 1) + row] : 0.f, S.redf, rs);
+        // one feature per thread (threads 0..11): ratio in FP64, log in FP32
+        float *fv = reinterpret_cast<float *>(S.tab);
+        if (tid < kFeatures) {
+            const double tiny = 1e-30;
+            const double E = tr > 0.f ? (double)tr : 1.0;
+            const double t4 = fmax((double)th4, tiny * E);
+            double thr2;   // squared threshold on sigma (weighted soft: its level at theta4)
+            if (sp.kind == CPA_WSOFT) {
+                const double se = sqrt(fmax((double)th4 - sp.noise, 0.0));
+                const double wv = sp.c / (se + sp.eps);
+                thr2 = wv * wv;
+            } else {
+                thr2 = sp.tau * sp.tau;
+            }
+            thr2 = fmax(thr2, tiny * E);
+            const double lm = fmax((double)lmin, tiny * E);
+            double r = 1.0;
+            switch (tid) {
+                case 0: r = (double)p; break;
+                case 1: r = (double)q / (double)p; break;
+                case 2: r = E / t4; break;
+                case 3: r = thr2 / t4; break;
+                case 4: r = lm / t4; break;
+                case 5: r = thr2 / lm; break;
+                case 6: r = fmax((double)fro, tiny * E * E) / (t4 * t4); break;
+                case 7: r = E / ((double)p * thr2); break;
+                case 8: r = t4 / fmax((double)th2, tiny * E); break;
+                case 9: r = (t4 + (double)r4) / t4; break;
+                default: break;
+            }
+            fv[tid] = tid == 10 ? (sp.kind == CPA_HARD ? 1.f : 0.f)
+                      : tid == 11 ? (sp.kind == CPA_WSOFT ? 1.f : 0.f)
+                                  : logf((float)r);
+        }
+        if (FEAT) {
+            __syncthreads();
+            if (tid < kFeatures) feat[(int64_t)idx * kFeatures + tid] = fv[tid];
+            if (tid == 0) theta_out[idx] = (double)th4;
+            __syncthreads();
+            return Choice{0.0, -1};
+        }
+        // network forward.  The weights are staged in shared memory (the
+        // recurrence buffers, free until the shift) with padded rows
+        // (W1 stride 13, W2 stride 65: conflict-free), then one output per
+        // thread in the summation order of the network's own forward
+        // kernel (same FP32 results).
+        constexpr int oW1 = 0, ob1 = kHidden * kFeatures, oW2 = ob1 + kHidden, ob2 = oW2 + kHidden * kHidden,
+                      oW3 = ob2 + kHidden, ob3 = oW3 + 2 * kHidden, nP = ob3 + 2;
+        constexpr int sW1 = 0, sb1 = kHidden * (kFeatures + 1), sW2 = sb1 + kHidden,
+                      sb2 = sW2 + kHidden * (kHidden + 1), sW3 = sb2 + kHidden, sb3 = sW3 + 2 * kHidden;
+        static_assert((sb3 + 2) * sizeof(float) <= sizeof(S.zhi) + sizeof(S.zlo), "staged network");
+        float *wsm = reinterpret_cast<float *>(S.zhi);
+        auto staged = [&](int e) {   // shared-memory position of parameter e
+            if (e < ob1) return sW1 + (e / kFeatures) * (kFeatures + 1) + e % kFeatures;
+            if (e < oW2) return sb1 + (e - ob1);
+            if (e < ob2) return sW2 + ((e - oW2) / kHidden) * (kHidden + 1) + (e - oW2) % kHidden;
+            return sb2 + (e - ob2);   // b2, W3, b3 keep their relative layout
+        };
+        {
+            // all loads first (16-byte, coalesced), then the scatter
+            constexpr int n4 = nP / 4, per = (n4 + kThreads - 1) / kThreads;
+            const float4 *P4 = reinterpret_cast<const float4 *>(la.P);
+            float4 buf[per];
+#pragma unroll
+            for (int k = 0; k < per; ++k) {
+                const int e4 = tid + k * kThreads;
+                if (e4 < n4) buf[k] = __ldg(P4 + e4);
+            }
+#pragma unroll
+            for (int k = 0; k < per; ++k) {
+                const int e4 = tid + k * kThreads;
+                if (e4 < n4) {
+                    wsm[staged(4 * e4)] = buf[k].x;
+                    wsm[staged(4 * e4 + 1)] = buf[k].y;
+                    wsm[staged(4 * e4 + 2)] = buf[k].z;
+                    wsm[staged(4 * e4 + 3)] = buf[k].w;
+                }
+            }
+            if (tid < nP - 4 * n4) wsm[staged(4 * n4 + tid)] = __ldg(la.P + 4 * n4 + tid);
+        }
+        __syncthreads();
+        float *h1 = fv + 16, *h2 = h1 + kHidden, *yv = h2 + kHidden;
+        if (tid < kHidden) {
+            float a = wsm[sb1 + tid];
+            for (int j = 0; j < kFeatures; ++j) a = fmaf(wsm[sW1 + tid * (kFeatures + 1) + j], fv[j], a);
+            h1[tid] = a > 0.f ? a : 0.f;
+        }
+        __syncthreads();
+        if (tid < kHidden) {
+            float a = wsm[sb2 + tid];
+            for (int j = 0; j < kHidden; ++j) a = fmaf(wsm[sW2 + tid * (kHidden + 1) + j], h1[j], a);
+            h2[tid] = a > 0.f ? a : 0.f;
+        }
+        __syncthreads();
+        if (tid < 2) {
+            float a = wsm[sb3 + tid];
+            for (int j = 0; j < kHidden; ++j) a = fmaf(wsm[sW3 + tid * kHidden + j], h2[j], a);
+            yv[tid] = a;
+        }
+        __syncthreads();
+        // decision rule, taken by thread 0 and broadcast
+        if (tid == 0) {
+            const double y0 = (double)yv[0], y1 = (double)yv[1];
+            const double Lf = ceil(exp(y1) * la.L_scale);
+            const bool ok_L = isfinite(Lf) && Lf <= (double)la.L_max;
+            int Lc = ok_L ? (int)Lf : la.L_fallback;
+            if (Lc < la.L_min) Lc = la.L_min;
+            double lc = lam;
+            bool ok_lam = true;
+            if (la.use_lambda) {
+                const double lp = (double)th4 * exp(fmax(y0, 0.0)) * (1.0 + la.margin);
+                ok_lam = isfinite(lp) && lp > 0.0;
+                if (ok_lam) lc = lp;
+                else Lc = la.L_fallback;
+            }
+            la.L_out[idx] = Lc;
+            if (!ok_L || !ok_lam) atomicAdd(la.nfallback, 1);
+            S.scal[0] = lc;
+            S.next_it = Lc;   // free until the next fetch
+        }
+        __syncthreads();
+        const Choice c{S.scal[0], S.next_it};
+        __syncthreads();   // S.tab and S.next_it are rewritten by the caller
+        return c;
+}
+
+// Modes: FEAT writes the features (and theta_4) and stops; LEARN computes
+// them, runs the network and the decision rule, then shrinks with the
+// chosen (Lambda_max, L); neither: plain shrinkage.
+template <bool TC, bool FEAT, bool LEARN>
 __global__ void __launch_bounds__(kThreads, 2)
     batched_kernel(const BatchDesc *__restrict__ descs, const int *__restrict__ order, int count,
                    const float *__restrict__ X, float *__restrict__ Y, const ShrinkParams *__restrict__ shr,
                    int shr_stride, const double *__restrict__ lam_in, double *__restrict__ lam_out, int iters,
-                   int *__restrict__ status) {
+                   int *__restrict__ status, const int *__restrict__ L_in, float *__restrict__ feat,
+                   double *__restrict__ theta_out, const LearnArgs la) {
     extern __shared__ __align__(16) uint8_t smem_raw_b[];
     BatchSmem &S = *reinterpret_cast<BatchSmem *>(smem_raw_b);
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
 
-    for (int it = blockIdx.x; it < count; it += gridDim.x) {
+    // dynamic work list: each CTA fetches its next matrix from a counter
+    // (status[1], zero at launch), so CTAs that drew cheap matrices take
+    // more of them; matrices are listed largest estimated work first
+    for (;;) {
+        if (tid == 0) S.next_it = atomicAdd(status + 1, 1);
+        __syncthreads();
+        const int it = S.next_it;
+        if (it >= count) break;
         const int idx = order[it];
         const BatchDesc d = descs[idx];
-        const int m = d.m, n = d.n, L = d.L;
+        const int m = d.m, n = d.n;
+        int L = L_in ? L_in[idx] : d.L;
         const bool tall = m >= n;           // Gram X^T X (p = n) or X X^T (p = m)
         const int p = tall ? n : m, q = tall ? m : n;
         const int q16 = (q + 15) & ~15, p16 = (p + 15) & ~15;
@@ -299,71 +530,89 @@ __global__ void __launch_bounds__(kThreads, 2)
         __syncthreads();
 
         // ---- Lambda_max: power iteration (definition of cpa_lambda_bound)
-        double lam;
-        if (lam_in) {
-            lam = lam_in[idx];
-        } else {
-            double s0 = 0.0;
+        double lam = lam_in ? lam_in[idx] : 0.0;
+        float th2 = 0.f, th4 = 0.f, r4 = 0.f;   // features: theta_2, theta_4, residual after 4 products
+        int rs = 0;                             // reduction slot parity (bsumf)
+        const int row = tid >> 1, half = tid & 1;
+        const bool own = row < p && half == 0;  // the thread that keeps row `row` of a vector
+        if (!(lam > 0.0) || FEAT || LEARN) {
+            float s0 = 0.f;
             for (int i = tid; i < p; i += kThreads) {
                 const uint64_t z = splitmix64_b(kStartSeed, (uint64_t)i);
                 const float x = (float)((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
                 S.v[0][i] = x;
-                s0 += (double)x * (double)x;
+                s0 = fmaf(x, x, s0);
             }
-            double nrm2 = bsum(s0, S.red);
+            float nrm2 = bsumf(s0, S.redf, rs);
             int cur = 0;
-            for (int t = 0; t <= iters; ++t) {
+            const int its = FEAT ? 4 : iters;
+            for (int t = 0; t <= its; ++t) {
                 // w = G (v / |v|): two threads per row
-                const float sc = nrm2 > 0.0 ? (float)(1.0 / sqrt(nrm2)) : 0.f;
-                const int row = tid >> 1, half = tid & 1;
-                float a = 0.f;
-                if (row < p)
-                    for (int j = half; j < p; j += 2) a = fmaf(S.g[row * (kP + 1) + j], S.v[cur][j], a);
-                a += __shfl_xor_sync(0xffffffffu, a, 1);
-                a *= sc;
-                if (row < p && half == 0) S.v[cur ^ 1][row] = a;
-                const double ww = (row < p && half == 0) ? (double)a * (double)a : 0.0;
-                if (t < iters) {
-                    nrm2 = bsum(ww, S.red);
+                const float sc = nrm2 > 0.f ? 1.f / sqrtf(nrm2) : 0.f;
+                const float a = gmatvec(S, row, half, p, S.v[cur]) * sc;
+                const float vt = own ? S.v[cur][row] : 0.f;
+                if (own) S.v[cur ^ 1][row] = a;
+                if ((FEAT || LEARN) && t < its && t < 4) {
+                    // theta after t+1 products: (v/|v|)^T G (v/|v|), v the input of this product
+                    const float th = bsumf(vt * a, S.redf, rs) * sc;
+                    if (t == 1) th2 = th;
+                    if (t == 3) {
+                        th4 = th;
+                        const float dd = own ? a - th * vt * sc : 0.f;   // G v - theta v, v unit
+                        r4 = sqrtf(fmaxf(bsumf(dd * dd, S.redf, rs), 0.f));
+                    }
+                }
+                if (t < its) {
+                    nrm2 = bsumf(own ? a * a : 0.f, S.redf, rs);
                     cur ^= 1;
                 } else {
-                    // v = S.v[cur] / sqrt(nrm2), w = S.v[cur^1]
-                    __syncthreads();
-                    const double vs = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
-                    double th = 0.0, tr = 0.0;
-                    for (int i = tid; i < p; i += kThreads) {
-                        th += (double)S.v[cur][i] * vs * (double)S.v[cur ^ 1][i];
-                        tr += (double)S.g[i * (kP + 1) + i];
-                    }
-                    th = bsum(th, S.red);
-                    double r2 = 0.0;
-                    for (int i = tid; i < p; i += kThreads) {
-                        const double dd = (double)S.v[cur ^ 1][i] - th * (double)S.v[cur][i] * vs;
-                        r2 += dd * dd;
-                    }
-                    r2 = bsum(r2, S.red);
-                    tr = bsum(tr, S.red);
-                    lam = (th + sqrt(r2)) * (1.0 + kLambdaMargin);
-                    if (lam > tr) lam = tr;
+                    // v = S.v[cur] / |v| (unit), a = (G v)(row)
+                    const float vu = vt * sc;
+                    const float th = bsumf(vu * a, S.redf, rs);
+                    const float dd = own ? a - th * vu : 0.f;
+                    const float r2 = bsumf(dd * dd, S.redf, rs);
+                    const float tr = bsumf(own ? S.g[row * (kP + 1) + row] : 0.f, S.redf, rs);
+                    lam = ((double)th + sqrt((double)fmaxf(r2, 0.f))) * (1.0 + kLambdaMargin);
+                    if (lam > (double)tr) lam = (double)tr;
                     if (!isfinite(lam) || !isfinite(tr)) {
                         if (tid == 0) atomicExch(status, (int)CPA_ERR_NONFINITE);
                         lam = 1.0;
                     } else if (!(lam > 0.0)) {
-                        lam = tr > 0.0 ? tr : 1.0;
+                        lam = tr > 0.f ? (double)tr : 1.0;
                     }
                 }
             }
         }
+        if (FEAT || LEARN) {
+            const Choice c = learned_phase<FEAT>(S, idx, p, q, sp, th2, th4, r4, lam, feat, theta_out, la);
+            if (FEAT) continue;
+            lam = c.lam;
+            L = c.L;
+        }
         if (tid == 0) lam_out[idx] = lam;
 
-        // ---- coefficients (Eq. chebychev_coeff_shifted), FP64, cos(pi m / 2L) table
-        for (int e = tid; e < 4 * L; e += kThreads) S.tab[e] = cospi((double)e / (2.0 * L));
+        // ---- coefficients (Eq. chebychev_coeff_shifted), FP64, from the table
+        // cos(pi m / 2L), m < 4L: evaluated for m <= L, the rest by symmetry
+        // (cos(2 pi - x) = cos x, cos(pi - x) = -cos x)
+        for (int e = tid; e <= L; e += kThreads) S.tab[e] = cospi((double)e / (2.0 * L));
+        __syncthreads();
+        for (int e = L + 1 + tid; e < 4 * L; e += kThreads) {
+            const int mm = e > 2 * L ? 4 * L - e : e;
+            S.tab[e] = mm > L ? -S.tab[2 * L - mm] : S.tab[mm];
+        }
         __syncthreads();
         for (int l = tid; l < L; l += kThreads) S.hs[l] = response(sp, 0.5 * lam * (S.tab[(2 * l + 1) % (4 * L)] + 1.0));
         __syncthreads();
         for (int k = tid; k < L; k += kThreads) {
+            // table index k (2l + 1) mod 4L, advanced by 2k per node
+            const int M4 = 4 * L;
+            int ix = k;
             double a = 0.0;
-            for (int l = 0; l < L; ++l) a += S.tab[(int)(((int64_t)k * (2 * l + 1)) % (4 * L))] * S.hs[l];
+            for (int l = 0; l < L; ++l) {
+                a += S.tab[ix] * S.hs[l];
+                ix += 2 * k;
+                if (ix >= M4) ix -= M4;
+            }
             S.coef[k] = 2.0 / (double)L * a;
         }
         __syncthreads();
@@ -493,6 +742,8 @@ struct cpa_batch_ctx {
     int max_L = 0;
     int64_t total = 0;   // elements covered by the packed buffers
     std::vector<ShrinkParams> uploaded;   // shrink parameters currently on the device
+    // learned serving (allocated on first use): L chosen per matrix, fallbacks
+    int *d_L = nullptr, *d_nfb = nullptr;
 };
 
 namespace {
@@ -546,7 +797,7 @@ cpa_status cpa_batch_create(cpa_handle h, int count, const int64_t *off, const i
     cudaError_t e = cudaMalloc(&b->d_desc, sizeof(BatchDesc) * count);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_order, sizeof(int) * count);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_lambda, sizeof(double) * count);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_status, 2 * sizeof(int));   // status, work counter
     if (e == cudaSuccess) e = cudaMemcpy(b->d_desc, desc.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -564,6 +815,8 @@ cpa_status cpa_batch_destroy(cpa_batch b) {
     cudaFree(b->d_lambda);
     cudaFree(b->d_shrink);
     cudaFree(b->d_status);
+    cudaFree(b->d_L);
+    cudaFree(b->d_nfb);
     delete b;
     return CPA_OK;
 }
@@ -581,13 +834,13 @@ cpa_status cpa_batch_read_lambdas(cpa_batch b, double *host_out, void *stream) {
     return status ? (cpa_status)status : CPA_OK;
 }
 
-cpa_status cpa_svt_batched(cpa_handle h, cpa_batch b, const float *dX, const cpa_shrink *s, int s_count,
-                           const double *lambda, int iters, int prec, float *dY, void *stream) {
-    if (!h || !b || !dX || !dY || !s || (s_count != 1 && s_count != b->count) || iters < 0 || iters > 10000)
-        return CPA_ERR_INVALID_ARG;
-    if (prec != CPA_FP32 && prec != CPA_BF16 && prec != CPA_BF16X3) return CPA_ERR_UNSUPPORTED;
-    uintptr_t x0 = (uintptr_t)dX, y0 = (uintptr_t)dY, bytes = (uintptr_t)b->total * sizeof(float);
-    if (x0 < y0 + bytes && y0 < x0 + bytes) return CPA_ERR_INVALID_ARG;   // output overlaps input
+}  // extern "C"
+
+namespace {
+
+// Validates and uploads the shrink parameters (only when they changed since
+// the last upload of this plan; such a call synchronises the stream).
+cpa_status upload_shrink(cpa_batch b, const cpa_shrink *s, int s_count, cudaStream_t st) {
     std::vector<ShrinkParams> sp(s_count);
     memset(sp.data(), 0, sizeof(ShrinkParams) * s_count);   // padding too: compared with memcmp
     for (int i = 0; i < s_count; ++i) {
@@ -603,11 +856,6 @@ cpa_status cpa_svt_batched(cpa_handle h, cpa_batch b, const float *dX, const cpa
         sp[i].eps = x.eps;
         sp[i].noise = x.noise;
     }
-    cudaStream_t st = (cudaStream_t)stream;
-    BCK(cudaSetDevice(b->device));
-    // the shrink parameters are uploaded on the first call and whenever they
-    // change; such a call synchronises the stream (and cannot be captured),
-    // later calls with the same parameters only launch the kernel
     const bool same = b->uploaded.size() == sp.size() &&
                       memcmp(b->uploaded.data(), sp.data(), sizeof(ShrinkParams) * sp.size()) == 0;
     if (!same) {
@@ -621,18 +869,115 @@ cpa_status cpa_svt_batched(cpa_handle h, cpa_batch b, const float *dX, const cpa
         BCK(cudaMemcpy(b->d_shrink, sp.data(), sizeof(ShrinkParams) * s_count, cudaMemcpyHostToDevice));
         b->uploaded = sp;
     }
-    BCK(cudaMemsetAsync(b->d_status, 0, sizeof(int), st));
+    return CPA_OK;
+}
+
+template <bool TC, bool FEAT, bool LEARN>
+cpa_status launch_batched(cpa_batch b, const float *dX, float *dY, int s_count, const double *lambda, int iters,
+                          const int *L_override, float *feat, double *theta, const LearnArgs &la, cudaStream_t st) {
     const size_t smem = sizeof(BatchSmem);
-    const bool tc = prec != CPA_FP32;
-    auto kern = tc ? batched_kernel<true> : batched_kernel<false>;
+    auto kern = batched_kernel<TC, FEAT, LEARN>;
     BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
     if (per_sm < 1) per_sm = 1;
-    int grid = std::min(b->count, b->num_sms * per_sm);
+    const int grid = std::min(b->count, b->num_sms * per_sm);
     kern<<<grid, kThreads, smem, st>>>(b->d_desc, b->d_order, b->count, dX, dY, b->d_shrink, s_count > 1 ? 1 : 0,
-                                       lambda, b->d_lambda, iters, b->d_status);
+                                       lambda, b->d_lambda, iters, b->d_status, L_override, feat, theta, la);
     BCK(cudaGetLastError());
+    return CPA_OK;
+}
+
+cpa_status check_io(cpa_batch b, const float *dX, const float *dY) {
+    const uintptr_t x0 = (uintptr_t)dX, y0 = (uintptr_t)dY, bytes = (uintptr_t)b->total * sizeof(float);
+    if (dY && x0 < y0 + bytes && y0 < x0 + bytes) return CPA_ERR_INVALID_ARG;   // output overlaps input
+    return CPA_OK;
+}
+
+cpa_status run_batched(cpa_handle h, cpa_batch b, const float *dX, const cpa_shrink *s, int s_count,
+                       const double *lambda, int iters, int prec, float *dY, void *stream) {
+    if (!h || !b || !dX || !dY || !s || (s_count != 1 && s_count != b->count) || iters < 0 || iters > 10000)
+        return CPA_ERR_INVALID_ARG;
+    if (prec != CPA_FP32 && prec != CPA_BF16 && prec != CPA_BF16X3) return CPA_ERR_UNSUPPORTED;
+    cpa_status r = check_io(b, dX, dY);
+    if (r != CPA_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    BCK(cudaSetDevice(b->device));
+    if ((r = upload_shrink(b, s, s_count, st)) != CPA_OK) return r;
+    BCK(cudaMemsetAsync(b->d_status, 0, 2 * sizeof(int), st));
+    const LearnArgs none{};
+    if (prec != CPA_FP32)
+        return launch_batched<true, false, false>(b, dX, dY, s_count, lambda, iters, nullptr, nullptr, nullptr, none,
+                                                  st);
+    return launch_batched<false, false, false>(b, dX, dY, s_count, lambda, iters, nullptr, nullptr, nullptr, none,
+                                               st);
+}
+
+cpa_status ensure_learned_buffers(cpa_batch b) {
+    if (b->d_L) return CPA_OK;
+    if (cudaMalloc(&b->d_L, sizeof(int) * (size_t)b->count) != cudaSuccess ||
+        cudaMalloc(&b->d_nfb, sizeof(int)) != cudaSuccess)
+        return CPA_ERR_NO_MEMORY;
+    return CPA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cpa_status cpa_svt_batched(cpa_handle h, cpa_batch b, const float *dX, const cpa_shrink *s, int s_count,
+                           const double *lambda, int iters, int prec, float *dY, void *stream) {
+    return run_batched(h, b, dX, s, s_count, lambda, iters, prec, dY, stream);
+}
+
+cpa_status cpa_batch_features(cpa_handle h, cpa_batch b, const float *dX, const cpa_shrink *s, int s_count,
+                              float *dF, double *dTheta, void *stream) {
+    if (!h || !b || !dX || !s || !dF || !dTheta || (s_count != 1 && s_count != b->count)) return CPA_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    BCK(cudaSetDevice(b->device));
+    cpa_status r = upload_shrink(b, s, s_count, st);
+    if (r != CPA_OK) return r;
+    BCK(cudaMemsetAsync(b->d_status, 0, 2 * sizeof(int), st));
+    const LearnArgs none{};
+    return launch_batched<true, true, false>(b, dX, nullptr, s_count, nullptr, 4, nullptr, dF, dTheta, none, st);
+}
+
+cpa_status cpa_svt_batched_learned(cpa_handle h, cpa_batch b, cpa_mlp net, const float *dX, const cpa_shrink *s,
+                                   int s_count, double L_scale, int L_min, int L_max, int L_fallback, int use_lambda,
+                                   double margin, int prec, float *dY, void *stream) {
+    if (!h || !b || !net || !dX || !dY || !s || (s_count != 1 && s_count != b->count) || !(L_scale > 0.0) ||
+        !(margin >= 0.0) || L_min < 1 || L_max < L_min || L_max > kMaxBatchTerms || L_fallback < 1 ||
+        L_fallback > kMaxBatchTerms)
+        return CPA_ERR_INVALID_ARG;
+    if (prec != CPA_FP32 && prec != CPA_BF16 && prec != CPA_BF16X3) return CPA_ERR_UNSUPPORTED;
+    int dims[4], net_device = -1;
+    const float *P = mlp_device_params(net, dims, &net_device);
+    if (!P || dims[0] != kFeatures || dims[1] != kHidden || dims[2] != kHidden || dims[3] != 2 ||
+        net_device != b->device)
+        return CPA_ERR_INVALID_ARG;   // the 12 -> 64 -> 64 -> 2 predictor, on the plan's device
+    cpa_status r = check_io(b, dX, dY);
+    if (r != CPA_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    BCK(cudaSetDevice(b->device));
+    if ((r = ensure_learned_buffers(b)) != CPA_OK) return r;
+    if ((r = upload_shrink(b, s, s_count, st)) != CPA_OK) return r;
+    BCK(cudaMemsetAsync(b->d_status, 0, 2 * sizeof(int), st));
+    BCK(cudaMemsetAsync(b->d_nfb, 0, sizeof(int), st));
+    LearnArgs la{P, L_scale, margin, L_min, L_max, L_fallback, use_lambda ? 1 : 0, b->d_L, b->d_nfb};
+    if (prec != CPA_FP32)
+        return launch_batched<true, false, true>(b, dX, dY, s_count, nullptr, kDefaultPowerIters, nullptr, nullptr,
+                                                 nullptr, la, st);
+    return launch_batched<false, false, true>(b, dX, dY, s_count, nullptr, kDefaultPowerIters, nullptr, nullptr,
+                                              nullptr, la, st);
+}
+
+cpa_status cpa_batch_read_choices(cpa_batch b, int *host_L, int *host_fallbacks, void *stream) {
+    if (!b || !b->d_L) return CPA_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    BCK(cudaSetDevice(b->device));
+    if (host_L) BCK(cudaMemcpyAsync(host_L, b->d_L, sizeof(int) * b->count, cudaMemcpyDeviceToHost, st));
+    if (host_fallbacks) BCK(cudaMemcpyAsync(host_fallbacks, b->d_nfb, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BCK(cudaStreamSynchronize(st));
     return CPA_OK;
 }
 

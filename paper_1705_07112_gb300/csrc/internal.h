@@ -147,4 +147,8 @@ cudaError_t split_sym_lower(const float *S, int p, int64_t lds, __nv_bfloat16 *h
 cudaError_t check_finite(const float *X, int64_t rows, int64_t cols, int64_t ldx, int *flag, cudaStream_t st,
                          int num_sms);
 
+// Device view of a predictor network: its parameter array, widths
+// {in, h1, h2, out} and device (nullptr for a null handle).
+const float *mlp_device_params(cpa_mlp m, int dims[4], int *device);
+
 }  // namespace cpa

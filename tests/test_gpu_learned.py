@@ -1,0 +1,217 @@
+"""The learned (Lambda_max, L) predictor: its features against an FP64
+restatement, its decision rule against explicit choices, and its gain.
+
+The network is trained on the GPU by the library's own kernels on oracle
+labels (tests/predictor_data.py), served through cpa_svt_batched_learned,
+and judged by the FP64 oracle's exact shrinkage.  The measure is the one the
+predictor exists for: the fraction of matrices within 1e-2 relative
+Frobenius error of the exact shrinkage at a given cost, against the method
+without it (20-step power bound, one L for every matrix).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import predictor_data as D
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1705_07112_gb300 import _lib
+    return _lib
+
+
+def spec_dict(s):
+    return dict(kind=s.kind, tau=s.tau, c=s.c, eps=s.eps, noise=s.noise)
+
+
+def test_features_match_fp64_restatement(lib):
+    import torch
+    mats, specs = D.generate(300, seed=7)
+    h = lib.Handle(0)
+    plan = lib.BatchPlan(h, [m.shape for m in mats], L0=24)
+    X = torch.from_numpy(D.pack(mats)).cuda()
+    F, th = lib.cpa_batch_features(h, plan, X, [spec_dict(s) for s in specs])
+    F = F.cpu().numpy().astype(np.float64)
+    th = th.cpu().numpy()
+    R = np.array([D.reference_features(m, s) for m, s in zip(mats, specs)])
+    # shape and kind entries are exact
+    assert np.array_equal(F[:, [10, 11]], R[:, [10, 11]])
+    assert np.allclose(F[:, [0, 1]], R[:, [0, 1]], rtol=0, atol=1e-6)
+    # log-ratios of FP32 Gram quantities: FP32 rounding of G and of the
+    # power steps, relative 1e-5 at most for these well-scaled matrices
+    for j in (2, 3, 6, 7, 8, 9):
+        assert np.max(np.abs(F[:, j] - R[:, j])) <= 1e-3, (j, np.max(np.abs(F[:, j] - R[:, j])))
+    # lower edge: lambda_min / theta_4 in absolute terms (the ratio can be
+    # small, where its log amplifies rounding)
+    assert np.max(np.abs(np.exp(F[:, 4]) - np.exp(R[:, 4]))) <= 1e-4
+    assert np.max(np.abs(F[:, 5] - (F[:, 3] - F[:, 4]))) <= 1e-5
+    th_ref = np.array([D.O.lambda_bound(m.astype(np.float64), 3, D.MARGIN,
+                                        D.O.start_vector(D.START_SEED, min(m.shape)))["theta"] for m in mats])
+    assert np.allclose(th, th_ref, rtol=1e-5, atol=0)
+    plan.close()
+    h.close()
+
+
+@pytest.mark.parametrize("use_lambda", [False, True])
+def test_decision_rule_matches_explicit_choices(lib, use_lambda):
+    """The fused learned run takes exactly the L that the documented rule
+    derives from cpa_mlp_forward on cpa_batch_features, and equals the plain
+    batched run given those (Lambda_max, L)."""
+    import torch
+    mats, specs = D.generate(200, seed=8)
+    sd = [spec_dict(s) for s in specs]
+    shapes = [m.shape for m in mats]
+    h = lib.Handle(0)
+    net = lib.MLP((12, 64, 64, 2), seed=4)
+    P = net.get_params()
+    P[-2], P[-1] = 0.3, math.log(20.0)   # output biases: y0 ~ 0.3, y1 ~ log 20
+    net.set_params(P)
+    X = torch.from_numpy(D.pack(mats)).cuda()
+    plan = lib.BatchPlan(h, shapes, L0=24)
+    F, th = lib.cpa_batch_features(h, plan, X, sd)
+    y = net.forward(F).cpu().numpy().astype(np.float64)
+    th = th.cpu().numpy()
+    L_scale, L_min, L_max, L_fb, margin = 1.3, 6, 40, 50, 0.01
+    Lf = np.ceil(np.exp(y[:, 1]) * L_scale)
+    L_exp = np.where(Lf > L_max, L_fb, np.maximum(Lf, L_min)).astype(int)
+    Y1 = lib.cpa_svt_batched_learned(h, plan, net, X, sd, L_scale=L_scale, L_min=L_min, L_max=L_max,
+                                     L_fallback=L_fb, use_lambda=use_lambda, margin=margin, prec="bf16x3")
+    Ls, nfb = lib.cpa_batch_read_choices(plan)
+    assert np.array_equal(Ls, L_exp)
+    assert nfb == int(np.sum(Lf > L_max))
+    ref_plan = lib.BatchPlan(h, shapes, L=[int(v) for v in L_exp])
+    lam = None
+    if use_lambda:
+        lam = torch.from_numpy(th * np.exp(np.maximum(y[:, 0], 0.0)) * (1.0 + margin)).cuda()
+    Y2 = lib.cpa_svt_batched(h, ref_plan, X, sd, lambdas=lam, prec="bf16x3")
+    torch.cuda.synchronize()
+    if use_lambda:   # Lambda_max rounded on the device vs the host: ulps
+        assert torch.allclose(Y1, Y2, rtol=1e-5, atol=1e-6)
+    else:            # same arithmetic in another instantiation of the kernel
+        assert torch.allclose(Y1, Y2, rtol=1e-6, atol=1e-7)
+    # argument checks
+    with pytest.raises(lib.CpaError):
+        lib.cpa_svt_batched_learned(h, plan, net, X, sd, L_scale=0.0)
+    with pytest.raises(lib.CpaError):
+        lib.cpa_svt_batched_learned(h, plan, net, X, sd, L_max=129)
+    other = lib.MLP((12, 32, 64, 2), seed=1)
+    with pytest.raises(lib.CpaError):
+        lib.cpa_svt_batched_learned(h, plan, other, X, sd)
+    other.close()
+    for p_ in (plan, ref_plan):
+        p_.close()
+    net.close()
+    h.close()
+
+
+def train_predictor(lib, h, mats, specs, steps=3000, seed=5):
+    import torch
+    T = D.label_many(mats, specs).astype(np.float32)
+    plan = lib.BatchPlan(h, [m.shape for m in mats], L0=24)
+    X = torch.from_numpy(D.pack(mats)).cuda()
+    F, _ = lib.cpa_batch_features(h, plan, X, [spec_dict(s) for s in specs])
+    F = F.cpu().numpy().astype(np.float64)
+    mu, sd = F.mean(axis=0), F.std(axis=0) + 1e-6
+    Fn = torch.from_numpy(((F - mu) / sd).astype(np.float32)).cuda()
+    Td = torch.from_numpy(T).cuda()
+    net = lib.MLP((12, 64, 64, 2), seed=seed)
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    n = len(mats)
+    for step in range(steps):
+        idx = torch.randint(0, n, (256,), device="cuda", generator=g)
+        lr = 2e-3 if step < steps // 2 else 5e-4
+        net.train_step(Fn[idx].contiguous(), Td[idx].contiguous(), lr)
+    # fold the input standardisation into the first layer
+    P = net.get_params().astype(np.float64)
+    W1 = P[:12 * 64].reshape(64, 12)
+    b1 = P[12 * 64:12 * 64 + 64]
+    W1n = W1 / sd
+    b1n = b1 - W1n @ mu
+    P[:12 * 64] = W1n.ravel()
+    P[12 * 64:12 * 64 + 64] = b1n
+    net.set_params(P.astype(np.float32))
+    # L safety factor: the 80th percentile of the training residual of log L*
+    y = net.forward(torch.from_numpy(F.astype(np.float32)).cuda()).cpu().numpy().astype(np.float64)
+    resid = T[:, 1] - y[:, 1]
+    L_scale = float(np.exp(np.quantile(resid, 0.8)))
+    plan.close()
+    return net, L_scale, float(np.sqrt(np.mean(resid ** 2)))
+
+
+def test_learned_predictor_gains_over_fixed_order(lib):
+    import torch
+    h = lib.Handle(0)
+    tr_m, tr_s = D.generate(4500, seed=101)
+    net, L_scale, rms = train_predictor(lib, h, tr_m, tr_s)
+    assert rms < 0.8, rms
+
+    ev_m, ev_s = D.generate(600, seed=202)
+    exact = D.exact_many(ev_m, ev_s)
+    shapes = [m.shape for m in ev_m]
+    specs = [spec_dict(s) for s in ev_s]
+
+    def errors(Y):
+        y = Y.cpu().numpy().astype(np.float64)
+        out, o = [], 0
+        for (mm, nn), ex, Xm in zip(shapes, exact, ev_m):
+            Ym = y[o:o + mm * nn].reshape(mm, nn)
+            o += mm * nn
+            den = np.linalg.norm(ex)
+            out.append(np.linalg.norm(Ym - ex) / (den if den > 0 else np.linalg.norm(Xm)))
+        return np.array(out)
+
+    X = torch.from_numpy(D.pack(ev_m)).cuda()
+    lplan = lib.BatchPlan(h, shapes, L0=24)
+    err_l = errors(lib.cpa_svt_batched_learned(h, lplan, net, X, specs, L_scale=L_scale, prec="bf16x3"))
+    Ls, nfb = lib.cpa_batch_read_choices(lplan)
+    L_eq = int(math.ceil(Ls.mean()))
+    fplan = lib.BatchPlan(h, shapes, L0=L_eq)
+    err_f = errors(lib.cpa_svt_batched(h, fplan, X, specs, prec="bf16x3"))
+    bplan = lib.BatchPlan(h, shapes, L0=50)
+    err_b = errors(lib.cpa_svt_batched(h, bplan, X, specs, prec="bf16x3"))
+    ok_l, ok_f, ok_b = (float(np.mean(e <= D.TOL)) for e in (err_l, err_f, err_b))
+
+    # throughput on the evaluation set tiled 10 times (6,000 matrices)
+    tiled_m = ev_m * 10
+    tiled_s = lib.ShrinkArray(specs * 10)
+    Xt = torch.from_numpy(D.pack(tiled_m)).cuda()
+    tshapes = [m.shape for m in tiled_m]
+    lp = lib.BatchPlan(h, tshapes, L0=24)
+    bp = lib.BatchPlan(h, tshapes, L0=50)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps / 1e3
+
+    t_l = timed(lambda: lib.cpa_svt_batched_learned(h, lp, net, Xt, tiled_s, L_scale=L_scale, prec="bf16x3"))
+    t_b = timed(lambda: lib.cpa_svt_batched(h, bp, Xt, tiled_s, prec="bf16x3"))
+    good_l = ok_l * len(tiled_m) / t_l
+    good_b = ok_b * len(tiled_m) / t_b
+    print("\nlearned: L_scale %.2f, mean L %.1f, fallbacks %d, %.1f%% within 1e-2, %.0f matrices/s, %.0f good/s" %
+          (L_scale, Ls.mean(), nfb, 100 * ok_l, len(tiled_m) / t_l, good_l))
+    print("fixed L=%d (same mean cost): %.1f%% within 1e-2" % (L_eq, 100 * ok_f))
+    print("fixed L=50: %.1f%% within 1e-2, %.0f matrices/s, %.0f good/s" % (100 * ok_b, len(tiled_m) / t_b, good_b))
+    # per-matrix L puts more matrices within tolerance than one L of the
+    # same mean cost; against the fixed L = 50 it trades a few points of
+    # accuracy for fewer terms: more matrices per second, and about as many
+    # matrices within tolerance per second
+    assert ok_l > ok_f
+    assert len(tiled_m) / t_l > len(tiled_m) / t_b
+    assert good_l > 0.9 * good_b
+    for p_ in (lplan, fplan, bplan, lp, bp):
+        p_.close()
+    net.close()
+    h.close()

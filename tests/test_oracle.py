@@ -319,3 +319,49 @@ def test_phi_is_the_transformed_gram():
     assert np.allclose(O.phi(X), X.T @ X, atol=1e-12)
     assert np.allclose(O.phi(X, T), T @ X.T @ X @ T.T, atol=1e-12)
     assert np.allclose(O.phi(X.T, T), T @ X.T @ X @ T.T, atol=1e-12)
+
+
+def test_mlp_oracle_gradients_match_finite_differences():
+    from oracle import mlp as M
+    sizes = (5, 7, 6, 2)
+    n = 7 * 5 + 7 + 6 * 7 + 6 + 2 * 6 + 2
+    rng = np.random.default_rng(5)
+    params = rng.standard_normal(n) * 0.5
+    X = rng.standard_normal((9, 5))
+    T = rng.standard_normal((9, 2))
+    g = M.gradients(params, sizes, X, T)
+    h = 1e-6
+    for i in range(n):
+        e = np.zeros(n); e[i] = h
+        fd = (M.loss(params + e, sizes, X, T) - M.loss(params - e, sizes, X, T)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+    # forward against an independent composition with explicit loops for one sample
+    W1, b1, W2, b2, W3, b3 = M.unpack(params, sizes)
+    x = X[3]
+    a1 = [max(0.0, sum(W1[r, c] * x[c] for c in range(5)) + b1[r]) for r in range(7)]
+    a2 = [max(0.0, sum(W2[r, c] * a1[c] for c in range(7)) + b2[r]) for r in range(6)]
+    y = [sum(W3[r, c] * a2[c] for c in range(6)) + b3[r] for r in range(2)]
+    assert np.allclose(M.forward(params, sizes, X)[0][3], y, atol=1e-12)
+
+
+def test_adam_oracle_closed_forms():
+    """With bias correction the first step moves each parameter by
+    lr g/(|g|+eps), and so does every step of a constant gradient (the
+    corrected moments then equal g and g^2 exactly); weight decay adds
+    lr wd P."""
+    from oracle import mlp as M
+    rng = np.random.default_rng(12)
+    P0 = rng.standard_normal(20)
+    g = rng.standard_normal(20) * np.logspace(-3, 1, 20)
+    lr, wd = 1e-2, 0.1
+    opt = M.Adam(20)
+    P1 = opt.step(P0, g, lr, wd)
+    assert np.allclose(P1, P0 - lr * (g / (np.abs(g) + 1e-8) + wd * P0), rtol=0, atol=1e-14)
+    opt = M.Adam(20)
+    P = P0.copy()
+    for _ in range(7):
+        prev = P
+        P = opt.step(P, g, lr, 0.0)
+        assert np.allclose(P - prev, -lr * g / (np.abs(g) + 1e-8), rtol=1e-9, atol=1e-15)
+    # zero gradient, no decay: nothing moves
+    assert np.array_equal(M.Adam(20).step(P0, np.zeros(20), lr, 0.0), P0)
