@@ -35,6 +35,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SVT matrices/sec & tensor-pipe % at ≤1e-3 rel-Frob err: learned+BF16 vs plain FP32 CPA"
 L2_BYTES = 129 * 1024 * 1024
+# DRAM bytes (read + write) per launch of the dominant kernel, from the ncu
+# captures summarised under profiles/ (recurrence_rpca_frame_1024_bf16.md);
+# drop an entry when its kernel changes
+NCU_TRAFFIC = {("rpca_frame", "bf16"): 8.613376e6 + 0.74368e6}
 SEED = 0x1705071120000000
 
 
@@ -70,19 +74,46 @@ def make_workload(name, index=0):
 
 
 class ClockSampler:
-    """Samples nvidia-smi clocks and throttle reasons while running."""
+    """Samples the SM clock and the clock-event (throttle) reasons while the
+    timed region runs: through NVML (read-only queries, every 2 ms) when
+    libnvidia-ml is loadable, else through `nvidia-smi -lms 100`."""
 
+    # NVML clock-event reason bits (nvml.h)
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index=0):
         self.gpu = gpu_index
-        self.rows = []
+        self.rows = []          # (sm_mhz, max_mhz, reason names)
         self.proc = None
         self.thread = None
+        self.stop_flag = threading.Event()
+        self.nvml = None
+
+    def _nvml_open(self):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.gpu), ctypes.byref(h)) != 0:
+                return None
+            fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+            return lib, h, fn
+        except Exception:
+            return None
 
     def start(self):
+        self.nvml = self._nvml_open()
+        if self.nvml is not None:
+            self.thread = threading.Thread(target=self._poll_nvml, daemon=True)
+            self.thread.start()
+            return
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
                                           "--format=csv,noheader,nounits", "-lms", "100"],
@@ -90,16 +121,32 @@ class ClockSampler:
         except Exception:
             self.proc = None
             return
-        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread = threading.Thread(target=self._read_smi, daemon=True)
         self.thread.start()
 
-    def _read(self):
+    def _poll_nvml(self):
+        import ctypes
+        lib, h, reasons_fn = self.nvml
+        clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self.stop_flag.is_set():
+            ok = lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0          # NVML_CLOCK_SM
+            ok = ok and lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0
+            ok = ok and reasons_fn(h, ctypes.byref(rs)) == 0
+            if ok:
+                names = [n for bit, n in self.REASONS.items() if rs.value & bit]
+                self.rows.append((float(clk.value), float(mx.value), names))
+            time.sleep(0.002)
+
+    def _read_smi(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                self.rows.append(parts)
+            if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                self.rows.append((float(parts[1]), float(parts[2]) if parts[2].replace(".", "").isdigit() else None,
+                                  [names[i] for i in range(4) if parts[5 + i].lower() == "active"]))
 
     def stop(self):
+        self.stop_flag.set()
         if self.proc:
             self.proc.terminate()
             try:
@@ -108,14 +155,18 @@ class ClockSampler:
                 self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
+        if self.nvml is not None:
+            try:
+                self.nvml[0].nvmlShutdown()
+            except Exception:
+                pass
         if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+        sm = [r[0] for r in self.rows]
+        mx = [r[1] for r in self.rows if r[1]]
+        reasons = sorted({n for r in self.rows for n in r[2]})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows), "source": "nvml" if self.nvml is not None else "nvidia-smi"}
 
 
 def dist_setup(args):
@@ -455,7 +506,8 @@ def run_gpu(args, world, rank, local):
     roof = {"kernel": ("recurrence, all steps in one cooperative tcgen05 launch" if args.prec != "fp32"
                        else "recurrence product (FP32 SIMT)"),
             "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if (achieved and peak) else None, "traffic": None,
+            "frac": (achieved / peak) if (achieved and peak) else None,
+            "traffic": NCU_TRAFFIC.get((args.workload, args.prec)),
             "flops_per_launch": flops, "products_per_launch": products_per_launch,
             "dense_tflops_equiv": (products_per_launch * 2.0 * p ** 3 / (rec_ms / 1e3) / 1e12) if rec_ms > 0 else None,
             "ms_per_launch": rec_ms, "peak_source": "%s bf16 burst" % peaks["source"],
