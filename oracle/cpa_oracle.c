@@ -474,6 +474,14 @@ int orc_svd_jacobi(const double *X, int m, int n, double *W, double *V, double *
     for (int i = 0; i < n; i++)
         for (int j = 0; j < n; j++)
             V[(size_t)i * n + j] = (i == j ? 1.0 : 0.0);
+    /* columns whose norm is at the rounding level of the whole matrix
+     * (numerically zero singular values) are not rotated against each
+     * other: their inner products are noise and never meet the relative
+     * test */
+    double fro2 = 0.0;
+    for (size_t e = 0; e < (size_t)m * n; e++)
+        fro2 += X[e] * X[e];
+    const double negligible = tol * tol * fro2;
     int sweep;
     for (sweep = 1; sweep <= max_sweeps; sweep++) {
         int rotated = 0;
@@ -486,7 +494,7 @@ int orc_svd_jacobi(const double *X, int m, int n, double *W, double *V, double *
                     b += wj * wj;
                     g += wi * wj;
                 }
-                if (g == 0.0 || fabs(g) <= tol * sqrt(a * b))
+                if (g == 0.0 || fabs(g) <= tol * sqrt(a * b) || a <= negligible || b <= negligible)
                     continue;
                 rotated = 1;
                 /* rotation that zeroes the (i,j) entry of W^T W */
@@ -596,7 +604,13 @@ int orc_shrink_exact(const double *X, int m, int n, int kind, double tau, double
     double *W = malloc((size_t)mm * nn * sizeof(double));
     double *V = malloc((size_t)nn * nn * sizeof(double));
     double *s = malloc((size_t)nn * sizeof(double));
-    int sw = orc_svd_jacobi(Xt, mm, nn, W, V, s, 1e-15, 60);
+    /* convergence level proportional to m eps: the computed column inner
+     * products carry rounding errors of that relative size (Demmel and
+     * Veselic, 1992), so a fixed 1e-15 can stall on tall matrices */
+    double tol = (double)mm * 2.220446049250313e-16;
+    if (tol < 1e-15)
+        tol = 1e-15;
+    int sw = orc_svd_jacobi(Xt, mm, nn, W, V, s, tol, 60);
     double *R = malloc((size_t)mm * nn * sizeof(double));
     for (size_t e = 0; e < (size_t)mm * nn; e++)
         R[e] = 0.0;

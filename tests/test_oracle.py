@@ -365,3 +365,21 @@ def test_adam_oracle_closed_forms():
         assert np.allclose(P - prev, -lr * g / (np.abs(g) + 1e-8), rtol=1e-9, atol=1e-15)
     # zero gradient, no decay: nothing moves
     assert np.array_equal(M.Adam(20).step(P0, np.zeros(20), lr, 0.0), P0)
+
+
+def test_jacobi_svd_converges_on_rank_deficient_matrices():
+    """Rank-1 and rank-2 inputs (numerically zero singular values): the
+    Jacobi SVD converges and its singular values match the closed form."""
+    u, v = RNG.standard_normal(60), RNG.standard_normal(50)
+    for X, ref in ((np.full((60, 50), 4.0 / 3.0), [4.0 / 3.0 * np.sqrt(3000.0)]),
+                   (np.outer(u, v), [np.linalg.norm(u) * np.linalg.norm(v)])):
+        W, V, s = O.svd_jacobi(X, tol=60 * 2.220446049250313e-16)
+        s = np.sort(s)[::-1]
+        assert abs(s[0] - ref[0]) <= 1e-12 * ref[0]
+        assert np.all(s[1:] <= 1e-12 * ref[0])
+        Y = O.shrink_exact(X, O.Shrink(O.SOFT, 1.0))
+        assert np.allclose(Y, X * (1.0 - 1.0 / ref[0]), atol=1e-12 * ref[0])
+    A2 = RNG.standard_normal((40, 2)) @ RNG.standard_normal((2, 30))
+    _, _, s = O.svd_jacobi(A2, tol=40 * 2.220446049250313e-16)
+    ref = np.linalg.svd(A2, compute_uv=False)
+    assert np.allclose(np.sort(s)[::-1][:2], ref[:2], rtol=1e-12)
