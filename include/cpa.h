@@ -356,6 +356,36 @@ CPA_API cpa_status cpa_svt_batched_learned(cpa_handle h, cpa_batch b, cpa_mlp ne
                                            void *stream);
 CPA_API cpa_status cpa_batch_read_choices(cpa_batch b, int *host_L, int *host_fallbacks, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Background-modelling ADMM around the shrinkage (Appendix B, Eq.
+ * admm_algorithm_mod): min |l|_* + eta |s|_1 subject to l + s = d, with
+ * rho the ADMM step.  Each iteration runs cpa_svt (soft threshold
+ * tau_nuclear = 1/rho on the singular values, L terms, Lambda_max computed
+ * on the device, precision `prec`) on l + u1, the entrywise soft threshold
+ * tau_l1 = eta/rho on s + u2, the projection z3 = d, the dual update, and
+ * the least-squares step l = (2a1 - a2 + a3)/3, s = (-a1 + 2a2 + a3)/3 with
+ * a = z - u, all but the shrinkage in one fused elementwise kernel.  Start:
+ * l = s = u = 1 (Section V-C).
+ *
+ * cpa_admm_create: solver for m x n problems on the handle's device; owns
+ *   6 m n floats of state (m n <= 2^31).
+ * cpa_admm_rpca: dD device m x n (row stride ldd >= n); dL, dS device m x n
+ *   contiguous outputs, the last z1 (low-rank, exactly the shrinkage output)
+ *   and z2 (sparse); they must not overlap each other or dD.  Runs
+ *   max_iters iterations, or stops after iteration t when tol > 0 and
+ *   E = |l_{t+2} - l_{t+1}|_F / |l_{t+2}|_F < tol (the check needs a host
+ *   synchronisation per iteration; tol = 0 runs without one).
+ *   *iters_done (optional) receives the iterations run; errors (optional,
+ *   host, max_iters doubles) receives E after each iteration (synchronises).
+ *   Errors: CPA_ERR_INVALID_ARG on bad arguments; errors of cpa_svt pass
+ *   through. */
+typedef struct cpa_admm_ctx *cpa_admm;
+CPA_API cpa_status cpa_admm_create(cpa_handle h, int64_t m, int64_t n, cpa_admm *out);
+CPA_API cpa_status cpa_admm_destroy(cpa_admm a);
+CPA_API cpa_status cpa_admm_rpca(cpa_admm a, const float *dD, int64_t ldd, double tau_nuclear, double tau_l1, int L,
+                                 int prec, int max_iters, double tol, float *dL, float *dS, int *iters_done,
+                                 double *errors, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

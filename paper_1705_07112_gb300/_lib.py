@@ -26,7 +26,8 @@ EXPORTS = ["cpa_create", "cpa_destroy", "cpa_status_string", "cpa_last_error", "
            "cpa_profile_read", "cpa_kernel_gemm_bf16", "cpa_kernel_split_bf16", "cpa_batch_read_lambdas",
            "cpa_lambda_bound_noalloc", "cpa_mlp_create", "cpa_mlp_destroy", "cpa_mlp_param_count",
            "cpa_mlp_set_params", "cpa_mlp_get_params", "cpa_mlp_forward", "cpa_mlp_gradients",
-           "cpa_mlp_train_step", "cpa_batch_features", "cpa_svt_batched_learned", "cpa_batch_read_choices"]
+           "cpa_mlp_train_step", "cpa_batch_features", "cpa_svt_batched_learned", "cpa_batch_read_choices",
+           "cpa_admm_create", "cpa_admm_destroy", "cpa_admm_rpca"]
 STAGES = ["prep", "gram", "bound", "coeff", "shift", "recur", "apply", "sparse"]
 T_IDENTITY, T_HAAR1_LOWPASS, T_BLOCK_DCT8, T_DCT = 0, 1, 2, 3
 SPARSE_OFF, SPARSE_ABS, SPARSE_TOPK = 0, 1, 2
@@ -104,6 +105,10 @@ def load(path: str = LIB_PATH):
             "cpa_kernel_split_bf16": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, ctypes.c_int, _vp,
                                                      _vp, _i64, _vp]),
             "cpa_profile_read": (ctypes.c_int, [_vp, _P(_d), _P(_i64), ctypes.c_int]),
+            "cpa_admm_create": (ctypes.c_int, [_vp, _i64, _i64, _P(_vp)]),
+            "cpa_admm_destroy": (ctypes.c_int, [_vp]),
+            "cpa_admm_rpca": (ctypes.c_int, [_vp, _vp, _i64, _d, _d, ctypes.c_int, ctypes.c_int, ctypes.c_int, _d,
+                                             _vp, _vp, _P(ctypes.c_int), _P(_d), _vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -460,3 +465,43 @@ def cpa_batch_read_choices(plan: BatchPlan, stream=None):
     _check(load().cpa_batch_read_choices(plan.ptr, Ls, ctypes.byref(nfb), _stream_ptr(stream)),
            "cpa_batch_read_choices")
     return np.array(Ls[:], dtype=np.int64), nfb.value
+
+
+class Admm:
+    """cpa_admm: background-modelling ADMM around the shrinkage for m x n
+    problems (Appendix B)."""
+
+    def __init__(self, h: Handle, m: int, n: int):
+        self._lib = load()
+        ptr = ctypes.c_void_p()
+        _check(self._lib.cpa_admm_create(h.ptr, int(m), int(n), ctypes.byref(ptr)), "cpa_admm_create")
+        self.ptr, self.m, self.n = ptr, int(m), int(n)
+
+    def close(self):
+        if self.ptr:
+            self._lib.cpa_admm_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rpca(self, D, tau_nuclear, tau_l1, L, iters, prec="fp32", tol=0.0, Lout=None, Sout=None, stream=None):
+        """Returns (L, S, errors); D a float32 CUDA tensor m x n (row stride
+        D.stride(0)); errors[t] = E after iteration t."""
+        import torch
+        if not (D.is_cuda and D.dtype == torch.float32 and D.dim() == 2 and D.stride(1) == 1 and
+                tuple(D.shape) == (self.m, self.n)):
+            raise ValueError("D must be a float32 CUDA m x n tensor with unit column stride")
+        Lout = torch.empty((self.m, self.n), dtype=torch.float32, device=D.device) if Lout is None else Lout
+        Sout = torch.empty((self.m, self.n), dtype=torch.float32, device=D.device) if Sout is None else Sout
+        done = ctypes.c_int()
+        errs = (_d * int(iters))()
+        p = PREC[prec] if isinstance(prec, str) else int(prec)
+        _check(self._lib.cpa_admm_rpca(self.ptr, ctypes.c_void_p(D.data_ptr()), D.stride(0), float(tau_nuclear),
+                                       float(tau_l1), int(L), p, int(iters), float(tol),
+                                       ctypes.c_void_p(Lout.data_ptr()), ctypes.c_void_p(Sout.data_ptr()),
+                                       ctypes.byref(done), errs, _stream_ptr(stream)), "cpa_admm_rpca")
+        return Lout, Sout, np.array(errs[:done.value])
