@@ -230,6 +230,45 @@ __device__ __forceinline__ void store_transposed(const Epilogue &e, const uint32
     }
 }
 
+// BF16 hi/lo parts of the 32 x 32 block held in the transpose buffer (word
+// [r][c] is element (r0 + r, j0 + c), hi in the low half) to Dhi / Dlo with
+// 16-byte stores: lane l writes columns 8 (l % 4) .. +7 of rows l / 4 + 8 s,
+// s = 0..3 (conflict-free reads of the buffer); a partial row at the right
+// edge falls back to 2-byte stores.
+__device__ __forceinline__ void store_transposed_bf16x8(const Epilogue &e, const uint32_t *t, int M, int N, int r0,
+                                                        int j0, int lane) {
+    const int q = lane & 3, cc = 8 * q, jj = j0 + cc;
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+        const int rr = (lane >> 2) + 8 * sp, ii = r0 + rr;
+        if (ii >= M || jj >= N) continue;
+        uint32_t w[8];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) w[x] = t[rr * 33 + cc + x];
+        const int64_t o = (int64_t)ii * e.ldb + jj;
+        if (jj + 8 <= N) {
+            uint4 h4, l4;
+            h4.x = (w[0] & 0xFFFFu) | (w[1] << 16);
+            h4.y = (w[2] & 0xFFFFu) | (w[3] << 16);
+            h4.z = (w[4] & 0xFFFFu) | (w[5] << 16);
+            h4.w = (w[6] & 0xFFFFu) | (w[7] << 16);
+            *reinterpret_cast<uint4 *>(e.Dhi + o) = h4;
+            if (e.Dlo) {
+                l4.x = (w[0] >> 16) | (w[1] & 0xFFFF0000u);
+                l4.y = (w[2] >> 16) | (w[3] & 0xFFFF0000u);
+                l4.z = (w[4] >> 16) | (w[5] & 0xFFFF0000u);
+                l4.w = (w[6] >> 16) | (w[7] & 0xFFFF0000u);
+                *reinterpret_cast<uint4 *>(e.Dlo + o) = l4;
+            }
+        } else {
+            for (int x = 0; x < 8 && jj + x < N; ++x) {
+                e.Dhi[o + x] = __ushort_as_bfloat16((unsigned short)(w[x] & 0xFFFF));
+                if (e.Dlo) e.Dlo[o + x] = __ushort_as_bfloat16((unsigned short)(w[x] >> 16));
+            }
+        }
+    }
+}
+
 // Symmetric output, one 32 x 32 block of the accumulator held by a warp:
 // lane l owns row i = r0 + l, acc[c] is column j = j0 + c, j0 >= r0.
 // The FP32 arrays live in the lower triangle, so the block is handled at
@@ -276,17 +315,31 @@ __device__ __forceinline__ void epilogue_sym_block(const Epilogue &e, const Step
     const int i = r0 + lane;
     uint32_t hl[32];
     if (!diag) {
+        // the inputs' scales, zero where an input is absent (its buffer is
+        // then not read); groups of 8 columns issue all their shared-memory
+        // loads before their stores, so the loads overlap
+        const float sa = e.s_acc, sc = e.C ? e.s_c : 0.f, sc2 = e.C2 ? e.s_c2 : 0.f;
+        const bool hasc = e.C != nullptr, hasc2 = e.C2 != nullptr, hash = e.H != nullptr;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-            float v = e.s_acc * acc[c];
-            if (e.C) v = fmaf(e.s_c, es.c[c * 32 + lane], v);
-            if (e.C2) v = fmaf(e.s_c2, es.c2[c * 32 + lane], v);
-            es.c[c * 32 + lane] = v;
-            if (e.H) es.h[c * 32 + lane] = fmaf(ck, v, es.h[c * 32 + lane]);
-            const uint32_t p = pack_hilo(v);
-            hl[c] = p;
-            es.hi[c * 32 + lane] = __ushort_as_bfloat16((unsigned short)(p & 0xFFFF));
-            es.lo[c * 32 + lane] = __ushort_as_bfloat16((unsigned short)(p >> 16));
+        for (int g = 0; g < 32; g += 8) {
+            float cv[8], c2v[8], hv[8];
+#pragma unroll
+            for (int x = 0; x < 8; ++x) {
+                cv[x] = hasc ? es.c[(g + x) * 32 + lane] : 0.f;
+                c2v[x] = hasc2 ? es.c2[(g + x) * 32 + lane] : 0.f;
+                hv[x] = hash ? es.h[(g + x) * 32 + lane] : 0.f;
+            }
+#pragma unroll
+            for (int x = 0; x < 8; ++x) {
+                const int c = g + x;
+                const float v = fmaf(sc2, c2v[x], fmaf(sc, cv[x], sa * acc[c]));
+                es.c[c * 32 + lane] = v;
+                if (hash) es.h[c * 32 + lane] = fmaf(ck, v, hv[x]);
+                const uint32_t p = pack_hilo(v);
+                hl[c] = p;
+                es.hi[c * 32 + lane] = __ushort_as_bfloat16((unsigned short)(p & 0xFFFF));
+                es.lo[c * 32 + lane] = __ushort_as_bfloat16((unsigned short)(p >> 16));
+            }
         }
     } else {
         // read every input first: the stores below touch both triangles
@@ -345,7 +398,7 @@ __device__ __forceinline__ void epilogue_sym_block(const Epilogue &e, const Step
 #pragma unroll
         for (int c = 0; c < 32; ++c) es.t[lane * 33 + c] = hl[c];
         __syncwarp();
-        store_transposed(e, es.t, 1, M, N, r0, j0, lane, false);
+        store_transposed_bf16x8(e, es.t, M, N, r0, j0, lane);
         __syncwarp();
     }
 }

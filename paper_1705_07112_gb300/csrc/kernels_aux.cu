@@ -286,12 +286,14 @@ __device__ __forceinline__ void grid_barrier(unsigned int *count, unsigned int &
 // G (w_t / |w_t|), one warp per row, |w_{t+1}|^2 accumulated in FP64 by
 // atomics into norm2[t+1]; a grid barrier separates iterations.  Block 0
 // then forms theta, r, the trace and lambda as power_final_kernel does.
+// Dynamic shared memory: when `cache`, every warp owns at most one row of
+// G and keeps it for all iterations (row stride p rounded up to 4); when
+// `stage`, the block copies the current iterate once per iteration
+// (coalesced 16-byte loads) instead of every warp reading it from L2.
 __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__restrict__ G, int64_t ldg, int p,
                                                                int iters, uint64_t seed, float *v0, float *v1,
                                                                double *norm2, unsigned int *bar, double margin,
-                                                               double *out, int *err, int cache) {
-    // cache != 0: every warp owns at most one row of G and keeps it in
-    // shared memory for all iterations (row stride p rounded up to 4)
+                                                               double *out, int *err, int cache, int stage) {
     extern __shared__ __align__(16) float grow[];
     unsigned int target = 0;
     const int lane = threadIdx.x & 31;
@@ -316,6 +318,7 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
     }
     const int p4 = (p + 3) & ~3;
     float *myrow = grow + (threadIdx.x >> 5) * p4;
+    float *vs = grow + (cache ? 16 * p4 : 0);   // staged iterate
     if (cache && gwarp < p) {
         const float *g = G + (int64_t)gwarp * ldg;
         for (int j = lane; j < p4; j += 32) myrow[j] = j < p ? __ldg(g + j) : 0.f;
@@ -327,13 +330,21 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
         float *w = (t & 1) ? v0 : v1;
         const double nin = __ldcg(&norm2[t]);   // written by other blocks: read at L2
         const float scale = nin > 0.0 ? (float)(1.0 / sqrt(nin)) : 0.f;
+        if (stage) {
+            // written by other blocks before the barrier: read at L2
+            const float4 *src = reinterpret_cast<const float4 *>(v);
+            float4 *dst = reinterpret_cast<float4 *>(vs);
+            for (int i = threadIdx.x; i < (p4 >> 2); i += blockDim.x) dst[i] = __ldcg(src + i);
+            __syncthreads();
+        }
+        const float *vsrc = stage ? vs : v;
         double part = 0.0;
         for (int row = gwarp; row < p; row += nwarps) {
             const float *g = G + (int64_t)row * ldg;
             float acc = 0.f;
             if (cache) {
                 const float4 *g4 = reinterpret_cast<const float4 *>(myrow);
-                const float4 *v4 = reinterpret_cast<const float4 *>(v);
+                const float4 *v4 = reinterpret_cast<const float4 *>(vsrc);
                 const int n4 = p4 >> 2;
                 for (int j0 = lane; j0 < n4; j0 += 32 * 8) {
                     float4 a[8], b[8];
@@ -341,7 +352,7 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
                     for (int u = 0; u < 8; ++u) {
                         const int j = j0 + 32 * u;
                         a[u] = j < n4 ? g4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-                        b[u] = j < n4 ? __ldcg(v4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        b[u] = j < n4 ? (stage ? v4[j] : __ldcg(v4 + j)) : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
@@ -351,25 +362,26 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
                 }
             } else if (vec) {
                 const float4 *g4 = reinterpret_cast<const float4 *>(g);
-                const float4 *v4 = reinterpret_cast<const float4 *>(v);
+                const float4 *v4 = reinterpret_cast<const float4 *>(vsrc);
                 const int n4 = p >> 2;
-                // sixteen independent float4 pairs in flight per lane
-                for (int j0 = lane; j0 < n4; j0 += 32 * 16) {
-                    float4 a[16], b[16];
+                // eight independent float4 pairs in flight per lane (64 KB a
+                // block of 16 warps)
+                for (int j0 = lane; j0 < n4; j0 += 32 * 8) {
+                    float4 a[8], b[8];
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) {
+                    for (int u = 0; u < 8; ++u) {
                         const int j = j0 + 32 * u;
                         a[u] = j < n4 ? __ldg(g4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-                        b[u] = j < n4 ? __ldcg(v4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        b[u] = j < n4 ? (stage ? v4[j] : __ldcg(v4 + j)) : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) {
+                    for (int u = 0; u < 8; ++u) {
                         acc = fmaf(a[u].x, b[u].x, acc); acc = fmaf(a[u].y, b[u].y, acc);
                         acc = fmaf(a[u].z, b[u].z, acc); acc = fmaf(a[u].w, b[u].w, acc);
                     }
                 }
             } else {
-                for (int j = lane; j < p; j += 32) acc = fmaf(__ldg(g + j), __ldcg(v + j), acc);
+                for (int j = lane; j < p; j += 32) acc = fmaf(__ldg(g + j), stage ? vs[j] : __ldcg(v + j), acc);
             }
             acc = warp_sumf(acc) * scale;
             if (lane == 0) {
@@ -443,13 +455,17 @@ cudaError_t power_bound_persistent(const float *G, int64_t ldg, int p, int iters
     if (grid > (p + rows_per_block - 1) / rows_per_block) grid = (p + rows_per_block - 1) / rows_per_block;
     if (grid < 1) grid = 1;
     const int p4 = (p + 3) & ~3;
+    const size_t budget = 200 * 1024;
     const size_t cache_bytes = (size_t)16 * p4 * sizeof(float);
-    const int cache = ((int64_t)grid * 16 >= p && cache_bytes <= 200 * 1024) ? 1 : 0;
-    if (cache) {
+    const int cache = ((int64_t)grid * 16 >= p && cache_bytes <= budget) ? 1 : 0;
+    const size_t stage_bytes = (size_t)p4 * sizeof(float);
+    const int stage = (cache ? cache_bytes : 0) + stage_bytes <= budget ? 1 : 0;
+    const size_t smem = (cache ? cache_bytes : 0) + (stage ? stage_bytes : 0);
+    if (smem > 48 * 1024) {
         static bool attr = false;
         if (!attr) {
             cudaError_t ra = cudaFuncSetAttribute(power_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  200 * 1024);
+                                                  (int)budget);
             if (ra != cudaSuccess) return ra;
             attr = true;
         }
@@ -457,7 +473,7 @@ cudaError_t power_bound_persistent(const float *G, int64_t ldg, int p, int iters
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(512);
-    cfg.dynamicSmemBytes = cache ? cache_bytes : 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -467,7 +483,7 @@ cudaError_t power_bound_persistent(const float *G, int64_t ldg, int p, int iters
     const double margin = kLambdaMargin;
     const uint64_t seed = kStartSeed;
     return cudaLaunchKernelEx(&cfg, power_persistent_kernel, G, ldg, p, iters, seed, v0, v1, norm2, bar, margin, out,
-                              err, cache);
+                              err, cache, stage);
 }
 
 cudaError_t power_bound(const float *G, int64_t ldg, int p, int iters, float *v0, float *v1,
