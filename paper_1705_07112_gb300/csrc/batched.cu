@@ -500,15 +500,37 @@ __global__ void __launch_bounds__(kThreads, 2)
 
         // ---- Xp (p x q, zero padded to multiples of 16) into shared memory:
         // Xp = X^T when m >= n, else X, so that G = Xp Xp^T and the final
-        // product is H Xp (stored back transposed when m >= n)
-        for (int e = tid; e < p16 * q16; e += kThreads) {
-            const int r = e / q16, c = e % q16;
-            float x = 0.f;
-            if (r < p && c < q) x = tall ? __ldg(Xg + (int64_t)c * n + r) : __ldg(Xg + (int64_t)r * n + c);
-            if (TC)
-                put_hilo(S.xhi, S.xlo, r * kLdX + c, x);
-            else
-                reinterpret_cast<float *>(S.xhi)[r * kLdX + c] = x;   // spans xhi and xlo
+        // product is H Xp (stored back transposed when m >= n).  X is read
+        // in its own row-major order (coalesced), sixteen independent loads
+        // in flight per thread, then scattered; the padding is zeroed apart.
+        {
+            auto put = [&](int idx, float x) {
+                if (TC)
+                    put_hilo(S.xhi, S.xlo, idx, x);
+                else
+                    reinterpret_cast<float *>(S.xhi)[idx] = x;   // spans xhi and xlo
+            };
+            for (int e = tid; e < p16 * q16; e += kThreads) {
+                const int r = e / q16, c = e - r * q16;
+                if (r >= p || c >= q) put(r * kLdX + c, 0.f);
+            }
+            const int mn = m * n;
+            for (int base = 0; base < mn; base += 16 * kThreads) {
+                float v[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int e = base + k * kThreads + tid;
+                    v[k] = e < mn ? __ldg(Xg + e) : 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int e = base + k * kThreads + tid;
+                    if (e < mn) {
+                        const int i = e / n, j = e - i * n;
+                        put(tall ? j * kLdX + i : i * kLdX + j, v[k]);
+                    }
+                }
+            }
         }
         __syncthreads();
 
