@@ -641,6 +641,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 
         // ---- shift: At = (2/lambda) G (operand), Psi_1 = At - Id, H = c0/2 Id + c1 Psi_1
         const float s2 = (float)(2.0 / lam);
+        const float c0h = (float)(0.5 * S.coef[0]), c1 = L > 1 ? (float)S.coef[1] : 0.f;
         Frag z1, z0, h;   // Psi_{k-1}, Psi_{k-2}, H in the accumulator layout
 #pragma unroll
         for (int nt = 0; nt < 8; ++nt)
@@ -652,7 +653,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 const float eye = (r == c && in) ? 1.f : 0.f;
                 z1.v[nt][e] = at - eye;
                 z0.v[nt][e] = eye;   // Psi_0 = Id
-                h.v[nt][e] = (float)(0.5 * S.coef[0]) * eye + (L > 1 ? (float)S.coef[1] : 0.f) * z1.v[nt][e];
+                h.v[nt][e] = c0h * eye + c1 * z1.v[nt][e];
                 if (TC) {
                     put_hilo(S.ahi, S.alo, r * kLdB + c, at);
                 } else {
