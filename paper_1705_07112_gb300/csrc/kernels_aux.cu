@@ -295,6 +295,8 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
                                                                double *norm2, unsigned int *bar, double margin,
                                                                double *out, int *err, int cache, int stage) {
     extern __shared__ __align__(16) float grow[];
+    __shared__ double wpart[16];   // per-warp |w|^2 partials
+    __shared__ float sscale;       // 1 / |v| of the current iterate
     unsigned int target = 0;
     const int lane = threadIdx.x & 31;
     const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -328,15 +330,19 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
     for (int t = 0; t <= iters; ++t) {
         const float *v = (t & 1) ? v1 : v0;
         float *w = (t & 1) ? v0 : v1;
-        const double nin = __ldcg(&norm2[t]);   // written by other blocks: read at L2
-        const float scale = nin > 0.0 ? (float)(1.0 / sqrt(nin)) : 0.f;
+        // 1 / |v| once per block (FP64 is a scarce pipe: one thread)
+        if (threadIdx.x == 0) {
+            const double nin = __ldcg(&norm2[t]);   // written by other blocks: read at L2
+            sscale = nin > 0.0 ? (float)(1.0 / sqrt(nin)) : 0.f;
+        }
         if (stage) {
             // written by other blocks before the barrier: read at L2
             const float4 *src = reinterpret_cast<const float4 *>(v);
             float4 *dst = reinterpret_cast<float4 *>(vs);
             for (int i = threadIdx.x; i < (p4 >> 2); i += blockDim.x) dst[i] = __ldcg(src + i);
-            __syncthreads();
         }
+        __syncthreads();
+        const float scale = sscale;
         const float *vsrc = stage ? vs : v;
         double part = 0.0;
         for (int row = gwarp; row < p; row += nwarps) {
@@ -389,8 +395,14 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
                 part += (double)acc * (double)acc;
             }
         }
-        part = block_sum(part);
-        if (threadIdx.x == 0 && part != 0.0) atomicAdd(&norm2[t + 1], part);
+        // lane 0 of each warp holds its rows' part: one warp adds the 16
+        if (lane == 0) wpart[threadIdx.x >> 5] = part;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double q = threadIdx.x < (int)(blockDim.x >> 5) ? wpart[threadIdx.x] : 0.0;
+            q = warp_sum(q);
+            if (threadIdx.x == 0 && q != 0.0) atomicAdd(&norm2[t + 1], q);
+        }
         grid_barrier(bar, target, err);
     }
     // after iters+1 products: v = buffer of step iters (unnormalised, norm2[iters]),
