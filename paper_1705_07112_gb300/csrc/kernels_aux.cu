@@ -184,10 +184,10 @@ __global__ void shift_kernel(const float *__restrict__ G, int64_t ldg, int p, co
     float s = (float)(2.0 / lam[0]);
     float c0h = (float)(0.5 * c[0]);
     float c1 = L > 1 ? (float)c[1] : 0.f;
-    int64_t total = (int64_t)p * p;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int i = (int)(e / p), j = (int)(e % p);
+    // a block per row (grid-stride), threads across the row: no 64-bit
+    // division per element
+    for (int i = blockIdx.x; i < p; i += gridDim.x)
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
         float at = s * G[(int64_t)i * ldg + j];
         float a = at - (i == j ? 1.f : 0.f);
         if (A) A[(int64_t)i * ld + j] = a;
@@ -534,8 +534,7 @@ cudaError_t device_coeffs(const double *lam_dev, double lam_host, int L, const S
 cudaError_t shift_init(const float *G, int64_t ldg, int p, const double *lam, const double *c, int L, float *A,
                        float *Z1, float *H, int64_t ld, __nv_bfloat16 *Athi, __nv_bfloat16 *Atlo,
                        __nv_bfloat16 *Z1hi, __nv_bfloat16 *Z1lo, int64_t ldb, cudaStream_t st, int num_sms) {
-    int64_t total = (int64_t)p * p;
-    int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 8);
+    int blocks = std::min(p, num_sms * 8);   // a block per row, grid-stride
     if (blocks < 1) blocks = 1;
     shift_kernel<<<blocks, 256, 0, st>>>(G, ldg, p, lam, c, L, A, Z1, H, ld, Athi, Atlo, Z1hi, Z1lo, ldb);
     return cudaGetLastError();
