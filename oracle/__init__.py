@@ -18,6 +18,7 @@ Functions and the passage each follows:
 * ``cpa``                 Algorithm 1, dense, optional transform T and entry
                           threshold (Eqs. sing_shrink_exact_sparse,
                           threshold_components, recurrence_our_method, SVD_fil)
+* ``cpa_clenshaw``        the same filter summed by Clenshaw's recurrence
 * ``cpa_vec``             the same filter applied to one vector
                           (Eq. prop_another_form), for sampled outputs at any size
 * ``lambda_bound``        power-iteration bound on Lambda_max (the paper names no
@@ -77,6 +78,7 @@ def _load():
                 "orc_gram": (None, [_P, _i, _i, _P]),
                 "orc_phi": (None, [_P, _i, _i, _P, _P]),
                 "orc_cpa": (_i, [_P, _i, _i, _i, _d, _d, _d, _d, _i, _d, _P, _d, _P, _P]),
+                "orc_cpa_clenshaw": (_i, [_P, _i, _i, _i, _d, _d, _d, _d, _i, _d, _P, _d, _P, _P]),
                 "orc_cpa_vec": (_i, [_P, _i, _i, _i, _d, _d, _d, _d, _i, _d, _P, _P]),
                 "orc_lambda_bound": (_i, [_P, _i, _i, _i, _d, _P, _P]),
                 "orc_svd_jacobi": (_i, [_P, _i, _i, _P, _P, _P, _d, _i]),
@@ -189,6 +191,22 @@ def cpa(X, s: Shrink, alpha: int, lam: float, T=None, eps_thr: float = -1.0,
                          float(eps_thr), _p(Y), _p(H))
     if rc:
         raise ValueError("orc_cpa: invalid arguments (alpha=%r, lam=%r)" % (alpha, lam))
+    return (Y, H) if return_H else Y
+
+
+def cpa_clenshaw(X, s: Shrink, alpha: int, lam: float, T=None, eps_thr: float = -1.0,
+                 return_H: bool = False):
+    """Algorithm 1 with the filter summed by Clenshaw's recurrence (FP64)."""
+    X = _arr(X)
+    m, n = X.shape
+    p = min(m, n)
+    Tm = _arr(T, (p, p)) if T is not None else None
+    Y = np.zeros((m, n))
+    H = np.zeros((p, p)) if return_H else None
+    rc = _load().orc_cpa_clenshaw(_p(X), m, n, *s.args(), int(alpha), float(lam), _p(Tm),
+                                  float(eps_thr), _p(Y), _p(H))
+    if rc:
+        raise ValueError("orc_cpa_clenshaw: invalid arguments (alpha=%r, lam=%r)" % (alpha, lam))
     return (Y, H) if return_H else Y
 
 

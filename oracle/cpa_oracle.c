@@ -239,9 +239,32 @@ void orc_phi(const double *X, int m, int n, const double *T, double *Phi)
 /* For m < n the paper's m > n statement is applied to X^T and transposed    */
 /* back: G_hat(X) = T^T H_hat(T X X^T T^T) T X.                              */
 /* ------------------------------------------------------------------------- */
+static int cpa_scheme(const double *X, int m, int n, int kind, double tau, double c,
+                      double eps, double noise, int alpha, double lam, const double *T,
+                      double eps_thr, double *Y, double *Hout, int clenshaw);
+
 int orc_cpa(const double *X, int m, int n, int kind, double tau, double c,
             double eps, double noise, int alpha, double lam, const double *T,
             double eps_thr, double *Y, double *Hout)
+{
+    return cpa_scheme(X, m, n, kind, tau, c, eps, noise, alpha, lam, T, eps_thr, Y, Hout, 0);
+}
+
+/* The same filter H_hat = c_0/2 Id + sum_{k>=1} c_k T_k(B_hat) summed by
+ * Clenshaw's recurrence (Clenshaw, 1955) instead of the forward one:
+ *   b_alpha = b_{alpha+1} = 0,  b_k = c_k Id + 2 B_hat b_{k+1} - b_{k+2}
+ *   (k = alpha-1 .. 0),  H_hat = (b_0 - b_2) / 2.
+ * Same number of products; the sum needs no running accumulator. */
+int orc_cpa_clenshaw(const double *X, int m, int n, int kind, double tau, double c,
+                     double eps, double noise, int alpha, double lam, const double *T,
+                     double eps_thr, double *Y, double *Hout)
+{
+    return cpa_scheme(X, m, n, kind, tau, c, eps, noise, alpha, lam, T, eps_thr, Y, Hout, 1);
+}
+
+static int cpa_scheme(const double *X, int m, int n, int kind, double tau, double c,
+                      double eps, double noise, int alpha, double lam, const double *T,
+                      double eps_thr, double *Y, double *Hout, int clenshaw)
 {
     if (alpha < 1 || !(lam > 0.0))
         return 1;
@@ -277,26 +300,55 @@ int orc_cpa(const double *X, int m, int n, int kind, double tau, double c,
     for (int i = 0; i < p; i++)
         for (int j = 0; j < p; j++)
             Bh[(size_t)i * p + j] = 2.0 / lam * Phi[(size_t)i * p + j] - (i == j ? 1.0 : 0.0);
-    /* initial polynomials: Psi_0 = Id, Psi_1 = B_hat */
-    for (int i = 0; i < p; i++)
-        for (int j = 0; j < p; j++)
-            Pm2[(size_t)i * p + j] = (i == j ? 1.0 : 0.0);
-    memcpy(Pm1, Bh, pp * sizeof(double));
-    /* initial sum: H = c_0/2 Psi_0 + c_1 Psi_1 */
-    for (size_t e = 0; e < pp; e++)
-        H[e] = 0.5 * ck[0] * Pm2[e] + (alpha > 1 ? ck[1] * Pm1[e] : 0.0);
-    /* recurrence (Eq. recurrence_our_method) with accumulation:
-     * Psi_k = 2 B_hat Psi_{k-1} - Psi_{k-2};  H += c_k Psi_k,  k = 2..alpha-1 */
-    for (int k = 2; k < alpha; k++) {
-        matmul(Bh, Pm1, tmp, p, p, p);
-        for (size_t e = 0; e < pp; e++) {
-            Pk[e] = 2.0 * tmp[e] - Pm2[e];
-            H[e] += ck[k] * Pk[e];
+    if (!clenshaw) {
+        /* initial polynomials: Psi_0 = Id, Psi_1 = B_hat */
+        for (int i = 0; i < p; i++)
+            for (int j = 0; j < p; j++)
+                Pm2[(size_t)i * p + j] = (i == j ? 1.0 : 0.0);
+        memcpy(Pm1, Bh, pp * sizeof(double));
+        /* initial sum: H = c_0/2 Psi_0 + c_1 Psi_1 */
+        for (size_t e = 0; e < pp; e++)
+            H[e] = 0.5 * ck[0] * Pm2[e] + (alpha > 1 ? ck[1] * Pm1[e] : 0.0);
+        /* recurrence (Eq. recurrence_our_method) with accumulation:
+         * Psi_k = 2 B_hat Psi_{k-1} - Psi_{k-2};  H += c_k Psi_k,  k = 2..alpha-1 */
+        for (int k = 2; k < alpha; k++) {
+            matmul(Bh, Pm1, tmp, p, p, p);
+            for (size_t e = 0; e < pp; e++) {
+                Pk[e] = 2.0 * tmp[e] - Pm2[e];
+                H[e] += ck[k] * Pk[e];
+            }
+            double *r = Pm2;
+            Pm2 = Pm1;
+            Pm1 = Pk;
+            Pk = r;
         }
-        double *r = Pm2;
-        Pm2 = Pm1;
-        Pm1 = Pk;
-        Pk = r;
+    } else {
+        /* Clenshaw: Pm1 = b_{k+1}, Pm2 = b_{k+2}, both zero at k = alpha - 1 */
+        for (size_t e = 0; e < pp; e++) {
+            Pm1[e] = 0.0;
+            Pm2[e] = 0.0;
+        }
+        for (int k = alpha - 1; k >= 0; k--) {
+            matmul(Bh, Pm1, tmp, p, p, p);
+            for (int i = 0; i < p; i++)
+                for (int j = 0; j < p; j++) {
+                    size_t e = (size_t)i * p + j;
+                    Pk[e] = (i == j ? ck[k] : 0.0) + 2.0 * tmp[e] - Pm2[e];
+                }
+            double *r = Pm2;   /* b_{k+2} <- b_{k+1}, b_{k+1} <- b_k */
+            Pm2 = Pm1;
+            Pm1 = Pk;
+            Pk = r;
+        }
+        /* now Pm1 = b_0, Pm2 = b_1: the closing step of Clenshaw's
+         * recurrence, sum_k c_k T_k = b_0 - B_hat b_1, less c_0/2 Id for
+         * the halved first term */
+        matmul(Bh, Pm2, tmp, p, p, p);
+        for (int i = 0; i < p; i++)
+            for (int j = 0; j < p; j++) {
+                size_t e = (size_t)i * p + j;
+                H[e] = Pm1[e] - tmp[e] - (i == j ? 0.5 * ck[0] : 0.0);
+            }
     }
     /* final product (Eq. SVD_fil): G_hat = B T^T H T  (m >= n);  T^T H T B  (m < n) */
     double *F = H;
