@@ -283,6 +283,7 @@ def workload_config(w, args, reference=False):
     if not reference:
         cfg["prec"] = args.prec
         cfg["cuda_graph"] = not args.no_graph
+        cfg["series"] = args.series
     return cfg
 
 
@@ -529,6 +530,9 @@ def run_gpu(args, world, rank, local):
     Xs = [torch.from_numpy(make_workload(args.workload, i + 1000 * rank).X).to(dev) for i in range(n_in)]
     Y = torch.empty((m, n), dtype=torch.float32, device=dev)
     h = cpa.Handle(local)
+    if args.series == "clenshaw":
+        from paper_1705_07112_gb300 import _lib
+        _lib.cpa_set_option(h, _lib.OPT_SERIES, _lib.SERIES_CLENSHAW)
     shrink = w0.shrink
     stream = torch.cuda.current_stream(dev)
 
@@ -657,6 +661,8 @@ def main():
     ap.add_argument("--workload", default="rpca_frame")
     ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16", "bf16x3"])
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--series", default="forward", choices=["forward", "clenshaw"],
+                    help="how the filter's series is summed (single-matrix workloads)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=256)
     ap.add_argument("--ref-rows", type=int, default=32)

@@ -171,6 +171,21 @@ CPA_API cpa_status cpa_get_lambda(cpa_handle h, double *lambda_out, void *stream
 CPA_API cpa_status cpa_get_coeffs(cpa_handle h, double *c_out, int L, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Handle options (no counterpart in the paper).
+ * CPA_OPT_SERIES: how cpa_svt sums the filter's series
+ *   H_hat = c_0/2 Id + sum_{k=1}^{L-1} c_k T_k(B_hat):
+ *   CPA_SERIES_FORWARD (default): Algorithm 1's forward recurrence
+ *     Psi_k = 2 B_hat Psi_{k-1} - Psi_{k-2} with the running sum H += c_k Psi_k;
+ *   CPA_SERIES_CLENSHAW: Clenshaw's recurrence b_k = c_k Id + 2 B_hat b_{k+1}
+ *     - b_{k+2} (k = L-1 .. 0), H_hat = (b_0 - b_2) / 2: the same L-2
+ *     products, no running sum (less memory traffic per step).
+ * Returns CPA_ERR_INVALID_ARG for an unknown option or value.
+ * ------------------------------------------------------------------------- */
+enum { CPA_OPT_SERIES = 1 };
+enum { CPA_SERIES_FORWARD = 0, CPA_SERIES_CLENSHAW = 1 };
+CPA_API cpa_status cpa_set_option(cpa_handle h, int option, int value);
+
+/* ---------------------------------------------------------------------------
  * Diagnostics: per-stage device time and kernel-launch counts.
  * When enabled, every stage of cpa_svt is bracketed by CUDA events recorded
  * on the call's stream (each recurrence product separately), so the average

@@ -27,7 +27,8 @@ EXPORTS = ["cpa_create", "cpa_destroy", "cpa_status_string", "cpa_last_error", "
            "cpa_lambda_bound_noalloc", "cpa_mlp_create", "cpa_mlp_destroy", "cpa_mlp_param_count",
            "cpa_mlp_set_params", "cpa_mlp_get_params", "cpa_mlp_forward", "cpa_mlp_gradients",
            "cpa_mlp_train_step", "cpa_batch_features", "cpa_svt_batched_learned", "cpa_batch_read_choices",
-           "cpa_admm_create", "cpa_admm_destroy", "cpa_admm_rpca"]
+           "cpa_admm_create", "cpa_admm_destroy", "cpa_admm_rpca", "cpa_set_option"]
+OPT_SERIES, SERIES_FORWARD, SERIES_CLENSHAW = 1, 0, 1
 STAGES = ["prep", "gram", "bound", "coeff", "shift", "recur", "apply", "sparse"]
 T_IDENTITY, T_HAAR1_LOWPASS, T_BLOCK_DCT8, T_DCT = 0, 1, 2, 3
 SPARSE_OFF, SPARSE_ABS, SPARSE_TOPK = 0, 1, 2
@@ -105,6 +106,7 @@ def load(path: str = LIB_PATH):
             "cpa_kernel_split_bf16": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, ctypes.c_int, _vp,
                                                      _vp, _i64, _vp]),
             "cpa_profile_read": (ctypes.c_int, [_vp, _P(_d), _P(_i64), ctypes.c_int]),
+            "cpa_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
             "cpa_admm_create": (ctypes.c_int, [_vp, _i64, _i64, _P(_vp)]),
             "cpa_admm_destroy": (ctypes.c_int, [_vp]),
             "cpa_admm_rpca": (ctypes.c_int, [_vp, _vp, _i64, _d, _d, ctypes.c_int, ctypes.c_int, ctypes.c_int, _d,
@@ -505,3 +507,7 @@ class Admm:
                                        ctypes.c_void_p(Lout.data_ptr()), ctypes.c_void_p(Sout.data_ptr()),
                                        ctypes.byref(done), errs, _stream_ptr(stream)), "cpa_admm_rpca")
         return Lout, Sout, np.array(errs[:done.value])
+
+
+def cpa_set_option(h: Handle, option: int, value: int):
+    _check(load().cpa_set_option(h.ptr, int(option), int(value)), "cpa_set_option")

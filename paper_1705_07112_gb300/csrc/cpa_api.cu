@@ -29,6 +29,7 @@ struct cpa_ctx {
     double *d_coef = nullptr;
     int last_L = 0;
     bool have_last = false;
+    int series = CPA_SERIES_FORWARD;   // how the filter's series is summed
     // diagnostics
     bool profiling = false;
     int64_t launches[CPA_NSTAGES] = {};
@@ -411,6 +412,7 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
     // latency-bound, and a single BF16 rounding of a tiny matrix is not
     // averaged out).
     const int nsplit_rec = (prec == CPA_BF16X3 || p < kSplitRecBelow) ? 3 : 1;
+    const int clenshaw = h->series == CPA_SERIES_CLENSHAW ? 1 : 0;
     ShrinkParams sp_ = to_params(sh);
 
     // operand preparation for the tensor-core path: X and X^T as BF16 hi/lo
@@ -471,7 +473,7 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
         StageScope sc(h, CPA_STAGE_SHIFT, st, 1);
         CK(shift_init(w.G, w.ldp, (int)p, w.out + 3, w.coef, L, tc ? nullptr : w.A, w.Z[1], w.H, w.ldp,
                       tc ? w.Ahi : nullptr, tc ? w.Alo : nullptr, tc ? w.Zhi[1] : nullptr,
-                      tc ? w.Zlo[1] : nullptr, w.ldp, st, h->num_sms));
+                      tc ? w.Zlo[1] : nullptr, w.ldp, st, h->num_sms, clenshaw));
     }
     // recurrence with fused accumulation: Psi_k = 2 B_hat Psi_{k-1} - Psi_{k-2}, H += c_k Psi_k.
     // Ring: Psi_k overwrites Psi_{k-2} in slot k&1; Psi_0 = Id is implicit.
@@ -496,7 +498,7 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
         TcOperand a;
         a.hi = w.Ahi; a.lo = w.Alo; a.ld = w.ldp; a.rows = (int)p;
         CK(gemm_tc_recurrence((int)p, a, nsplit_rec, e, 2, L, w.Z, w.Zhi, w.Zlo, (unsigned int *)(w.flag + 2), st,
-                              h->num_sms));
+                              h->num_sms, clenshaw, L));
     }
     for (int k = 2; k < L && !tc; ++k) {
         StageScope sc(h, CPA_STAGE_RECUR, st, 1);
@@ -514,6 +516,17 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
         e.coef = w.coef;
         e.k = k;
         e.symmetric_upper = 1;
+        if (clenshaw) {
+            // b_kk = 2 B_hat b_{kk+1} - b_{kk+2} + c_kk Id, kk = L-1-k; b_{L-1} =
+            // c_{L-1} Id enters the first step on the diagonal; b_0 goes to H
+            const int kk = L - 1 - k;
+            e.D = kk == 0 ? w.H : w.Z[cur];
+            e.diag = 0.f;
+            e.dcoef = w.coef;
+            e.dk = kk;
+            e.dk2 = (k == 2) ? L - 1 : -1;
+            e.H = nullptr;
+        }
         if (!tc) {
             CK(gemm_f32((int)p, (int)p, (int)p, w.A, w.ldp, true, w.Z[prev], w.ldp, true, e, st));
         } else {
@@ -528,6 +541,13 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
             b.hi = w.Zhi[prev]; b.lo = w.Zlo[prev]; b.ld = w.ldp; b.rows = (int)p;
             CK(gemm_tc((int)p, (int)p, (int)p, a, b, nsplit_rec, e, st, h->num_sms));
         }
+    }
+    // Clenshaw's closing step: H = (b_0 - b_2) / 2, b_2 in ring slot (L-1)&1
+    // (L = 3: b_2 = c_2 Id); the tensor-core path keeps the lower triangle
+    if (clenshaw && L >= 3) {
+        StageScope sc(h, CPA_STAGE_RECUR, st, 1);
+        CK(clenshaw_finish(w.H, L == 3 ? nullptr : w.Z[(L - 1) & 1], (int)p, w.ldp, w.coef, tc ? 1 : 0, st,
+                           h->num_sms));
     }
     // with the sparsity option the filter applied to X is T^T H T (Eq. SVD_fil)
     float *Hf = w.H;
@@ -606,6 +626,16 @@ cpa_status cpa_get_coeffs(cpa_handle h, double *c_out, int L, void *stream) {
 }  // extern "C"
 
 extern "C" {
+
+cpa_status cpa_set_option(cpa_handle h, int option, int value) {
+    if (!h) return CPA_ERR_INVALID_ARG;
+    if (option == CPA_OPT_SERIES) {
+        if (value != CPA_SERIES_FORWARD && value != CPA_SERIES_CLENSHAW) return CPA_ERR_INVALID_ARG;
+        h->series = value;
+        return CPA_OK;
+    }
+    return CPA_ERR_INVALID_ARG;
+}
 
 cpa_status cpa_profile_enable(cpa_handle h, int enable) {
     if (!h) return CPA_ERR_INVALID_ARG;

@@ -16,7 +16,7 @@ __device__ __forceinline__ void epi_store(const Epilogue &e, float ck, int i, in
     float v = e.s_acc * acc;
     if (e.C) v = fmaf(e.s_c, e.C[(int64_t)i * e.ldc + j], v);
     if (e.C2) v = fmaf(e.s_c2, e.C2[(int64_t)i * e.ldc2 + j], v);
-    if (i == j) v += e.diag;
+    if (i == j) v += epilogue_diag(e);
     e.D[(int64_t)i * e.ldd + j] = v;
     if (e.H) {
         float *hp = e.H + (int64_t)i * e.ldh + j;

@@ -172,6 +172,12 @@ struct MultiStep {
     float *z[2] = {nullptr, nullptr};
     __nv_bfloat16 *zhi[2] = {nullptr, nullptr}, *zlo[2] = {nullptr, nullptr};
     unsigned int *bar = nullptr;
+    // Clenshaw's sum instead of the forward recurrence: step k produces
+    // b_{L-1-k} = 2 B_hat b_{L-k} - b_{L+1-k} + c_{L-1-k} Id in the same ring
+    // (b_{L-1} = c_{L-1} Id enters the first step as a diagonal term), no
+    // running sum; the last step writes b_0 into H's array
+    int clenshaw = 0;
+    int L = 0;
 };
 
 __device__ __forceinline__ void fence_proxy_async_global() {
@@ -304,7 +310,7 @@ __device__ __forceinline__ void epilogue_sym_block(const Epilogue &e, const Step
                                                    float ck, int M, int N,
                                                    int r0, int j0, int lane, const float *acc, EpiSmem &es,
                                                    uint64_t *bar, uint32_t &phase, volatile int *abort_flag,
-                                                   bool preloaded) {
+                                                   bool preloaded, const CUtensorMap *dmap) {
     const bool diag = (j0 == r0);
     const bool any_load = e.C || e.C2 || e.H;
     if (!preloaded) epilogue_issue_loads(e, maps, hmap, r0, j0, lane, es, bar);
@@ -377,7 +383,7 @@ __device__ __forceinline__ void epilogue_sym_block(const Epilogue &e, const Step
     fence_proxy_async();
     __syncwarp();
     if (lane == 0) {
-        tma_store_2d(&maps.d, es.c, r0, j0);
+        tma_store_2d(dmap, es.c, r0, j0);
         if (e.H) tma_store_2d(&hmap, es.h, r0, j0);
         if (e.Dhi) {
             tma_store_2d(&maps.dhi, es.hi, r0, j0);
@@ -607,7 +613,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int k = ms.k_first; k < ms.k_end && alive; ++k) {
             Epilogue es_e = e;
             const int par = ms.multi ? (k & 1) : 0;
-            if (ms.multi) {
+            bool final_to_h = false;
+            if (ms.multi && !ms.clenshaw) {
                 es_e.D = ms.z[par];
                 es_e.C = (k == 2) ? nullptr : ms.z[par];
                 es_e.C2 = ms.z[par ^ 1];
@@ -615,7 +622,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                 es_e.Dlo = ms.zlo[par];
                 es_e.diag = (k == 2) ? -1.f : 0.f;
                 es_e.k = k;
+            } else if (ms.multi) {
+                const int kk = ms.L - 1 - k;   // b_kk
+                const bool first = (k == ms.k_first);
+                final_to_h = (kk == 0);
+                es_e.D = final_to_h ? e.H : ms.z[par];
+                es_e.C = first ? nullptr : ms.z[par];   // b_{kk+2}
+                es_e.C2 = ms.z[par ^ 1];                 // b_{kk+1}
+                es_e.Dhi = ms.zhi[par];
+                es_e.Dlo = ms.zlo[par];
+                es_e.diag = (float)(e.coef[kk] - (first ? e.coef[ms.L - 1] : 0.0));
+                es_e.H = nullptr;
+                es_e.k = k;
             }
+            const CUtensorMap *dmap = final_to_h ? &maps.h : &maps.s[par].d;
             const float ck = es_e.H ? (float)es_e.coef[es_e.k] : 0.f;
             for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
                 const int buf = local & 1;
@@ -651,7 +671,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (sym) {
                         if (j0 < r0) continue;   // block below the diagonal: written as another block's mirror
                         epilogue_sym_block(es_e, maps.s[par], maps.h, ck, M, N, r0, j0, lane, acc, es, bar, ephase,
-                                           abort_flag, c == c_pre);
+                                           abort_flag, c == c_pre, dmap);
                     } else {
                         epilogue_general_block(es_e, M, N, r0, j0, lane, acc, es);
                     }
@@ -859,7 +879,7 @@ cudaError_t dispatch_bn(int bn, F f) {
 
 cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epilogue &e, int k_first, int k_end,
                                float *const z[2], __nv_bfloat16 *const zhi[2], __nv_bfloat16 *const zlo[2],
-                               unsigned int *bar, cudaStream_t st, int num_sms) {
+                               unsigned int *bar, cudaStream_t st, int num_sms, int clenshaw, int L) {
     if (p <= 0 || k_end <= k_first) return cudaSuccess;
     if (!load_encode()) return cudaErrorNotSupported;
     if ((A.ld % 8) || ((uintptr_t)A.hi % 16) || !e.symmetric_upper || !e.H || !bar) return cudaErrorInvalidValue;
@@ -881,6 +901,8 @@ cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epil
         ms.zlo[i] = zlo[i];
     }
     ms.bar = bar;
+    ms.clenshaw = clenshaw;
+    ms.L = L;
     TcOperand B;
     B.ld = A.ld;
     B.rows = p;

@@ -77,7 +77,17 @@ struct Epilogue {
     int64_t ldb = 0;
     int symmetric_upper = 0;
     int sym_full_d = 0;
+    // diagonal term read on the device: diag + dcoef[dk] - (dk2 >= 0 ? dcoef[dk2] : 0)
+    const double *dcoef = nullptr;
+    int dk = 0, dk2 = -1;
 };
+
+// The diagonal term of an epilogue (host value plus the device coefficients).
+__device__ __forceinline__ float epilogue_diag(const Epilogue &e) {
+    float d = e.diag;
+    if (e.dcoef) d += (float)(e.dcoef[e.dk] - (e.dk2 >= 0 ? e.dcoef[e.dk2] : 0.0));
+    return d;
+}
 
 // SIMT FP32 GEMM: out(i,j) = epi(sum_k A(i,k) B(j,k)),  i < M, j < N, k < K.
 // a_kmajor: A(i,k) = A[i*lda + k], else A[k*lda + i]; likewise B.
@@ -103,7 +113,7 @@ cudaError_t gemm_tc(int M, int N, int K, const TcOperand &A, const TcOperand &B,
 // zhi/zlo[k&1]; it reads Psi_{k-1} from slot (k&1)^1.  bar: one device word.
 cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epilogue &e, int k_first, int k_end,
                                float *const z[2], __nv_bfloat16 *const zhi[2], __nv_bfloat16 *const zlo[2],
-                               unsigned int *bar, cudaStream_t st, int num_sms);
+                               unsigned int *bar, cudaStream_t st, int num_sms, int clenshaw = 0, int L = 0);
 
 // Sparsity-based reduction helpers (sparsify.cu).
 cudaError_t make_transform(int type, int p, float *T, int64_t ld, cudaStream_t st, int num_sms);
@@ -139,7 +149,12 @@ cudaError_t device_coeffs(const double *lam_dev, double lam_host, int L, const S
 // Z1 as BF16 hi/lo.
 cudaError_t shift_init(const float *G, int64_t ldg, int p, const double *lam, const double *c, int L, float *A,
                        float *Z1, float *H, int64_t ld, __nv_bfloat16 *Athi, __nv_bfloat16 *Atlo,
-                       __nv_bfloat16 *Z1hi, __nv_bfloat16 *Z1lo, int64_t ldb, cudaStream_t st, int num_sms);
+                       __nv_bfloat16 *Z1hi, __nv_bfloat16 *Z1lo, int64_t ldb, cudaStream_t st, int num_sms,
+                       int clenshaw = 0);
+// Clenshaw's closing step H = (b_0 - b_2) / 2 with b_0 in H and b_2 in B2
+// (B2 null: b_2 = c[2] Id); lower triangle only when lower_only.
+cudaError_t clenshaw_finish(float *H, const float *B2, int p, int64_t ld, const double *c, int lower_only,
+                            cudaStream_t st, int num_sms);
 // hi/lo split of a symmetric p x p matrix valid in its lower triangle, both
 // triangles written.
 cudaError_t split_sym_lower(const float *S, int p, int64_t lds, __nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t ldo,

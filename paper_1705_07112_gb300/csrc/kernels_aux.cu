@@ -177,24 +177,28 @@ __device__ __forceinline__ void put_split(__nv_bfloat16 *hi, __nv_bfloat16 *lo, 
 
 // A = (2/lambda) G - Id;  Z1 = A;  H = c0/2 Id + c1 A  (the initial sum of
 // Algorithm 1).  Tensor-core path: At = (2/lambda) G and Z1 as BF16 hi/lo.
+// Clenshaw's sum (L >= 3): Z1 = b_{L-2} = c_{L-2} Id + 2 c_{L-1} A instead.
 __global__ void shift_kernel(const float *__restrict__ G, int64_t ldg, int p, const double *lam,
                              const double *c, int L, float *A, float *Z1, float *H, int64_t ld,
                              __nv_bfloat16 *Athi, __nv_bfloat16 *Atlo, __nv_bfloat16 *Z1hi, __nv_bfloat16 *Z1lo,
-                             int64_t ldb) {
+                             int64_t ldb, int clenshaw) {
     float s = (float)(2.0 / lam[0]);
     float c0h = (float)(0.5 * c[0]);
     float c1 = L > 1 ? (float)c[1] : 0.f;
+    const bool cl = clenshaw && L >= 3;
+    const float zc = cl ? (float)c[L - 2] : 0.f, za = cl ? (float)(2.0 * c[L - 1]) : 1.f;
     // a block per row (grid-stride), threads across the row: no 64-bit
     // division per element
     for (int i = blockIdx.x; i < p; i += gridDim.x)
     for (int j = threadIdx.x; j < p; j += blockDim.x) {
         float at = s * G[(int64_t)i * ldg + j];
         float a = at - (i == j ? 1.f : 0.f);
+        const float z1 = za * a + (i == j ? zc : 0.f);
         if (A) A[(int64_t)i * ld + j] = a;
-        if (Z1) Z1[(int64_t)i * ld + j] = a;
+        if (Z1) Z1[(int64_t)i * ld + j] = z1;
         H[(int64_t)i * ld + j] = c1 * a + (i == j ? c0h : 0.f);
         if (Athi) put_split(Athi, Atlo, (int64_t)i * ldb + j, at);
-        if (Z1hi) put_split(Z1hi, Z1lo, (int64_t)i * ldb + j, a);
+        if (Z1hi) put_split(Z1hi, Z1lo, (int64_t)i * ldb + j, z1);
     }
 }
 
@@ -531,12 +535,26 @@ cudaError_t device_coeffs(const double *lam_dev, double lam_host, int L, const S
     return cudaGetLastError();
 }
 
+// H = (b_0 - b_2) / 2, b_0 in H, b_2 in B2 or c[2] Id.
+__global__ void clenshaw_finish_kernel(float *H, const float *B2, int p, int64_t ld, const double *c,
+                                       int lower_only) {
+    const float c2 = B2 ? 0.f : (float)c[2];
+    for (int i = blockIdx.x; i < p; i += gridDim.x)
+        for (int j = threadIdx.x; j <= (lower_only ? i : p - 1); j += blockDim.x) {
+            const int64_t o = (int64_t)i * ld + j;
+            const float b2 = (B2 ? B2[o] : 0.f) + (i == j ? c2 : 0.f);
+            H[o] = 0.5f * (H[o] - b2);
+        }
+}
+
 cudaError_t shift_init(const float *G, int64_t ldg, int p, const double *lam, const double *c, int L, float *A,
                        float *Z1, float *H, int64_t ld, __nv_bfloat16 *Athi, __nv_bfloat16 *Atlo,
-                       __nv_bfloat16 *Z1hi, __nv_bfloat16 *Z1lo, int64_t ldb, cudaStream_t st, int num_sms) {
+                       __nv_bfloat16 *Z1hi, __nv_bfloat16 *Z1lo, int64_t ldb, cudaStream_t st, int num_sms,
+                       int clenshaw) {
     int blocks = std::min(p, num_sms * 8);   // a block per row, grid-stride
     if (blocks < 1) blocks = 1;
-    shift_kernel<<<blocks, 256, 0, st>>>(G, ldg, p, lam, c, L, A, Z1, H, ld, Athi, Atlo, Z1hi, Z1lo, ldb);
+    shift_kernel<<<blocks, 256, 0, st>>>(G, ldg, p, lam, c, L, A, Z1, H, ld, Athi, Atlo, Z1hi, Z1lo, ldb,
+                                         clenshaw);
     return cudaGetLastError();
 }
 
@@ -560,6 +578,14 @@ cudaError_t check_finite(const float *X, int64_t rows, int64_t cols, int64_t ldx
     int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 8);
     if (blocks < 1) blocks = 1;
     check_finite_kernel<<<blocks, 256, 0, st>>>(X, rows, cols, ldx, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t clenshaw_finish(float *H, const float *B2, int p, int64_t ld, const double *c, int lower_only,
+                            cudaStream_t st, int num_sms) {
+    int blocks = std::min(p, num_sms * 8);
+    if (blocks < 1) blocks = 1;
+    clenshaw_finish_kernel<<<blocks, 256, 0, st>>>(H, B2, p, ld, c, lower_only);
     return cudaGetLastError();
 }
 

@@ -201,3 +201,32 @@ def test_video_background_full_size_sampled(cpa, handle, prec):
     w = inputs.video_background()
     s = O.Shrink(O.SOFT, w.shrink.tau)
     sampled_rows_check(cpa, handle, w.X, s, w.L, prec, [0, 8191], TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
+def test_clenshaw_series_matches_oracle(cpa, handle, prec):
+    """The series summed by Clenshaw's recurrence (CPA_OPT_SERIES) against
+    the oracle's Algorithm 1 at the same L and Lambda_max, across shapes
+    (one tile, ragged multi-tile, tall, wide) and orders including the
+    boundary cases L = 1, 2, 3 (no product, no step, a single step)."""
+    from paper_1705_07112_gb300 import _lib
+    rng = np.random.default_rng(77)
+    _lib.cpa_set_option(handle, _lib.OPT_SERIES, _lib.SERIES_CLENSHAW)
+    try:
+        for shape in [(96, 64), (300, 170), (170, 300), (129, 257), (1, 7)]:
+            X64 = (rng.standard_normal((shape[0], 5)) @ rng.standard_normal((5, shape[1]))
+                   + 0.1 * rng.standard_normal(shape)).astype(np.float32).astype(np.float64)
+            lam = oracle_lambda(X64)
+            for kind in (O.SOFT, O.HARD):
+                s = shrink_of(kind, X64)
+                for L in (1, 2, 3, 4, 20):
+                    got = run(cpa, handle, X64.astype(np.float32), s, L, lam, prec)
+                    ref = O.cpa(X64, s, L, lam)
+                    assert rel(got, ref) <= TOL[prec], (shape, kind, L, rel(got, ref))
+                    assert rel(got, O.cpa_clenshaw(X64, s, L, lam)) <= TOL[prec]
+    finally:
+        _lib.cpa_set_option(handle, _lib.OPT_SERIES, _lib.SERIES_FORWARD)
+    with pytest.raises(_lib.CpaError):
+        _lib.cpa_set_option(handle, _lib.OPT_SERIES, 7)
+    with pytest.raises(_lib.CpaError):
+        _lib.cpa_set_option(handle, 99, 0)
