@@ -78,3 +78,41 @@ def test_cpa_run_tracks_the_exact_run():
     Le, _, _ = A.rpca_admm(D, eta / rho, 30, A.svt_exact(1.0 / rho))
     Lc, _, _ = A.rpca_admm(D, eta / rho, 30, A.svt_cpa(1.0 / rho, 120))
     assert np.linalg.norm(Lc - Le) / np.linalg.norm(Le) < 2e-2
+
+
+def test_eps_schedule_is_the_papers_piecewise_rule():
+    """Eq. recommendation_epsilon: 0.5e-4 above E_l = 0.03, 1.5e-4 down to
+    (and excluding) E_m = 6e-4, 0.5e-3 below; E_l itself and E_m itself
+    fall in the lower branch of their comparison."""
+    assert A.eps_fraction(2.0) == 0.5e-4
+    assert A.eps_fraction(0.0300001) == 0.5e-4
+    assert A.eps_fraction(0.03) == 1.5e-4
+    assert A.eps_fraction(6.0001e-4) == 1.5e-4
+    assert A.eps_fraction(6e-4) == 0.5e-3
+    assert A.eps_fraction(0.0) == 0.5e-3
+
+
+def test_lambda_bound_sym_equals_the_gram_bound():
+    """On S = X^T X the symmetric-matrix bound is the library's bound of X
+    (the C oracle's implementation of the same definition)."""
+    X = RNG.standard_normal((30, 12))
+    v0 = O.start_vector(0x1705071120000000, 12)
+    for iters in (1, 5, 20):
+        ref = O.lambda_bound(X, iters, 0.01, v0)["lam"]
+        assert abs(A.lambda_bound_sym(X.T @ X, iters, 0.01, v0) - ref) <= 1e-12 * ref
+
+
+def test_sparse_svt_reduces_to_dense_when_everything_is_kept():
+    """With a fraction keeping all p^2 entries and T = Id the sparse step is
+    the dense Algorithm 1 with the Gram bound."""
+    X = RNG.standard_normal((20, 9))
+    f = A.svt_cpa_sparse(0.5, 12, np.eye(9))
+    saved = A.eps_fraction
+    try:
+        A.eps_fraction = lambda E: 1.0
+        got = f(X, 1.0)
+    finally:
+        A.eps_fraction = saved
+    lam = O.lambda_bound(X, 20, 0.01, O.start_vector(0x1705071120000000, 9))["lam"]
+    assert np.allclose(got, O.cpa(X, O.Shrink(O.SOFT, 0.5), 12, lam), atol=1e-12)
+    assert A.kth_largest_abs(np.array([[3.0, -5.0], [1.0, 2.0]]), 2) == 3.0
