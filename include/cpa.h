@@ -384,7 +384,12 @@ CPA_API cpa_status cpa_batch_read_choices(cpa_batch b, int *host_L, int *host_fa
  *
  * cpa_admm_create: solver for m x n problems on the handle's device; owns
  *   6 m n floats of state (m n <= 2^31).
- * cpa_admm_rpca: dD device m x n (row stride ldd >= n); dL, dS device m x n
+ * cpa_admm_rpca: sp (optional) applies the sparsity-based reduction in every
+ *   shrinkage; with schedule != 0 (sp->mode must be CPA_SPARSE_TOPK) the
+ *   kept fraction follows Section V-D's rule (Eq. recommendation_epsilon)
+ *   on the current E_t: 0.5e-4 of p^2 while E_t > 0.03, 1.5e-4 while
+ *   E_t > 6e-4, 0.5e-3 below (one host synchronisation per iteration).
+ *   dD device m x n (row stride ldd >= n); dL, dS device m x n
  *   contiguous outputs, the last z1 (low-rank, exactly the shrinkage output)
  *   and z2 (sparse); they must not overlap each other or dD.  Runs
  *   max_iters iterations, or stops after iteration t when tol > 0 and
@@ -398,8 +403,8 @@ typedef struct cpa_admm_ctx *cpa_admm;
 CPA_API cpa_status cpa_admm_create(cpa_handle h, int64_t m, int64_t n, cpa_admm *out);
 CPA_API cpa_status cpa_admm_destroy(cpa_admm a);
 CPA_API cpa_status cpa_admm_rpca(cpa_admm a, const float *dD, int64_t ldd, double tau_nuclear, double tau_l1, int L,
-                                 int prec, int max_iters, double tol, float *dL, float *dS, int *iters_done,
-                                 double *errors, void *stream);
+                                 int prec, const cpa_sparsify *sp, int schedule, int max_iters, double tol,
+                                 float *dL, float *dS, int *iters_done, double *errors, void *stream);
 
 #ifdef __cplusplus
 }

@@ -109,8 +109,9 @@ def load(path: str = LIB_PATH):
             "cpa_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
             "cpa_admm_create": (ctypes.c_int, [_vp, _i64, _i64, _P(_vp)]),
             "cpa_admm_destroy": (ctypes.c_int, [_vp]),
-            "cpa_admm_rpca": (ctypes.c_int, [_vp, _vp, _i64, _d, _d, ctypes.c_int, ctypes.c_int, ctypes.c_int, _d,
-                                             _vp, _vp, _P(ctypes.c_int), _P(_d), _vp]),
+            "cpa_admm_rpca": (ctypes.c_int, [_vp, _vp, _i64, _d, _d, ctypes.c_int, ctypes.c_int,
+                                             _P(CpaSparsify), ctypes.c_int, ctypes.c_int, _d, _vp, _vp,
+                                             _P(ctypes.c_int), _P(_d), _vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -490,9 +491,12 @@ class Admm:
         except Exception:
             pass
 
-    def rpca(self, D, tau_nuclear, tau_l1, L, iters, prec="fp32", tol=0.0, Lout=None, Sout=None, stream=None):
+    def rpca(self, D, tau_nuclear, tau_l1, L, iters, prec="fp32", tol=0.0, Lout=None, Sout=None, stream=None,
+             sparsify=None, schedule=False):
         """Returns (L, S, errors); D a float32 CUDA tensor m x n (row stride
-        D.stride(0)); errors[t] = E after iteration t."""
+        D.stride(0)); errors[t] = E after iteration t.  sparsify: None or
+        (transform, mode, eps_or_frac); schedule: the kept fraction follows
+        E_t (mode must be SPARSE_TOPK)."""
         import torch
         if not (D.is_cuda and D.dtype == torch.float32 and D.dim() == 2 and D.stride(1) == 1 and
                 tuple(D.shape) == (self.m, self.n)):
@@ -503,7 +507,9 @@ class Admm:
         errs = (_d * int(iters))()
         p = PREC[prec] if isinstance(prec, str) else int(prec)
         _check(self._lib.cpa_admm_rpca(self.ptr, ctypes.c_void_p(D.data_ptr()), D.stride(0), float(tau_nuclear),
-                                       float(tau_l1), int(L), p, int(iters), float(tol),
+                                       float(tau_l1), int(L), p,
+                                       ctypes.byref(CpaSparsify(*sparsify)) if sparsify else None,
+                                       1 if schedule else 0, int(iters), float(tol),
                                        ctypes.c_void_p(Lout.data_ptr()), ctypes.c_void_p(Sout.data_ptr()),
                                        ctypes.byref(done), errs, _stream_ptr(stream)), "cpa_admm_rpca")
         return Lout, Sout, np.array(errs[:done.value])

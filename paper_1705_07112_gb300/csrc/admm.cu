@@ -142,11 +142,12 @@ cpa_status cpa_admm_destroy(cpa_admm a) {
 }
 
 cpa_status cpa_admm_rpca(cpa_admm a, const float *dD, int64_t ldd, double tau_nuclear, double tau_l1, int L,
-                         int prec, int max_iters, double tol, float *dL, float *dS, int *iters_done,
-                         double *errors, void *stream) {
+                         int prec, const cpa_sparsify *sp, int schedule, int max_iters, double tol, float *dL,
+                         float *dS, int *iters_done, double *errors, void *stream) {
     if (!a || !dD || !dL || !dS || ldd < a->n || !(tau_nuclear >= 0.0) || !(tau_l1 >= 0.0) || L < 1 ||
         max_iters < 1 || !(tol >= 0.0) || !std::isfinite(tau_nuclear) || !std::isfinite(tau_l1))
         return CPA_ERR_INVALID_ARG;
+    if (schedule && (!sp || sp->mode != CPA_SPARSE_TOPK)) return CPA_ERR_INVALID_ARG;
     const int64_t m = a->m, n = a->n, total = m * n;
     // outputs must not overlap the input or each other
     auto overlap = [](const void *p, size_t pb, const void *q, size_t qb) {
@@ -173,9 +174,26 @@ cpa_status cpa_admm_rpca(cpa_admm a, const float *dD, int64_t ldd, double tau_nu
     sh.kind = CPA_SOFT;
     sh.tau = tau_nuclear;
     int done = 0;
+    cpa_sparsify spt{};
+    if (sp) spt = *sp;
     for (int t = 0; t < max_iters; ++t) {
+        if (schedule) {
+            // the current E_t picks the kept fraction (Eq. recommendation_epsilon);
+            // the start l_1 = 1/3 after l_0 = 1 has E = 2
+            double E = 2.0;
+            if (t > 0) {
+                double e2[2];
+                if ((r = admm_cuda(cudaMemcpyAsync(e2, a->acc + 2 * (t - 1), sizeof e2, cudaMemcpyDeviceToHost,
+                                                   st))) != CPA_OK)
+                    return r;
+                if ((r = admm_cuda(cudaStreamSynchronize(st))) != CPA_OK) return r;
+                E = e2[1] > 0.0 ? std::sqrt(e2[0] / e2[1]) : 0.0;
+            }
+            spt.eps_or_frac = E > 0.3e-1 ? 0.5e-4 : (E > 6e-4 ? 1.5e-4 : 0.5e-3);
+        }
         // z1 = prox_{(1/rho)|.|_*}(l + u1): Algorithm 1, Lambda_max computed
-        if ((r = cpa_svt(a->h, w, m, n, n, &sh, L, 0.0, prec, nullptr, dL, n, stream)) != CPA_OK) return r;
+        if ((r = cpa_svt(a->h, w, m, n, n, &sh, L, 0.0, prec, sp ? &spt : nullptr, dL, n, stream)) != CPA_OK)
+            return r;
         admm_step_kernel<<<blocks, kAdmmThreads, 0, st>>>(dD, ldd, (int)m, (int)n, l, s, u1, u2, u3, w, dL, dS,
                                                           (float)tau_l1, a->acc + 2 * t);
         if ((r = admm_cuda(cudaGetLastError())) != CPA_OK) return r;

@@ -141,5 +141,28 @@ def video_background(seed_index=0, m=4096, n=8192, rank=5, frac=0.03, sigma=0.01
                     ShrinkSpec(kind, tau), L, 20, {"sig_hat": sig_hat})
 
 
+def smooth_video(seed_index=0, side=16, frames=96, rank=3, frac=0.03, sigma=0.01):
+    """Background-modelling frames whose background is smooth in space and
+    time, so that a DCT over the frame index concentrates the frames' Gram
+    matrix: D (side^2 pixels x frames) = sum_r A_r F_r^T + sparse +-U[0.5,1]
+    foreground on frac of the entries + N(0, sigma^2), with A_r low-frequency
+    2-D cosines over the frame (frequencies 0..2 per axis) and F_r
+    low-frequency cosines over time (frequencies 0..2), random amplitudes."""
+    rng = rng_for(6, seed_index)
+    y, x = np.meshgrid(np.arange(side) + 0.5, np.arange(side) + 0.5, indexing="ij")
+    t = np.arange(frames) + 0.5
+    D = np.zeros((side * side, frames))
+    for _ in range(rank):
+        a, b, c = rng.integers(0, 3, size=3)
+        A = np.cos(np.pi * a * x / side) * np.cos(np.pi * b * y / side)
+        F = np.cos(np.pi * c * t / frames)
+        D += rng.uniform(0.5, 1.5) * np.outer(A.ravel(), F)
+    D += sparse_pm_uniform(rng, side * side, frames, frac, 0.5, 1.0)
+    D += sigma * rng.standard_normal(D.shape)
+    m, n = D.shape
+    mu = m * n / (4.0 * np.abs(D).sum())
+    return D.astype(np.float32), mu, 1.0 / math.sqrt(max(m, n))
+
+
 def random_gaussian(rng, m, n, scale=1.0):
     return (scale * rng.standard_normal((m, n))).astype(np.float32)

@@ -99,3 +99,42 @@ def test_admm_full_frame_precisions(lib):
     assert d3 <= 1e-2
     ad.close()
     h.close()
+
+
+def test_admm_with_the_sparsity_schedule_matches_the_oracle(lib):
+    """The ADMM with the sparsity-based reduction (DCT over the frame index)
+    and Section V-D's threshold schedule on smooth frames (96 frames, so the
+    three kept fractions keep 1, 2 and 5 entries of the 96 x 96 Phi) against
+    the FP64 oracle ADMM with the same schedule, FP32 shrinkage."""
+    import math
+    import torch
+    D, mu, eta = inputs.smooth_video()
+    m, n = D.shape
+    p = min(m, n)
+    T = np.zeros((p, p))
+    for k in range(p):
+        s = math.sqrt((1.0 if k == 0 else 2.0) / p)
+        T[k] = s * np.cos(np.pi * (2 * np.arange(p) + 1) * k / (2 * p))
+    iters = 16   # E_t falls below E_l = 0.03 at the fifteenth iterate
+    Lo, So, Eo = A.rpca_admm(D.astype(np.float64), eta / mu, iters + 1, A.svt_cpa_sparse(1.0 / mu, 30, T),
+                             schedule=True)
+    Ld, _, _ = A.rpca_admm(D.astype(np.float64), eta / mu, iters, A.svt_cpa(1.0 / mu, 30))
+    Lo, So, _ = A.rpca_admm(D.astype(np.float64), eta / mu, iters, A.svt_cpa_sparse(1.0 / mu, 30, T), schedule=True)
+    h = lib.Handle(0)
+    ad = lib.Admm(h, m, n)
+    Dd = torch.from_numpy(D).cuda()
+    Lg, Sg, E = ad.rpca(Dd, 1.0 / mu, eta / mu, 30, iters, prec="fp32", sparsify=(lib.T_DCT, lib.SPARSE_TOPK, 0.0),
+                        schedule=True)
+    torch.cuda.synchronize()
+    assert rel(Lg.cpu().numpy(), Lo) <= 1e-3, rel(Lg.cpu().numpy(), Lo)
+    assert rel(Sg.cpu().numpy(), So) <= 1e-3, rel(Sg.cpu().numpy(), So)
+    assert np.allclose(E, Eo[1:iters + 1], rtol=1e-2)
+    # the schedule reached more than one branch, and the reduction changed the result
+    fr = sorted({A.eps_fraction(e) for e in Eo[:iters]})
+    print("\nkept fractions used:", fr, " E:", ["%.2e" % e for e in Eo[:iters]])
+    assert len(fr) >= 2
+    assert rel(Lo, Ld) > 1e-3
+    with pytest.raises(lib.CpaError):
+        ad.rpca(Dd, 1.0 / mu, eta / mu, 30, 3, sparsify=(lib.T_DCT, lib.SPARSE_ABS, 0.1), schedule=True)
+    ad.close()
+    h.close()
