@@ -479,6 +479,7 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
     // Ring: Psi_k overwrites Psi_{k-2} in slot k&1; Psi_0 = Id is implicit.
     // The tensor-core path multiplies by At = (2/lambda) G and applies the
     // shift exactly in the FP32 epilogue:  Psi_k = 2 At Psi_{k-1} - 2 Psi_{k-1} - Psi_{k-2}.
+    int closed = 0;   // Clenshaw's closing step already applied by the launch
     if (tc && L > 2) {
         // every step in one cooperative launch (grid barrier between steps)
         StageScope sc(h, CPA_STAGE_RECUR, st, 1);
@@ -498,7 +499,7 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
         TcOperand a;
         a.hi = w.Ahi; a.lo = w.Alo; a.ld = w.ldp; a.rows = (int)p;
         CK(gemm_tc_recurrence((int)p, a, nsplit_rec, e, 2, L, w.Z, w.Zhi, w.Zlo, (unsigned int *)(w.flag + 2), st,
-                              h->num_sms, clenshaw, L));
+                              h->num_sms, clenshaw, L, &closed));
     }
     for (int k = 2; k < L && !tc; ++k) {
         StageScope sc(h, CPA_STAGE_RECUR, st, 1);
@@ -544,7 +545,7 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
     }
     // Clenshaw's closing step: H = (b_0 - b_2) / 2, b_2 in ring slot (L-1)&1
     // (L = 3: b_2 = c_2 Id); the tensor-core path keeps the lower triangle
-    if (clenshaw && L >= 3) {
+    if (clenshaw && L >= 3 && !closed) {
         StageScope sc(h, CPA_STAGE_RECUR, st, 1);
         CK(clenshaw_finish(w.H, L == 3 ? nullptr : w.Z[(L - 1) & 1], (int)p, w.ldp, w.coef, tc ? 1 : 0, st,
                            h->num_sms));

@@ -4,9 +4,11 @@
 //   K-major in global memory, FP32 accumulation in tensor memory (TMEM).
 //
 // Structure (one CTA per SM, persistent over output tiles of 128 x BN):
-//   warp 0      TMA producer: cp.async.bulk.tensor 2-D loads of A and B
+//   warp 0      TMA producer: cp.async.bulk.tensor loads of A and B
 //               K-slices (64 elements = one 128-byte swizzle row) into a
-//               ring of shared-memory stages, completion on mbarriers.
+//               ring of shared-memory stages, completion on mbarriers; with
+//               K a multiple of 64 the operands are viewed as 3-D
+//               {64, rows, K/64} so one load brings several slices.
 //   warp 1      MMA issuer: allocates TMEM, one elected thread issues
 //               tcgen05.mma kind::f16 (M=128, N=BN, K=16) per 32-byte K step,
 //               tcgen05.commit frees a stage / publishes an accumulator.
@@ -87,6 +89,15 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         "l"(map), "r"(su32(bar)), "r"(x), "r"(y)
         : "memory");
 }
+// 3-D load (x, y, z): used for operand maps viewed as {64, rows, K/64}, so
+// one instruction brings several consecutive 128-byte K slices.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+            su32(dst)),
+        "l"(map), "r"(su32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
 
 // Shared-memory matrix descriptor (tcgen05): K-major, 128-byte swizzle,
 // 8-row atoms 1024 bytes apart (stride byte offset), version 1.
@@ -137,6 +148,35 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Three 8-column loads (one row per lane) completed together.
+__device__ __forceinline__ void tmem_ld8x3(uint32_t ta, uint32_t tb, uint32_t tc, float *a, float *b, float *c) {
+    uint32_t r[24];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%24];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%25];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%26];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
+        : "r"(ta), "r"(tb), "r"(tc)
+        : "memory");
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+        a[x] = __uint_as_float(r[x]);
+        b[x] = __uint_as_float(r[8 + x]);
+        c[x] = __uint_as_float(r[16 + x]);
+    }
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y) {
     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(map),
@@ -178,6 +218,13 @@ struct MultiStep {
     // running sum; the last step writes b_0 into H's array
     int clenshaw = 0;
     int L = 0;
+    // resident: every CTA owns at most one tile, whose FP32 Psi_{k-1},
+    // Psi_{k-2} and H (forward sum) stay in tensor memory between steps
+    // (columns 2 BN.. after the two accumulators); only the first step reads
+    // them from global memory and only the last writes H back (Clenshaw: the
+    // last step also applies the closing H = (b_0 - b_2) / 2).  The FP32
+    // ring arrays are then not written during the launch.
+    int resident = 0;
 };
 
 __device__ __forceinline__ void fence_proxy_async_global() {
@@ -197,11 +244,17 @@ struct EpiSmem {
     uint32_t pad[32 - (32 * 33) % 32];
 };
 
+// A stage holds up to kG consecutive 64-element K slices of A and of B,
+// stored slice after slice (each slice a 128-byte swizzled tile), so one
+// 3-D TMA instruction per operand fills it: issuing TMA instructions costs
+// about 100 cycles each, which bounds a tile's main loop when every K slice
+// takes its own pair of instructions.
 template <int BN>
 struct Smem {
-    static constexpr int kStageA = BM * BK * 2;
-    static constexpr int kStageB = BN * BK * 2;
-    static constexpr int kStages = (BN == 256) ? 3 : (BN == 128 ? 4 : 6);   // BN 64: 6 x 24 KB, 32: 6 x 20 KB
+    static constexpr int kG = (BN == 256) ? 1 : 2;
+    static constexpr int kStageA = BM * BK * 2 * kG;
+    static constexpr int kStageB = BN * BK * 2 * kG;
+    static constexpr int kStages = (BN == 128) ? 2 : 3;   // 256: 3 x 48 KB, 128: 2 x 64, 64: 3 x 48, 32: 3 x 40
     static constexpr int kBytes =
         kStages * (kStageA + kStageB) + 4 * (int)sizeof(EpiSmem) + 1024 /* align */ + 256 /* barriers */;
 };
@@ -409,6 +462,162 @@ __device__ __forceinline__ void epilogue_sym_block(const Epilogue &e, const Step
     }
 }
 
+// Resident recurrence step, one 32 x 32 block of the accumulator held by a
+// warp (lane l owns row r0 + l, acc[c] is column j0 + c, j0 >= r0).  The
+// block's state lives in tensor memory in the same orientation: tC (Psi_{k-2},
+// overwritten by Psi_k), tC2 (Psi_{k-1}) and tH (H, forward sum only), each
+// the address of the block's first column in this warp's lane quarter.
+// from_tmem = false (first step): the inputs come from global memory through
+// the TMA block loads, as in the non-resident step.  The BF16 copies of
+// Psi_k are written as in the non-resident step; FP32 D and H go to global
+// memory only when store_d / store_h.  close: Clenshaw's last step, the
+// value kept is (b_0 - b_2) / 2 with b_2 = C (+ close_diag on the diagonal
+// when b_2 = c_{L-1} Id enters this same step).
+__device__ __forceinline__ void epilogue_res_block(const Epilogue &e, const StepMaps &maps, const CUtensorMap &hmap,
+                                                   float ck, int M, int N, int r0, int j0, int lane,
+                                                   const float *acc, EpiSmem &es, uint64_t *bar, uint32_t &phase,
+                                                   volatile int *abort_flag, bool preloaded, const CUtensorMap *dmap,
+                                                   bool from_tmem, uint32_t tC, uint32_t tC2, uint32_t tH,
+                                                   bool store_d, bool store_h, bool close, float close_diag) {
+    const bool diag = (j0 == r0);
+    const bool hasc = e.C != nullptr, hasc2 = e.C2 != nullptr, hact = e.H != nullptr;
+    if (from_tmem) {
+        // the warp's buffers are rewritten below: the previous block's TMA
+        // stores must have finished reading them
+        if (lane == 0) bulk_wait_read_all();
+        __syncwarp();
+    } else {
+        if (!preloaded) epilogue_issue_loads(e, maps, hmap, r0, j0, lane, es, bar);
+        if (hasc || hasc2 || hact) {
+            mbar_wait(bar, phase, abort_flag);
+            phase ^= 1u;
+        }
+    }
+    uint32_t hl[32];
+    if (!diag) {
+        const float sa = e.s_acc, sc = hasc ? e.s_c : 0.f, sc2 = hasc2 ? e.s_c2 : 0.f;
+#pragma unroll
+        for (int g = 0; g < 32; g += 8) {
+            float cv[8], c2v[8], hv[8];
+            if (from_tmem) {
+                tmem_ld8x3(tC + g, tC2 + g, tH + g, cv, c2v, hv);
+#pragma unroll
+                for (int x = 0; x < 8; ++x) {
+                    cv[x] = hasc ? cv[x] : 0.f;
+                    c2v[x] = hasc2 ? c2v[x] : 0.f;
+                    hv[x] = hact ? hv[x] : 0.f;
+                }
+            } else {
+#pragma unroll
+                for (int x = 0; x < 8; ++x) {
+                    cv[x] = hasc ? es.c[(g + x) * 32 + lane] : 0.f;
+                    c2v[x] = hasc2 ? es.c2[(g + x) * 32 + lane] : 0.f;
+                    hv[x] = hact ? es.h[(g + x) * 32 + lane] : 0.f;
+                }
+            }
+            float vo[8], ho[8];
+#pragma unroll
+            for (int x = 0; x < 8; ++x) {
+                const int c = g + x;
+                float v = fmaf(sc2, c2v[x], fmaf(sc, cv[x], sa * acc[c]));
+                if (close) v = 0.5f * (v - cv[x]);
+                vo[x] = v;
+                ho[x] = fmaf(ck, v, hv[x]);
+                if (store_d) es.c[c * 32 + lane] = v;
+                if (store_h) es.h[c * 32 + lane] = ho[x];
+                const uint32_t p = pack_hilo(v);
+                hl[c] = p;
+                es.hi[c * 32 + lane] = __ushort_as_bfloat16((unsigned short)(p & 0xFFFF));
+                es.lo[c * 32 + lane] = __ushort_as_bfloat16((unsigned short)(p >> 16));
+            }
+            tmem_st8(tC + g, vo);
+            if (hact) tmem_st8(tH + g, ho);
+            if (!from_tmem) tmem_st8(tC2 + g, c2v);   // Psi_{k-1} for the next step
+        }
+    } else {
+        float cv[32], c2v[32], hv[32];
+        if (from_tmem) {
+            // the state holds both triangles of a diagonal block
+            tmem_ld32(tC, cv);
+            tmem_ld32(tC2, c2v);
+            tmem_ld32(tH, hv);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                cv[c] = hasc ? cv[c] : 0.f;
+                c2v[c] = hasc2 ? c2v[c] : 0.f;
+                hv[c] = hact ? hv[c] : 0.f;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                const int a = c >= lane ? c * 32 + lane : lane * 32 + c;   // lower-triangle copy
+                cv[c] = hasc ? es.c[a] : 0.f;
+                c2v[c] = hasc2 ? es.c2[a] : 0.f;
+                hv[c] = hact ? es.h[a] : 0.f;
+            }
+        }
+        __syncwarp();
+        const float diagv = epilogue_diag(e);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            if (c < lane) continue;   // the pair is written by lane c
+            float v = fmaf(e.s_c2, c2v[c], fmaf(e.s_c, cv[c], e.s_acc * acc[c]));
+            if (c == lane) v += diagv;
+            if (close) v = 0.5f * (v - cv[c] - (c == lane ? close_diag : 0.f));
+            const float hn = fmaf(ck, v, hv[c]);
+            const uint32_t p = pack_hilo(v);
+            const __nv_bfloat16 bh = __ushort_as_bfloat16((unsigned short)(p & 0xFFFF));
+            const __nv_bfloat16 bl = __ushort_as_bfloat16((unsigned short)(p >> 16));
+            es.c[c * 32 + lane] = v;
+            es.c[lane * 32 + c] = v;
+            if (hact) {
+                es.h[c * 32 + lane] = hn;
+                es.h[lane * 32 + c] = hn;
+            }
+            es.hi[c * 32 + lane] = bh;
+            es.hi[lane * 32 + c] = bh;
+            es.lo[c * 32 + lane] = bl;
+            es.lo[lane * 32 + c] = bl;
+        }
+        __syncwarp();
+        // this lane's row of the block (both triangles) into tensor memory
+        if (!from_tmem) {
+#pragma unroll
+            for (int g = 0; g < 32; g += 8) tmem_st8(tC2 + g, c2v + g);   // Psi_{k-1} for the next step
+        }
+#pragma unroll
+        for (int c = 0; c < 32; ++c) cv[c] = es.c[c * 32 + lane];
+#pragma unroll
+        for (int g = 0; g < 32; g += 8) tmem_st8(tC + g, cv + g);
+        if (hact) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) hv[c] = es.h[c * 32 + lane];
+#pragma unroll
+            for (int g = 0; g < 32; g += 8) tmem_st8(tH + g, hv + g);
+        }
+    }
+    tmem_st_wait();
+    fence_proxy_async();
+    __syncwarp();
+    if (lane == 0) {
+        if (store_d) tma_store_2d(dmap, es.c, r0, j0);
+        if (store_h) tma_store_2d(&hmap, es.h, r0, j0);
+        if (e.Dhi) {
+            tma_store_2d(&maps.dhi, es.hi, r0, j0);
+            if (e.Dlo) tma_store_2d(&maps.dlo, es.lo, r0, j0);
+        }
+        bulk_commit();
+    }
+    if (diag) return;
+    if (e.Dhi) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) es.t[lane * 33 + c] = hl[c];
+        __syncwarp();
+        store_transposed_bf16x8(e, es.t, M, N, r0, j0, lane);
+        __syncwarp();
+    }
+}
+
 // General (non-symmetric) output: D(i,j) = s_acc acc + diag, stored through
 // the transpose buffer.
 __device__ __forceinline__ void epilogue_general_block(const Epilogue &e, int M, int N, int r0, int j0, int lane,
@@ -458,11 +667,12 @@ __host__ __device__ inline int count_tiles(int tiles_m, int tiles_n, int sym, in
 
 template <int BN>
 __global__ void __launch_bounds__(kThreads, 1)
-    gemm_tc_kernel(const __grid_constant__ TileMaps maps, int M, int N, int K, int nsplit, Epilogue e, MultiStep ms,
-                   int *err) {
+    gemm_tc_kernel(const __grid_constant__ TileMaps maps, int M, int N, int K, int nsplit, int g, Epilogue e,
+                   MultiStep ms, int *err) {
     using S = Smem<BN>;
     constexpr int kStages = S::kStages;
-    constexpr uint32_t kTmemCols = 2 * BN;   // two accumulators
+    // two accumulators, plus three BN-column state slots when resident
+    const uint32_t tmem_cols = ms.resident ? (BN == 32 ? 256u : 512u) : 2u * BN;
     constexpr uint32_t kIdesc = idesc_bf16(BM, BN);
 
     extern __shared__ uint8_t smem_raw[];
@@ -486,6 +696,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int ntiles = count_tiles(tiles_m, tiles_n, sym, BN);
     const int kb_per = (K + BK - 1) / BK;
     const int nkb = kb_per * nsplit;
+    // g > 0: 3-D operand maps with g slices per load (g divides kb_per);
+    // g == 0: 2-D maps, one slice per stage
+    const bool tma3d = S::kG > 1 && g > 0;
+    const int gs = tma3d ? g : 1;
+    const uint32_t stage_bytes = (uint32_t)gs * (uint32_t)(BM + BN) * (uint32_t)(BK * 2);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -503,7 +718,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                     "r"(kTmemCols)
+                     "r"(tmem_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -530,14 +745,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                     int tm, tn;
                     tile_of(t, tiles_m, tiles_n, sym, BN, tm, tn);
                     const int m0 = tm * BM, n0 = tn * BN;
-                    for (int kb = 0; kb < nkb; ++kb) {
+                    for (int kb = 0; kb < nkb; kb += gs) {
                         if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) break;
-                        const int seg = kb / kb_per, kx = (kb % kb_per) * BK;
+                        const int seg = kb / kb_per, z = kb % kb_per;
                         const CUtensorMap *ma = (seg < 2) ? &maps.a_hi : &maps.a_lo;
                         const CUtensorMap *mb = (seg == 1) ? &sm.b_lo : &sm.b_hi;
-                        mbar_expect_tx(&full[stage], S::kStageA + S::kStageB);
-                        tma_load_2d(sA + stage * S::kStageA, ma, &full[stage], kx, m0);
-                        tma_load_2d(sB + stage * S::kStageB, mb, &full[stage], kx, n0);
+                        mbar_expect_tx(&full[stage], stage_bytes);
+                        if (tma3d) {
+                            tma_load_3d(sA + stage * S::kStageA, ma, &full[stage], 0, m0, z);
+                            tma_load_3d(sB + stage * S::kStageB, mb, &full[stage], 0, n0, z);
+                        } else {
+                            tma_load_2d(sA + stage * S::kStageA, ma, &full[stage], z * BK, m0);
+                            tma_load_2d(sB + stage * S::kStageB, mb, &full[stage], z * BK, n0);
+                        }
                         armed_mask |= 1u << stage;
                         armed_phase = (armed_phase & ~(1u << stage)) | (phase << stage);
                         if (++stage == kStages) {
@@ -578,7 +798,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tphase[buf] ^= 1;
                     fence_after();
                     const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
-                    for (int kb = 0; kb < nkb; ++kb) {
+                    for (int kb = 0; kb < nkb; kb += gs) {
                         if (!mbar_wait(&full[stage], phase, abort_flag)) {
                             ok = false;
                             break;
@@ -586,9 +806,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                         fence_after();
                         const uint64_t da = smem_desc(su32(sA + stage * S::kStageA));
                         const uint64_t db = smem_desc(su32(sB + stage * S::kStageB));
+                        for (int sub = 0; sub < gs; ++sub) {
+                            // slice sub starts BM (BN) 128-byte rows further on;
+                            // descriptor addresses count 16-byte units
+                            const uint64_t das = da + (uint64_t)(sub * BM * 8), dbs = db + (uint64_t)(sub * BN * 8);
 #pragma unroll
-                        for (int kk = 0; kk < BK / 16; ++kk)
-                            mma_bf16(d_tmem, da + 2 * kk, db + 2 * kk, kIdesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                            for (int kk = 0; kk < BK / 16; ++kk)
+                                mma_bf16(d_tmem, das + 2 * kk, dbs + 2 * kk, kIdesc,
+                                         (kb > 0 || sub > 0 || kk > 0) ? 1u : 0u);
+                        }
                         mma_commit(&empty[stage]);
                         if (++stage == kStages) {
                             stage = 0;
@@ -637,6 +863,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const CUtensorMap *dmap = final_to_h ? &maps.h : &maps.s[par].d;
             const float ck = es_e.H ? (float)es_e.coef[es_e.k] : 0.f;
+            // resident state: slot par takes Psi_k over Psi_{k-2}, slot par^1
+            // holds Psi_{k-1}, then H
+            const bool res = BN <= 64 && ms.multi && ms.resident;
+            const bool first = (k == ms.k_first), last = (k + 1 == ms.k_end);
+            const uint32_t sC = (uint32_t)(2 * BN + par * BN), sC2 = (uint32_t)(2 * BN + (par ^ 1) * BN),
+                           sH = (uint32_t)(4 * BN);
+            const bool close = res && final_to_h;
+            const float close_diag = (close && first) ? (float)e.coef[ms.L - 1] : 0.f;
+            const bool store_h = res && last && es_e.H != nullptr;
             for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
                 const int buf = local & 1;
                 int tm, tn;
@@ -645,7 +880,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // the first block's inputs do not depend on the accumulator:
                 // load them while the MMAs of this tile are still running
                 int c_pre = -1;
-                if (sym && r0 < M) {
+                if (sym && r0 < M && (!res || first)) {
                     for (int c = 0; c < BN / 32; ++c) {
                         const int j0 = n0 + c * 32;
                         if (j0 < N && j0 >= r0) {
@@ -670,6 +905,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (r0 >= M || j0 >= N) continue;
                     if (sym) {
                         if (j0 < r0) continue;   // block below the diagonal: written as another block's mirror
+                        if constexpr (BN <= 64) {
+                          if (res) {
+                            const uint32_t tq = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(c * 32);
+                            epilogue_res_block(es_e, maps.s[par], maps.h, ck, M, N, r0, j0, lane, acc, es, bar,
+                                               ephase, abort_flag, c == c_pre, dmap, !first, tq + sC, tq + sC2,
+                                               tq + sH, final_to_h, store_h, close, close_diag);
+                            continue;
+                          }
+                        }
                         epilogue_sym_block(es_e, maps.s[par], maps.h, ck, M, N, r0, j0, lane, acc, es, bar, ephase,
                                            abort_flag, c == c_pre, dmap);
                     } else {
@@ -719,7 +963,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     if (warp == 1) {
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(tmem_cols)
                      : "memory");
     }
     if (threadIdx.x == 0 && *abort_flag) atomicExch(err, CPA_ERR_TIMEOUT);
@@ -740,6 +984,20 @@ bool load_encode() {
             g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     });
     return g_encode != nullptr;
+}
+
+// Operand map viewed as {64, rows, K/64} (K a multiple of 64): a box of g
+// consecutive 128-byte swizzled K slices, each box_rows rows high, lands as g
+// stacked slices in shared memory.
+bool make_map3(CUtensorMap *map, const __nv_bfloat16 *ptr, int64_t ld, int rows, int K, int box_rows, int g) {
+    cuuint64_t dims[3] = {(cuuint64_t)BK, (cuuint64_t)rows, (cuuint64_t)(K / BK)};
+    cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), (cuuint64_t)(BK * 2)};
+    cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, (cuuint32_t)g};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)ptr, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 // Operand map: BF16 rows of K elements, 128-byte swizzled K slices.
@@ -784,7 +1042,12 @@ cudaError_t launch(int M, int N, int K, const TcOperand &A, const TcOperand &B, 
     memset(&maps, 0, sizeof(maps));
     const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32, b16 = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     const __nv_bfloat16 *alo = A.lo ? A.lo : A.hi;
-    if (!make_map(&maps.a_hi, A.hi, A.ld, A.rows, K, BM) || !make_map(&maps.a_lo, alo, A.ld, A.rows, K, BM))
+    // grouped 3-D loads need whole 64-element slices (no K tail to fill)
+    const int g = (S::kG > 1 && K % BK == 0 && (K / BK) % S::kG == 0) ? S::kG : 0;
+    auto opmap = [&](CUtensorMap *m, const __nv_bfloat16 *ptr, int64_t ld, int rows, int box_rows) {
+        return g > 0 ? make_map3(m, ptr, ld, rows, K, box_rows, g) : make_map(m, ptr, ld, rows, K, box_rows);
+    };
+    if (!opmap(&maps.a_hi, A.hi, A.ld, A.rows, BM) || !opmap(&maps.a_lo, alo, A.ld, A.rows, BM))
         return cudaErrorInvalidValue;
     if (e.H && !make_block_map(&maps.h, e.H, f32, 4, e.ldh, M, N)) return cudaErrorInvalidValue;
     for (int par = 0; par < (ms.multi ? 2 : 1); ++par) {
@@ -792,7 +1055,7 @@ cudaError_t launch(int M, int N, int K, const TcOperand &A, const TcOperand &B, 
         const __nv_bfloat16 *bhi = ms.multi ? ms.zhi[par ^ 1] : B.hi;
         const __nv_bfloat16 *blo = ms.multi ? ms.zlo[par ^ 1] : B.lo;
         if (!blo) blo = bhi;
-        bool ok = make_map(&sm.b_hi, bhi, B.ld, B.rows, K, BN) && make_map(&sm.b_lo, blo, B.ld, B.rows, K, BN);
+        bool ok = opmap(&sm.b_hi, bhi, B.ld, B.rows, BN) && opmap(&sm.b_lo, blo, B.ld, B.rows, BN);
         if (e.symmetric_upper) {
             const float *D = ms.multi ? ms.z[par] : e.D;
             const float *C2 = ms.multi ? ms.z[par ^ 1] : e.C2;
@@ -809,7 +1072,7 @@ cudaError_t launch(int M, int N, int K, const TcOperand &A, const TcOperand &B, 
     const int tiles = count_tiles((M + BM - 1) / BM, (N + BN - 1) / BN, e.symmetric_upper, BN);
     const int grid = tiles < num_sms ? tiles : num_sms;
     if (!ms.multi) {
-        gemm_tc_kernel<BN><<<grid, kThreads, S::kBytes, st>>>(maps, M, N, K, nsplit, e, ms, g_err_dev);
+        gemm_tc_kernel<BN><<<grid, kThreads, S::kBytes, st>>>(maps, M, N, K, nsplit, g, e, ms, g_err_dev);
         return cudaGetLastError();
     }
     cudaError_t r = cudaMemsetAsync(ms.bar, 0, sizeof(unsigned int), st);
@@ -824,7 +1087,7 @@ cudaError_t launch(int M, int N, int K, const TcOperand &A, const TcOperand &B, 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<BN>, maps, M, N, K, nsplit, e, ms, g_err_dev);
+    return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<BN>, maps, M, N, K, nsplit, g, e, ms, g_err_dev);
 }
 
 template <int BN>
@@ -879,7 +1142,8 @@ cudaError_t dispatch_bn(int bn, F f) {
 
 cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epilogue &e, int k_first, int k_end,
                                float *const z[2], __nv_bfloat16 *const zhi[2], __nv_bfloat16 *const zlo[2],
-                               unsigned int *bar, cudaStream_t st, int num_sms, int clenshaw, int L) {
+                               unsigned int *bar, cudaStream_t st, int num_sms, int clenshaw, int L, int *closed) {
+    if (closed) *closed = 0;
     if (p <= 0 || k_end <= k_first) return cudaSuccess;
     if (!load_encode()) return cudaErrorNotSupported;
     if ((A.ld % 8) || ((uintptr_t)A.hi % 16) || !e.symmetric_upper || !e.H || !bar) return cudaErrorInvalidValue;
@@ -903,13 +1167,21 @@ cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epil
     ms.bar = bar;
     ms.clenshaw = clenshaw;
     ms.L = L;
+    // tensor-memory resident state when every CTA owns at most one tile and
+    // the state fits beside the two accumulators; the closing step of
+    // Clenshaw's sum is then applied in the last step
+    const int bn = choose_bn(p, p, 1, num_sms);
+    const int tiles = count_tiles((p + BM - 1) / BM, (p + bn - 1) / bn, 1, bn);
+    ms.resident = (bn <= 64 && tiles <= num_sms && k_end == L) ? 1 : 0;
     TcOperand B;
     B.ld = A.ld;
     B.rows = p;
     B.hi = zhi[0];   // per-step operands come from the ring
-    return dispatch_bn(choose_bn(p, p, 1, num_sms), [&](auto bn) {
-        return launch<decltype(bn)::value>(p, p, p, A, B, nsplit, e, ms, st, num_sms);
+    cudaError_t r2 = dispatch_bn(bn, [&](auto b) {
+        return launch<decltype(b)::value>(p, p, p, A, B, nsplit, e, ms, st, num_sms);
     });
+    if (r2 == cudaSuccess && closed) *closed = (ms.resident && clenshaw) ? 1 : 0;
+    return r2;
 }
 
 cudaError_t gemm_tc(int M, int N, int K, const TcOperand &A, const TcOperand &B, int nsplit, const Epilogue &e,

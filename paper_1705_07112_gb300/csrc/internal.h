@@ -111,9 +111,13 @@ cudaError_t gemm_tc(int M, int N, int K, const TcOperand &A, const TcOperand &B,
 // epilogue fields (s_acc, s_c, s_c2, H, ldh, coef, ldd, ldb, symmetric_upper).
 // Step k writes Psi_k over Psi_{k-2} in z[k&1] and its BF16 copies in
 // zhi/zlo[k&1]; it reads Psi_{k-1} from slot (k&1)^1.  bar: one device word.
+// When the launch keeps the state in tensor memory (one tile per CTA) the
+// FP32 ring is not written; with Clenshaw's sum the closing step is then
+// applied inside the launch and *closed is set to 1.
 cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epilogue &e, int k_first, int k_end,
                                float *const z[2], __nv_bfloat16 *const zhi[2], __nv_bfloat16 *const zlo[2],
-                               unsigned int *bar, cudaStream_t st, int num_sms, int clenshaw = 0, int L = 0);
+                               unsigned int *bar, cudaStream_t st, int num_sms, int clenshaw = 0, int L = 0,
+                               int *closed = nullptr);
 
 // Sparsity-based reduction helpers (sparsify.cu).
 cudaError_t make_transform(int type, int p, float *T, int64_t ld, cudaStream_t st, int num_sms);
