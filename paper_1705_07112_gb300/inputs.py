@@ -21,6 +21,9 @@ Laboratory video of Section V, are not available; these stand in for them):
                        patches with weighted soft thresholding.
 * ``video_background`` 4096 x 8192: rank-5 Gaussian background, 3 % sparse
                        foreground +-U[0.5, 1], N(0, 0.01^2) noise.
+* ``block_completion`` Section V-E's synthetic matrix J - blkdiag(0.5 1 1^T, n)
+                       (rank n, entries 0.5 and 1) with a random x % of its
+                       entries set to zero and marked unobserved.
 """
 from __future__ import annotations
 
@@ -166,3 +169,25 @@ def smooth_video(seed_index=0, side=16, frames=96, rank=3, frac=0.03, sigma=0.01
 
 def random_gaussian(rng, m, n, scale=1.0):
     return (scale * rng.standard_normal((m, n))).astype(np.float32)
+
+
+def block_completion(seed_index=0, size=1000, rank=100, frac_zero=0.10):
+    """Section V-E's synthetic completion input: D = J - blkdiag(D_s, rank)
+    with J the all-ones size x size matrix and D_s = 0.5 * ones(b, b),
+    b = size / rank (size a multiple of rank); a uniformly random set of
+    round(frac_zero * size^2) entries is set to zero.  Returns (D, I, mask):
+    the clean matrix, the corrupted one and the observation mask (uint8, 1 =
+    observed, 0 = zeroed), all row-major."""
+    if size % rank:
+        raise ValueError("size must be a multiple of rank")
+    b = size // rank
+    blk = (np.arange(size)[:, None] // b) == (np.arange(size)[None, :] // b)
+    D = np.where(blk, 0.5, 1.0)
+    rng = rng_for(6, seed_index)
+    nz = int(round(frac_zero * size * size))
+    idx = rng.choice(size * size, size=nz, replace=False)
+    mask = np.ones(size * size, dtype=np.uint8)
+    mask[idx] = 0
+    mask = mask.reshape(size, size)
+    I = np.where(mask == 1, D, 0.0)
+    return D.astype(np.float32), I.astype(np.float32), mask
