@@ -11,7 +11,8 @@ matrices whose total size exceeds the 129 MB L2, so no step starts from a
 warm cache.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16|bf16x3|fp32]
-                  [--workload rpca_frame|single_lowrank|video_background|patch_groups|rpca_admm]
+                  [--workload rpca_frame|single_lowrank|video_background|patch_groups|rpca_admm|
+                              block_completion]
                   [--impl reference]
 
 Prints ONE JSON line.  `--impl reference` times the FP64 CPU oracle (the
@@ -71,7 +72,18 @@ def make_workload(name, index=0):
         return inputs.single_lowrank(seed_index=index)
     if name == "video_background":
         return inputs.video_background(seed_index=index)
+    if name == "block_completion":
+        D, I, mask = inputs.block_completion(seed_index=index)
+        return inputs.Workload("block_completion_%dx%d_rank100_zero10pct_L20" % D.shape, I,
+                               inputs.ShrinkSpec(inputs.SOFT, COMPLETION_TAU_N), 20,
+                               meta={"D": D, "mask": mask, "tau_l1": COMPLETION_TAU_L1})
     raise SystemExit("unknown workload %s" % name)
+
+
+# Section V-E's completion test gives no (1/rho, eta/rho): 1/rho below the
+# block matrix's smallest nonzero singular value (500/rank >= 1 for every
+# rank the section uses) and the inpainting experiment's eta/rho
+COMPLETION_TAU_N, COMPLETION_TAU_L1 = 0.5, 0.1
 
 
 class ClockSampler:
@@ -233,7 +245,7 @@ def run_reference(args, world, rank):
     value = args.steps * rows / float(m if m >= n else n) / tot
     sample = "%d of %d output %s per step via the oracle's vector form (plus its FP64 power-iteration bound)" % (
         rows, m if m >= n else n, "rows" if m >= n else "columns")
-    unit = "ADMM iterations/s" if args.workload == "rpca_admm" else "matrices/s"
+    unit = "ADMM iterations/s" if args.workload in ("rpca_admm", "block_completion") else "matrices/s"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -243,6 +255,9 @@ def run_reference(args, world, rank):
     if args.workload == "rpca_admm":
         line["config"]["workload"] = "rpca_admm_%dx%d_L%d" % (m, n, w.L)
         line["cpu_baseline"]["sample"] += "; the shrinkage step of one ADMM iteration (its dominant cost)"
+    if args.workload == "block_completion":
+        line["cpu_baseline"]["sample"] += ("; the shrinkage step of one completion ADMM iteration (the 2-D DCT "
+                                           "products and elementwise updates not counted)")
     print(json.dumps(line))
     return 0
 
@@ -511,11 +526,125 @@ def run_gpu_admm(args, world, rank, local):
     return 0
 
 
+def run_gpu_completion(args, world, rank, local):
+    """Section V-E's completion test, 1000 x 1000 rank 100 with 10 % of the
+    entries zeroed: one step = one ADMM iteration (two 2-D DCT passes of two
+    FP32 products each, one shrinkage, two elementwise kernels), timed over
+    one `Completion.run` call of --steps iterations."""
+    import torch
+
+    import paper_1705_07112_gb300 as cpa
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks = load_peaks()
+    w = make_workload("block_completion", rank)
+    m, n = w.X.shape
+    I = torch.from_numpy(w.X).to(dev)
+    M = torch.from_numpy(w.meta["mask"]).to(dev)
+    h = cpa.Handle(local)
+    co = cpa.Completion(h, m, n)
+    Lo = torch.empty((m, n), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def solve(iters, Iin=I, Min=M):
+        return co.run(Iin, Min, COMPLETION_TAU_N, COMPLETION_TAU_L1, w.L, iters, prec=args.prec, Lout=Lo,
+                      stream=stream)
+
+    solve(args.warmup)
+    torch.cuda.synchronize()
+    cpa.cpa_profile_read(h, reset=True)
+    cpa.cpa_profile_enable(h, True)
+    solve(args.steps)
+    prof = cpa.cpa_profile_read(h, reset=True)
+    cpa.cpa_profile_enable(h, False)
+    # + 4 transform products + 2 elementwise kernels per iteration
+    launches_per_step = sum(v["launches"] for v in prof.values()) / args.steps + 6
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, _, E = solve(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    barrier(world)
+    clk = clocks.stop()
+    ms_max = max_over_ranks(world, ms, dev)
+    value = world * args.steps / (ms_max / 1e3)
+    D = w.meta["D"].astype(np.float64)
+    miss = w.meta["mask"] == 0
+    l = Lo.cpu().numpy().astype(np.float64)
+    err_miss = float(np.linalg.norm((l - D)[miss]) / np.linalg.norm(D[miss]))
+
+    # end to end: I and the mask from pinned host memory, l back
+    hI = torch.from_numpy(w.X).pin_memory()
+    hM = torch.from_numpy(w.meta["mask"]).pin_memory()
+    hL = torch.empty((m, n), dtype=torch.float32).pin_memory()
+    Id, Md = torch.empty_like(I), torch.empty_like(M)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    Id.copy_(hI, non_blocking=True)
+    Md.copy_(hM, non_blocking=True)
+    solve(args.steps, Id, Md)
+    hL.copy_(Lo, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0, dev)
+    e2e = {"value": world * args.steps / e2e_s, "unit": "ADMM iterations/s",
+           "h2d_bytes_per_step": m * n * 5 / args.steps, "d2h_bytes_per_step": m * n * 4 / args.steps,
+           "note": "one solve of --steps iterations per timed region: I and the mask in once, l out once"}
+
+    p = min(m, n)
+    rec = prof["recur"]
+    rec_ms = rec["ms"] / max(1, rec["launches"])
+    products = (w.L - 2) * args.steps / max(1, rec["launches"])
+    flops = products * float(p) ** 2 * (p + 1)
+    achieved = flops / (rec_ms / 1e3) / 1e12 if rec_ms > 0 else None
+    peak = peaks["bf16_tflops"] if args.prec != "fp32" else None
+    svt_ms = sum(v["ms"] for v in prof.values()) / args.steps
+    roof = {"kernel": "recurrence, all steps in one cooperative tcgen05 launch", "bound": "tensor",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if (achieved and peak) else None,
+            "traffic": None, "flops_per_launch": flops, "ms_per_launch": rec_ms,
+            "peak_source": "%s bf16 burst" % peaks["source"],
+            "stage_ms_per_step": dict({k: v["ms"] / args.steps for k, v in prof.items()},
+                                      transforms_and_updates=ms_max / args.steps - svt_ms)}
+    cfg = {"workload": w.name, "m": m, "n": n, "L": w.L, "prec": args.prec, "tau_nuclear": COMPLETION_TAU_N,
+           "tau_l1": COMPLETION_TAU_L1, "iterations_per_solve": args.steps, "final_E": float(E[-1]),
+           "missing_entry_error": err_miss,
+           "inputs": "ADMM state (10 x 4 MB) stays L2-resident across iterations by design",
+           "parallelism": "replicas x%d" % world}
+    line = {"metric": METRIC, "value": value, "unit": "ADMM iterations/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.prec], "data": "synthetic",
+            "config": cfg, "roofline": roof, "e2e": e2e,
+            "gpu_launches": int(round(launches_per_step * args.steps)), "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, dt, cores = oracle_rows_rate(w, args.cpu_rows, w.L)
+        line["cpu_baseline"] = {"value": rate, "unit": "ADMM iterations/s", "cores": cores, "kind": "oracle",
+                                "sample": "the shrinkage step of one iteration, %d of %d output rows through the "
+                                          "FP64 oracle's vector form, %.1f s (the DCT products and updates not "
+                                          "counted)" % (args.cpu_rows, m, dt)}
+    if rank == 0:
+        print(json.dumps(line))
+    co.close()
+    h.close()
+    return 0
+
+
 def run_gpu(args, world, rank, local):
     if args.workload == "patch_groups":
         return run_gpu_batched(args, world, rank, local)
     if args.workload == "rpca_admm":
         return run_gpu_admm(args, world, rank, local)
+    if args.workload == "block_completion":
+        return run_gpu_completion(args, world, rank, local)
     import torch
 
     import paper_1705_07112_gb300 as cpa

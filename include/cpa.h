@@ -406,6 +406,45 @@ CPA_API cpa_status cpa_admm_rpca(cpa_admm a, const float *dD, int64_t ldd, doubl
                                  int prec, const cpa_sparsify *sp, int schedule, int max_iters, double tol,
                                  float *dL, float *dS, int *iters_done, double *errors, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Matrix completion ADMM of Section V-E: the inpainting problem of Section
+ * V-B (Eq. texture_repaire4) without its average term, min |L|_* +
+ * eta |Psi l|_1 subject to the observed entries and 0 <= L <= 1, in the
+ * ADMM form of Appendix A (Eq. admm_algorithm_inp without the z^(5) block):
+ * z = K l, K = [Id; Psi; Omega; Id], Psi the orthonormal 2-D DCT (Psi l =
+ * C_m L C_n^T, C_p[k][j] = s_k cos(pi (2j+1) k / (2p)), s_0 = sqrt(1/p),
+ * s_k = sqrt(2/p)), Omega the observation mask.  Each iteration: the
+ * least-squares step l = (a1 + Psi^T a2 + omega a3 + a4) / (3 + omega)
+ * (a = z - u), z1 = cpa_svt(l + u1) (soft threshold tau_nuclear = 1/rho, L
+ * terms, Lambda_max computed on the device, precision `prec`), z2 = the
+ * entrywise soft threshold tau_l1 = eta/rho of Psi l + u2, z3 = the observed
+ * values, z4 = l + u4 clipped to [0, 1], u += K l - z.  The four products
+ * with C_m, C_n run in FP32 (prec = CPA_FP32) or on the tensor cores with
+ * BF16 hi/lo operands, three products each (other precisions).  Start
+ * (Section V-B): l = u = 1, z = K l.
+ *
+ * cpa_completion_create: solver for m x n problems (m, n <= 65536, m n <=
+ *   2^31) on the handle's device; owns 10 m n + m^2 + n^2 floats and about
+ *   4 (m^2 + n^2 + 2 m n) BF16 values.
+ * cpa_completion_run: dI device m x n (row stride ldi >= n), the observed
+ *   values where dmask (uint8, row stride ldmask >= n) is nonzero, ignored
+ *   elsewhere.  dL (row stride ldl >= n) receives the last least-squares
+ *   iterate l; dZ1 (optional, contiguous m x n) the last shrinkage output.
+ *   Outputs must not overlap the inputs or each other.  Runs max_iters
+ *   iterations, or stops after the iteration whose E = |l_new - l|_F /
+ *   |l_new|_F (the stopping quantity of Section IV's footnote, computed
+ *   after each least-squares step) is below tol > 0 (one host
+ *   synchronisation per iteration).  *iters_done and errors (host, max_iters
+ *   doubles) as for cpa_admm_rpca.  Errors: CPA_ERR_INVALID_ARG on bad
+ *   arguments; errors of cpa_svt pass through. */
+typedef struct cpa_completion_ctx *cpa_completion;
+CPA_API cpa_status cpa_completion_create(cpa_handle h, int64_t m, int64_t n, cpa_completion *out);
+CPA_API cpa_status cpa_completion_destroy(cpa_completion c);
+CPA_API cpa_status cpa_completion_run(cpa_completion c, const float *dI, int64_t ldi, const uint8_t *dmask,
+                                      int64_t ldmask, double tau_nuclear, double tau_l1, int L, int prec,
+                                      int max_iters, double tol, float *dL, int64_t ldl, float *dZ1,
+                                      int *iters_done, double *errors, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,7 +5,7 @@ include/cpa.h); this package is its thin ctypes binding plus seeded
 synthetic workloads.  Importing the package does not load the library;
 the first call does, and raises if it is missing.
 """
-from ._lib import (BF16, BF16X3, FP32, HARD, SOFT, TF32, WSOFT, Admm, BatchPlan, CpaError, Handle,  # noqa: F401
+from ._lib import (BF16, BF16X3, FP32, HARD, SOFT, TF32, WSOFT, Admm, BatchPlan, Completion, CpaError, Handle,  # noqa: F401
                    ShrinkArray,
                    cpa_coeffs, cpa_svt_batched,
                    cpa_get_coeffs, cpa_get_lambda, cpa_lambda_bound, cpa_profile_enable, cpa_profile_read,

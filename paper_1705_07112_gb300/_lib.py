@@ -27,7 +27,8 @@ EXPORTS = ["cpa_create", "cpa_destroy", "cpa_status_string", "cpa_last_error", "
            "cpa_lambda_bound_noalloc", "cpa_mlp_create", "cpa_mlp_destroy", "cpa_mlp_param_count",
            "cpa_mlp_set_params", "cpa_mlp_get_params", "cpa_mlp_forward", "cpa_mlp_gradients",
            "cpa_mlp_train_step", "cpa_batch_features", "cpa_svt_batched_learned", "cpa_batch_read_choices",
-           "cpa_admm_create", "cpa_admm_destroy", "cpa_admm_rpca", "cpa_set_option"]
+           "cpa_admm_create", "cpa_admm_destroy", "cpa_admm_rpca", "cpa_set_option",
+           "cpa_completion_create", "cpa_completion_destroy", "cpa_completion_run"]
 OPT_SERIES, SERIES_FORWARD, SERIES_CLENSHAW = 1, 0, 1
 STAGES = ["prep", "gram", "bound", "coeff", "shift", "recur", "apply", "sparse"]
 T_IDENTITY, T_HAAR1_LOWPASS, T_BLOCK_DCT8, T_DCT = 0, 1, 2, 3
@@ -112,6 +113,11 @@ def load(path: str = LIB_PATH):
             "cpa_admm_rpca": (ctypes.c_int, [_vp, _vp, _i64, _d, _d, ctypes.c_int, ctypes.c_int,
                                              _P(CpaSparsify), ctypes.c_int, ctypes.c_int, _d, _vp, _vp,
                                              _P(ctypes.c_int), _P(_d), _vp]),
+            "cpa_completion_create": (ctypes.c_int, [_vp, _i64, _i64, _P(_vp)]),
+            "cpa_completion_destroy": (ctypes.c_int, [_vp]),
+            "cpa_completion_run": (ctypes.c_int, [_vp, _vp, _i64, _vp, _i64, _d, _d, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_int, _d, _vp, _i64, _vp, _P(ctypes.c_int), _P(_d),
+                                                  _vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -513,6 +519,51 @@ class Admm:
                                        ctypes.c_void_p(Lout.data_ptr()), ctypes.c_void_p(Sout.data_ptr()),
                                        ctypes.byref(done), errs, _stream_ptr(stream)), "cpa_admm_rpca")
         return Lout, Sout, np.array(errs[:done.value])
+
+
+class Completion:
+    """cpa_completion: Section V-E's matrix completion ADMM (the inpainting
+    problem without its average term) around the shrinkage for m x n
+    problems."""
+
+    def __init__(self, h: Handle, m: int, n: int):
+        self._lib = load()
+        ptr = ctypes.c_void_p()
+        _check(self._lib.cpa_completion_create(h.ptr, int(m), int(n), ctypes.byref(ptr)), "cpa_completion_create")
+        self.ptr, self.m, self.n = ptr, int(m), int(n)
+
+    def close(self):
+        if self.ptr:
+            self._lib.cpa_completion_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, I, mask, tau_nuclear, tau_l1, L, iters, prec="fp32", tol=0.0, Lout=None, Z1out=None,
+            stream=None):
+        """Returns (l, z1 or None, errors); I a float32 CUDA tensor m x n,
+        mask a uint8 CUDA tensor m x n (nonzero = observed), both with unit
+        column stride."""
+        import torch
+        for t, dt, nm in ((I, torch.float32, "I"), (mask, torch.uint8, "mask")):
+            if not (t.is_cuda and t.dtype == dt and t.dim() == 2 and t.stride(1) == 1 and
+                    tuple(t.shape) == (self.m, self.n)):
+                raise ValueError("%s must be a CUDA m x n tensor of %s with unit column stride" % (nm, dt))
+        Lout = torch.empty((self.m, self.n), dtype=torch.float32, device=I.device) if Lout is None else Lout
+        done = ctypes.c_int()
+        errs = (_d * int(iters))()
+        p = PREC[prec] if isinstance(prec, str) else int(prec)
+        _check(self._lib.cpa_completion_run(self.ptr, ctypes.c_void_p(I.data_ptr()), I.stride(0),
+                                            ctypes.c_void_p(mask.data_ptr()), mask.stride(0), float(tau_nuclear),
+                                            float(tau_l1), int(L), p, int(iters), float(tol),
+                                            ctypes.c_void_p(Lout.data_ptr()), Lout.stride(0),
+                                            ctypes.c_void_p(Z1out.data_ptr()) if Z1out is not None else None,
+                                            ctypes.byref(done), errs, _stream_ptr(stream)), "cpa_completion_run")
+        return Lout, Z1out, np.array(errs[:done.value])
 
 
 def cpa_set_option(h: Handle, option: int, value: int):

@@ -78,4 +78,4 @@ def test_cpa_run_tracks_the_exact_run():
     D, I, mask = inputs.block_completion(1, 40, 4, 0.10)
     le, _, _ = C.completion_admm(I, mask, 0.1, 30, A.svt_exact(0.5))
     lc, _, _ = C.completion_admm(I, mask, 0.1, 30, A.svt_cpa(0.5, 120))
-    assert np.linalg.norm(lc - le) / np.linalg.norm(le) < 2e-2
+    assert np.linalg.norm(lc - le) / np.linalg.norm(le) < 2e-3

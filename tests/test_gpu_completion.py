@@ -1,0 +1,100 @@
+"""The device completion ADMM (cpa_completion_run, Section V-E) against the
+FP64 oracle ADMM (oracle/completion.py) with Algorithm 1 in FP64 as the
+shrinkage step, on Section V-E's block matrix J - blkdiag(0.5 1 1^T, n)
+with 10 % of its entries zeroed; (1/rho, eta/rho) = (0.5, 0.1), L = 20."""
+import numpy as np
+import pytest
+
+from oracle import admm as A
+from oracle import completion as C
+from paper_1705_07112_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TAU_N, TAU_L1, L = 0.5, 0.1, 20
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1705_07112_gb300 import _lib
+    return _lib
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, dtype=np.float64) - b) / np.linalg.norm(b))
+
+
+def case(shape):
+    size, rank, rows = shape
+    D, I, mask = inputs.block_completion(0, size, rank, 0.10)
+    return D[:rows], I[:rows], mask[:rows]
+
+
+# FP32: the transforms and the shrinkage each carry ~1e-6 relative error per
+# iteration; twelve coupled iterations: 2e-4.  BF16X3 (~4e-6 per shrinkage
+# of its input, which z1 keeps almost whole here): 2e-3.
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-4), ("bf16x3", 2e-3)])
+@pytest.mark.parametrize("shape", [(60, 6, 60), (90, 9, 71)])
+def test_completion_matches_the_oracle_cpa_run(lib, prec, tol, shape):
+    import torch
+    D, I, mask = case(shape)
+    iters = 12
+    lo, z1o, Eo = C.completion_admm(I.astype(np.float64), mask, TAU_L1, iters, A.svt_cpa(TAU_N, L))
+    h = lib.Handle(0)
+    c = lib.Completion(h, *I.shape)
+    Id, Md = torch.from_numpy(I).cuda(), torch.from_numpy(mask).cuda()
+    Z1 = torch.empty_like(Id)
+    lg, _, E = c.run(Id, Md, TAU_N, TAU_L1, L, iters, prec=prec, Z1out=Z1)
+    torch.cuda.synchronize()
+    assert rel(lg.cpu().numpy(), lo) <= tol, rel(lg.cpu().numpy(), lo)
+    assert rel(Z1.cpu().numpy(), z1o) <= tol, rel(Z1.cpu().numpy(), z1o)
+    assert len(E) == iters
+    assert np.allclose(E, Eo, rtol=50 * tol, atol=1e-7)
+    c.close()
+    h.close()
+
+
+def test_completion_stop_rule_and_arguments(lib):
+    import torch
+    D, I, mask = case((60, 6, 60))
+    h = lib.Handle(0)
+    c = lib.Completion(h, 60, 60)
+    Id, Md = torch.from_numpy(I).cuda(), torch.from_numpy(mask).cuda()
+    _, _, E = c.run(Id, Md, TAU_N, TAU_L1, L, 200, prec="fp32", tol=1e-3)
+    assert len(E) < 200 and E[-1] < 1e-3 and np.all(E[:-1] >= 1e-3)
+    with pytest.raises(ValueError):
+        c.run(Id[:, :59], Md, TAU_N, TAU_L1, L, 3)
+    with pytest.raises(lib.CpaError):
+        c.run(Id, Md, -1.0, TAU_L1, L, 3)
+    with pytest.raises(lib.CpaError):
+        c.run(Id, Md, TAU_N, TAU_L1, L, 3, Lout=Id)   # output overlapping the input
+    c.close()
+    h.close()
+
+
+def test_completion_full_size_restores_the_block_matrix(lib):
+    """Section V-E's size: 1000 x 1000, rank 100, 10 % zeroed, BF16X3.  The
+    oracle cannot run this size in seconds, so the checks are the
+    properties any converged run has: E_t falls below 1e-4 (the paper's
+    stop rule), the observed entries are kept, the range constraint holds,
+    and the zeroed entries are restored."""
+    import torch
+    D, I, mask = inputs.block_completion(0, 1000, 100, 0.10)
+    h = lib.Handle(0)
+    c = lib.Completion(h, 1000, 1000)
+    Id, Md = torch.from_numpy(I).cuda(), torch.from_numpy(mask).cuda()
+    lg, _, E = c.run(Id, Md, TAU_N, TAU_L1, L, 300, prec="bf16x3", tol=1e-4)
+    l = lg.cpu().numpy().astype(np.float64)
+    D = D.astype(np.float64)
+    miss = mask == 0
+    err_miss = np.linalg.norm((l - D)[miss]) / np.linalg.norm(D[miss])
+    print("\niterations %d, E %.2e, missing-entry error %.3e, observed max dev %.2e"
+          % (len(E), E[-1], err_miss, np.abs((l - D)[~miss]).max()))
+    assert E[-1] < 1e-4 and len(E) < 300
+    assert err_miss < 1e-2
+    assert np.abs((l - D)[~miss]).max() < 2e-2
+    assert l.min() > -2e-2 and l.max() < 1 + 2e-2
+    c.close()
+    h.close()
