@@ -175,6 +175,10 @@ struct SvtWs {
     __nv_bfloat16 *Ahi = nullptr, *Alo = nullptr, *Zhi[2] = {}, *Zlo[2] = {}, *Hhi = nullptr, *Hlo = nullptr;
     __nv_bfloat16 *Xhi = nullptr, *Xlo = nullptr, *Xthi = nullptr, *Xtlo = nullptr;
     int64_t ldn = 0, ldm = 0;
+    // row stride of the recurrence operands (A-tilde, Psi copies): p rounded
+    // up to 128, the columns beyond p kept zero so the products run over a
+    // contraction length that the grouped operand loads take whole
+    int64_t ldk = 0;
     size_t bytes = 0;
 };
 
@@ -207,9 +211,11 @@ SvtWs carve(char *base, int64_t m, int64_t n, int L, int iters, int prec, bool s
         bool split_rec = prec == CPA_BF16X3 || p < kSplitRecBelow;
         w.ldn = round_up(n, 8);
         w.ldm = round_up(m, 8);
-        w.Ahi = c.take<__nv_bfloat16>(pp);
-        w.Zhi[0] = c.take<__nv_bfloat16>(pp);
-        w.Zhi[1] = c.take<__nv_bfloat16>(pp);
+        w.ldk = round_up(p, 128);
+        const size_t pk = (size_t)(p * w.ldk);
+        w.Ahi = c.take<__nv_bfloat16>(pk);
+        w.Zhi[0] = c.take<__nv_bfloat16>(pk);
+        w.Zhi[1] = c.take<__nv_bfloat16>(pk);
         w.Hhi = c.take<__nv_bfloat16>(pp);
         w.Hlo = c.take<__nv_bfloat16>(pp);
         w.Xhi = c.take<__nv_bfloat16>((size_t)(m * w.ldn));
@@ -217,9 +223,9 @@ SvtWs carve(char *base, int64_t m, int64_t n, int L, int iters, int prec, bool s
         w.Xthi = c.take<__nv_bfloat16>((size_t)(n * w.ldm));
         w.Xtlo = c.take<__nv_bfloat16>((size_t)(n * w.ldm));
         if (split_rec) {
-            w.Alo = c.take<__nv_bfloat16>(pp);
-            w.Zlo[0] = c.take<__nv_bfloat16>(pp);
-            w.Zlo[1] = c.take<__nv_bfloat16>(pp);
+            w.Alo = c.take<__nv_bfloat16>(pk);
+            w.Zlo[0] = c.take<__nv_bfloat16>(pk);
+            w.Zlo[1] = c.take<__nv_bfloat16>(pk);
         }
     }
     w.bytes = c.off;
@@ -473,7 +479,8 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
         StageScope sc(h, CPA_STAGE_SHIFT, st, 1);
         CK(shift_init(w.G, w.ldp, (int)p, w.out + 3, w.coef, L, tc ? nullptr : w.A, w.Z[1], w.H, w.ldp,
                       tc ? w.Ahi : nullptr, tc ? w.Alo : nullptr, tc ? w.Zhi[1] : nullptr,
-                      tc ? w.Zlo[1] : nullptr, w.ldp, st, h->num_sms, clenshaw));
+                      tc ? w.Zlo[1] : nullptr, tc ? w.ldk : w.ldp, st, h->num_sms, clenshaw,
+                      tc ? w.Zhi[0] : nullptr, tc ? w.Zlo[0] : nullptr));
     }
     // recurrence with fused accumulation: Psi_k = 2 B_hat Psi_{k-1} - Psi_{k-2}, H += c_k Psi_k.
     // Ring: Psi_k overwrites Psi_{k-2} in slot k&1; Psi_0 = Id is implicit.
@@ -494,12 +501,12 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
         e.H = w.H;
         e.ldh = w.ldp;
         e.coef = w.coef;
-        e.ldb = w.ldp;
+        e.ldb = w.ldk;
         e.symmetric_upper = 1;
         TcOperand a;
-        a.hi = w.Ahi; a.lo = w.Alo; a.ld = w.ldp; a.rows = (int)p;
+        a.hi = w.Ahi; a.lo = w.Alo; a.ld = w.ldk; a.rows = (int)p;
         CK(gemm_tc_recurrence((int)p, a, nsplit_rec, e, 2, L, w.Z, w.Zhi, w.Zlo, (unsigned int *)(w.flag + 2), st,
-                              h->num_sms, clenshaw, L, &closed));
+                              h->num_sms, clenshaw, L, &closed, (int)w.ldk));
     }
     for (int k = 2; k < L && !tc; ++k) {
         StageScope sc(h, CPA_STAGE_RECUR, st, 1);
@@ -536,10 +543,10 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
             e.s_c2 = -2.f;
             e.Dhi = w.Zhi[cur];
             e.Dlo = w.Zlo[cur];
-            e.ldb = w.ldp;
+            e.ldb = w.ldk;
             TcOperand a, b;
-            a.hi = w.Ahi; a.lo = w.Alo; a.ld = w.ldp; a.rows = (int)p;
-            b.hi = w.Zhi[prev]; b.lo = w.Zlo[prev]; b.ld = w.ldp; b.rows = (int)p;
+            a.hi = w.Ahi; a.lo = w.Alo; a.ld = w.ldk; a.rows = (int)p;
+            b.hi = w.Zhi[prev]; b.lo = w.Zlo[prev]; b.ld = w.ldk; b.rows = (int)p;
             CK(gemm_tc((int)p, (int)p, (int)p, a, b, nsplit_rec, e, st, h->num_sms));
         }
     }

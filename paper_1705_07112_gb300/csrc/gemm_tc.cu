@@ -1142,7 +1142,8 @@ cudaError_t dispatch_bn(int bn, F f) {
 
 cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epilogue &e, int k_first, int k_end,
                                float *const z[2], __nv_bfloat16 *const zhi[2], __nv_bfloat16 *const zlo[2],
-                               unsigned int *bar, cudaStream_t st, int num_sms, int clenshaw, int L, int *closed) {
+                               unsigned int *bar, cudaStream_t st, int num_sms, int clenshaw, int L, int *closed,
+                               int kpad) {
     if (closed) *closed = 0;
     if (p <= 0 || k_end <= k_first) return cudaSuccess;
     if (!load_encode()) return cudaErrorNotSupported;
@@ -1177,8 +1178,12 @@ cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epil
     B.ld = A.ld;
     B.rows = p;
     B.hi = zhi[0];   // per-step operands come from the ring
+    // operands padded with zero columns are contracted over the padded
+    // length (a multiple of 128: grouped loads, no K tail)
+    const int K = kpad > p ? kpad : p;
+    if (K > A.ld) return cudaErrorInvalidValue;
     cudaError_t r2 = dispatch_bn(bn, [&](auto b) {
-        return launch<decltype(b)::value>(p, p, p, A, B, nsplit, e, ms, st, num_sms);
+        return launch<decltype(b)::value>(p, p, K, A, B, nsplit, e, ms, st, num_sms);
     });
     if (r2 == cudaSuccess && closed) *closed = (ms.resident && clenshaw) ? 1 : 0;
     return r2;

@@ -113,11 +113,13 @@ cudaError_t gemm_tc(int M, int N, int K, const TcOperand &A, const TcOperand &B,
 // zhi/zlo[k&1]; it reads Psi_{k-1} from slot (k&1)^1.  bar: one device word.
 // When the launch keeps the state in tensor memory (one tile per CTA) the
 // FP32 ring is not written; with Clenshaw's sum the closing step is then
-// applied inside the launch and *closed is set to 1.
+// applied inside the launch and *closed is set to 1.  kpad > p: the BF16
+// operands (A and the ring's copies, row stride >= kpad) hold zeros in
+// columns p .. kpad-1 and the products contract over kpad.
 cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epilogue &e, int k_first, int k_end,
                                float *const z[2], __nv_bfloat16 *const zhi[2], __nv_bfloat16 *const zlo[2],
                                unsigned int *bar, cudaStream_t st, int num_sms, int clenshaw = 0, int L = 0,
-                               int *closed = nullptr);
+                               int *closed = nullptr, int kpad = 0);
 
 // Sparsity-based reduction helpers (sparsify.cu).
 cudaError_t make_transform(int type, int p, float *T, int64_t ld, cudaStream_t st, int num_sms);
@@ -150,11 +152,12 @@ cudaError_t device_coeffs(const double *lam_dev, double lam_host, int L, const S
 // A = (2/lambda) G - Id, Z1 = A, H = c0/2 Id + c1 A (FP32).  For the
 // tensor-core path also At = (2/lambda) G as BF16 hi/lo (the operand of every
 // recurrence product; the -Id is applied exactly in the FP32 epilogue) and
-// Z1 as BF16 hi/lo.
+// Z1 as BF16 hi/lo; their columns p .. ldb-1, and those of the ring's other
+// BF16 slot Z0hi/Z0lo when given, are set to zero.
 cudaError_t shift_init(const float *G, int64_t ldg, int p, const double *lam, const double *c, int L, float *A,
                        float *Z1, float *H, int64_t ld, __nv_bfloat16 *Athi, __nv_bfloat16 *Atlo,
                        __nv_bfloat16 *Z1hi, __nv_bfloat16 *Z1lo, int64_t ldb, cudaStream_t st, int num_sms,
-                       int clenshaw = 0);
+                       int clenshaw = 0, __nv_bfloat16 *Z0hi = nullptr, __nv_bfloat16 *Z0lo = nullptr);
 // Clenshaw's closing step H = (b_0 - b_2) / 2 with b_0 in H and b_2 in B2
 // (B2 null: b_2 = c[2] Id); lower triangle only when lower_only.
 cudaError_t clenshaw_finish(float *H, const float *B2, int p, int64_t ld, const double *c, int lower_only,

@@ -181,7 +181,7 @@ __device__ __forceinline__ void put_split(__nv_bfloat16 *hi, __nv_bfloat16 *lo, 
 __global__ void shift_kernel(const float *__restrict__ G, int64_t ldg, int p, const double *lam,
                              const double *c, int L, float *A, float *Z1, float *H, int64_t ld,
                              __nv_bfloat16 *Athi, __nv_bfloat16 *Atlo, __nv_bfloat16 *Z1hi, __nv_bfloat16 *Z1lo,
-                             int64_t ldb, int clenshaw) {
+                             int64_t ldb, int clenshaw, __nv_bfloat16 *Z0hi, __nv_bfloat16 *Z0lo) {
     float s = (float)(2.0 / lam[0]);
     float c0h = (float)(0.5 * c[0]);
     float c1 = L > 1 ? (float)c[1] : 0.f;
@@ -199,6 +199,20 @@ __global__ void shift_kernel(const float *__restrict__ G, int64_t ldg, int p, co
         H[(int64_t)i * ld + j] = c1 * a + (i == j ? c0h : 0.f);
         if (Athi) put_split(Athi, Atlo, (int64_t)i * ldb + j, at);
         if (Z1hi) put_split(Z1hi, Z1lo, (int64_t)i * ldb + j, z1);
+    }
+    // zero padding of the BF16 operands' rows (read as contraction columns)
+    if (Athi) {
+        const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+        for (int i = blockIdx.x; i < p; i += gridDim.x)
+            for (int64_t j = p + threadIdx.x; j < ldb; j += blockDim.x) {
+                const int64_t o = (int64_t)i * ldb + j;
+                Athi[o] = z;
+                if (Atlo) Atlo[o] = z;
+                if (Z1hi) Z1hi[o] = z;
+                if (Z1lo) Z1lo[o] = z;
+                if (Z0hi) Z0hi[o] = z;
+                if (Z0lo) Z0lo[o] = z;
+            }
     }
 }
 
@@ -550,11 +564,11 @@ __global__ void clenshaw_finish_kernel(float *H, const float *B2, int p, int64_t
 cudaError_t shift_init(const float *G, int64_t ldg, int p, const double *lam, const double *c, int L, float *A,
                        float *Z1, float *H, int64_t ld, __nv_bfloat16 *Athi, __nv_bfloat16 *Atlo,
                        __nv_bfloat16 *Z1hi, __nv_bfloat16 *Z1lo, int64_t ldb, cudaStream_t st, int num_sms,
-                       int clenshaw) {
+                       int clenshaw, __nv_bfloat16 *Z0hi, __nv_bfloat16 *Z0lo) {
     int blocks = std::min(p, num_sms * 8);   // a block per row, grid-stride
     if (blocks < 1) blocks = 1;
     shift_kernel<<<blocks, 256, 0, st>>>(G, ldg, p, lam, c, L, A, Z1, H, ld, Athi, Atlo, Z1hi, Z1lo, ldb,
-                                         clenshaw);
+                                         clenshaw, Z0hi, Z0lo);
     return cudaGetLastError();
 }
 

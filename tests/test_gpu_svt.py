@@ -230,3 +230,38 @@ def test_clenshaw_series_matches_oracle(cpa, handle, prec):
         _lib.cpa_set_option(handle, _lib.OPT_SERIES, 7)
     with pytest.raises(_lib.CpaError):
         _lib.cpa_set_option(handle, 99, 0)
+
+
+# The recurrence launch takes different forms by size: one tile per CTA with
+# the state in tensor memory at BN = 32 (p up to 1024) or BN = 64 (p about
+# 1088 to 1280), several tiles per CTA with the state in global memory at
+# BN = 128 / 256; operand loads grouped two slices per TMA instruction when
+# p is a multiple of 128, one slice otherwise.  Each form against the
+# oracle's vector form on sampled rows, forward and Clenshaw's sum.
+# Clenshaw's sum in plain BF16 misses the 2e-3 bar at these sizes: measured
+# on sampled rows at L = 30, 4.3e-3 to 6.0e-3 for p = 1000 .. 2048 against
+# 0.7e-4 to 1.2e-4 for the forward recurrence (BF16X3: 1.5e-5 against
+# 0.8e-5).  Its intermediates b_k sum second-kind polynomials whose size
+# grows with the number of remaining terms, and H = (b_0 - b_2)/2 cancels
+# them, so the BF16 rounding of the operand b_{k+1} is amplified; the
+# forward recurrence's T_k stay in [-1, 1].  The bar asserted for it is the
+# measured behaviour with margin, 1e-2; the forward recurrence stays the
+# default and the only series quoted at BF16.
+CLENSHAW_BF16_TOL = 1e-2
+@pytest.mark.parametrize("shape", [(1152, 1300), (1400, 1088), (2048, 2100)])
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("series", ["forward", "clenshaw"])
+def test_recurrence_launch_forms_sampled(cpa, handle, shape, prec, series):
+    from paper_1705_07112_gb300 import _lib
+    rng = np.random.default_rng(shape[0] + shape[1])
+    m, n = shape
+    X = (rng.standard_normal((m, 6)) @ rng.standard_normal((6, n)) + 0.1 * rng.standard_normal((m, n))).astype(np.float32)
+    s = O.Shrink(O.SOFT, 0.5 * 0.1 * (np.sqrt(m) + np.sqrt(n)))
+    p = min(m, n)
+    _lib.cpa_set_option(handle, _lib.OPT_SERIES,
+                        _lib.SERIES_CLENSHAW if series == "clenshaw" else _lib.SERIES_FORWARD)
+    try:
+        tol = CLENSHAW_BF16_TOL if (series == "clenshaw" and prec == "bf16") else TOL[prec]
+        sampled_rows_check(cpa, handle, X, s, 30, prec, [0, 1, p // 2, p - 2, p - 1], tol)
+    finally:
+        _lib.cpa_set_option(handle, _lib.OPT_SERIES, _lib.SERIES_FORWARD)
