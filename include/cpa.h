@@ -129,6 +129,21 @@ CPA_API const char *cpa_status_string(cpa_status s);
 /* Text of the last CUDA failure seen by the calling thread ("" if none). */
 CPA_API const char *cpa_last_error(void);
 
+/* cpa_svt over a sequence of `count` host matrices of one shape: hX[i] (m x
+ * n, row stride ldx) -> hY[i] (row stride ldy), other arguments as for
+ * cpa_svt.  The handle stages two matrices on the device (4 m n floats,
+ * allocated on first use) and overlaps the host-to-device copy of matrix
+ * i + 1 and the device-to-host copy of matrix i - 1 with the shrinkage of
+ * matrix i, on two copy streams of its own.  Asynchronous: `stream` waits for
+ * the last copy, so a synchronisation of `stream` makes every hY valid.  The
+ * copies overlap only for page-locked host memory (cudaMallocHost or
+ * cudaHostRegister); pageable buffers work but serialise.  Host buffers must
+ * not be touched until `stream` is synchronised.  Errors as cpa_svt, plus
+ * INVALID_ARG for null or short buffers. */
+CPA_API cpa_status cpa_svt_host(cpa_handle h, int count, const float *const *hX, int64_t m, int64_t n, int64_t ldx,
+                                const cpa_shrink *s, int L, double lambda_max, int prec, const cpa_sparsify *sp,
+                                float *const *hY, int64_t ldy, void *stream);
+
 /* Shifted Chebyshev coefficients (Eq. chebychev_coeff_shifted), host FP64:
  *   c_k = (2/L) sum_{l=1}^{L} cos(k theta_l) h(lambda_max/2 (cos theta_l + 1)),
  *   theta_l = pi (l - 1/2)/L,  k = 0..L-1.

@@ -9,4 +9,4 @@ from ._lib import (BF16, BF16X3, FP32, HARD, SOFT, TF32, WSOFT, Admm, BatchPlan,
                    ShrinkArray,
                    cpa_coeffs, cpa_svt_batched,
                    cpa_get_coeffs, cpa_get_lambda, cpa_lambda_bound, cpa_profile_enable, cpa_profile_read,
-                   cpa_svt, load, shrink_struct)
+                   cpa_svt, cpa_svt_host, load, shrink_struct)

@@ -21,7 +21,7 @@ PREC = {"fp32": FP32, "tf32": TF32, "bf16": BF16, "bf16x3": BF16X3}
 
 # every function include/cpa.h declares
 EXPORTS = ["cpa_create", "cpa_destroy", "cpa_status_string", "cpa_last_error", "cpa_coeffs",
-           "cpa_lambda_bound", "cpa_svt", "cpa_get_lambda", "cpa_get_coeffs", "cpa_batch_create",
+           "cpa_lambda_bound", "cpa_svt", "cpa_svt_host", "cpa_get_lambda", "cpa_get_coeffs", "cpa_batch_create",
            "cpa_batch_destroy", "cpa_svt_batched", "cpa_batch_lambdas", "cpa_profile_enable",
            "cpa_profile_read", "cpa_kernel_gemm_bf16", "cpa_kernel_split_bf16", "cpa_batch_read_lambdas",
            "cpa_lambda_bound_noalloc", "cpa_mlp_create", "cpa_mlp_destroy", "cpa_mlp_param_count",
@@ -73,6 +73,8 @@ def load(path: str = LIB_PATH):
             "cpa_lambda_bound": (ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, ctypes.c_int, _P(_d), _vp]),
             "cpa_svt": (ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, _P(CpaShrink), ctypes.c_int, _d,
                                        ctypes.c_int, _P(CpaSparsify), _vp, _i64, _vp]),
+            "cpa_svt_host": (ctypes.c_int, [_vp, ctypes.c_int, _P(_vp), _i64, _i64, _i64, _P(CpaShrink),
+                                            ctypes.c_int, _d, ctypes.c_int, _P(CpaSparsify), _P(_vp), _i64, _vp]),
             "cpa_get_lambda": (ctypes.c_int, [_vp, _P(_d), _vp]),
             "cpa_get_coeffs": (ctypes.c_int, [_vp, _P(_d), ctypes.c_int, _vp]),
             "cpa_batch_create": (ctypes.c_int, [_vp, ctypes.c_int, _P(_i64), _P(_i32), _P(_i32), _P(_i32),
@@ -249,6 +251,38 @@ def cpa_svt(h: Handle, X, shrink, L: int, lambda_max: float = 0.0, prec="fp32", 
     _check(load().cpa_svt(h.ptr, ctypes.c_void_p(ptr), m, n, ld, ctypes.byref(s), int(L), float(lambda_max), p,
                           sp, ctypes.c_void_p(yptr), ldy, _stream_ptr(stream)), "cpa_svt")
     return Y
+
+
+def cpa_svt_host(h: Handle, Xs, shrink, L: int, lambda_max: float = 0.0, prec="fp32", sparsify=None, Ys=None,
+                 stream=None):
+    """cpa_svt over a list of host (CPU, float32) matrices of one shape with
+    the copies overlapped (pinned tensors for overlap).  Returns the list of
+    outputs (allocated pinned if not given).  Asynchronous on `stream`:
+    synchronise it before reading the outputs."""
+    import torch
+    if not Xs:
+        return []
+    m, n = Xs[0].shape
+    for X in Xs:
+        if X.is_cuda or X.dtype != torch.float32 or X.dim() != 2 or tuple(X.shape) != (m, n) or X.stride(1) != 1:
+            raise ValueError("Xs must be host float32 m x n tensors with unit column stride")
+    if Ys is None:
+        Ys = [torch.empty((m, n), dtype=torch.float32, pin_memory=True) for _ in Xs]
+    for Y in Ys:
+        if Y.is_cuda or Y.dtype != torch.float32 or tuple(Y.shape) != (m, n) or Y.stride(1) != 1:
+            raise ValueError("Ys must be host float32 m x n tensors with unit column stride")
+    if len(Ys) != len(Xs) or len({X.stride(0) for X in Xs}) != 1 or len({Y.stride(0) for Y in Ys}) != 1:
+        raise ValueError("Xs and Ys must have the same length and one row stride each")
+    xp = (_vp * len(Xs))(*[ctypes.c_void_p(X.data_ptr()) for X in Xs])
+    yp = (_vp * len(Ys))(*[ctypes.c_void_p(Y.data_ptr()) for Y in Ys])
+    s = _as_shrink(shrink)
+    sp = None
+    if sparsify is not None:
+        sp = ctypes.byref(CpaSparsify(int(sparsify[0]), int(sparsify[1]), float(sparsify[2])))
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    _check(load().cpa_svt_host(h.ptr, len(Xs), xp, m, n, Xs[0].stride(0), ctypes.byref(s), int(L),
+                               float(lambda_max), p, sp, yp, Ys[0].stride(0), _stream_ptr(stream)), "cpa_svt_host")
+    return Ys
 
 
 def cpa_get_lambda(h: Handle, stream=None) -> float:

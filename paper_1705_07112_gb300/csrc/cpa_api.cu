@@ -36,6 +36,12 @@ struct cpa_ctx {
     double ms[CPA_NSTAGES] = {};
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
     std::vector<cudaEvent_t> event_pool;
+    // host-buffer streaming (cpa_svt_host): two device slots of X and Y, one
+    // copy stream per direction, slot events
+    float *stage = nullptr;
+    size_t stage_bytes = 0;
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t in_ready[2] = {}, computed[2] = {}, out_done[2] = {};
 };
 
 namespace {
@@ -295,6 +301,14 @@ cpa_status cpa_destroy(cpa_handle h) {
         cudaEventDestroy(p.second.second);
     }
     for (auto e : h->event_pool) cudaEventDestroy(e);
+    if (h->stage) cudaFree(h->stage);
+    if (h->h2d) cudaStreamDestroy(h->h2d);
+    if (h->d2h) cudaStreamDestroy(h->d2h);
+    for (int i = 0; i < 2; ++i) {
+        if (h->in_ready[i]) cudaEventDestroy(h->in_ready[i]);
+        if (h->computed[i]) cudaEventDestroy(h->computed[i]);
+        if (h->out_done[i]) cudaEventDestroy(h->out_done[i]);
+    }
     delete h;
     return CPA_OK;
 }
@@ -724,6 +738,82 @@ cpa_status cpa_kernel_split_bf16(const float *X, int rows, int cols, int64_t ldx
         return CPA_ERR_INVALID_ARG;
     CK(split_bf16(X, rows, cols, ldx, transpose != 0, (__nv_bfloat16 *)hi, (__nv_bfloat16 *)lo, ldo,
                   (cudaStream_t)stream));
+    return CPA_OK;
+}
+
+
+// A sequence of host matrices through cpa_svt with the copies overlapped:
+// slot i % 2 holds matrix i on the device.  The H2D copy of matrix i + 1
+// (stream h2d) runs while matrix i is shrunk (the caller's stream) and the
+// D2H copy of matrix i (stream d2h) runs while matrix i + 1 is; events
+// order slot reuse.  The caller's stream waits for the last D2H copy.
+cpa_status cpa_svt_host(cpa_handle h, int count, const float *const *hX, int64_t m, int64_t n, int64_t ldx,
+                        const cpa_shrink *sh, int L, double lambda_max, int prec, const cpa_sparsify *sp,
+                        float *const *hY, int64_t ldy, void *stream) {
+    if (!h || count < 0 || (count > 0 && (!hX || !hY)) || m < 1 || n < 1 || ldx < n || ldy < n)
+        return CPA_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i)
+        if (!hX[i] || !hY[i]) return CPA_ERR_INVALID_ARG;
+    if (count == 0) return CPA_OK;
+    cpa_status r;
+    if ((r = set_device(h)) != CPA_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t mat = sizeof(float) * (size_t)(m * n);
+    if (h->stage_bytes < 4 * mat) {
+        if (h->stage) {
+            CK(cudaStreamSynchronize(st));
+            if (h->h2d) CK(cudaStreamSynchronize(h->h2d));
+            if (h->d2h) CK(cudaStreamSynchronize(h->d2h));
+            cudaFree(h->stage);
+            h->stage = nullptr;
+            h->stage_bytes = 0;
+        }
+        if (cudaMalloc(&h->stage, 4 * mat) != cudaSuccess) return CPA_ERR_NO_MEMORY;
+        h->stage_bytes = 4 * mat;
+    }
+    if (!h->h2d) {
+        CK(cudaStreamCreateWithFlags(&h->h2d, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&h->d2h, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+            CK(cudaEventCreateWithFlags(&h->in_ready[i], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&h->computed[i], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&h->out_done[i], cudaEventDisableTiming));
+        }
+    }
+    float *Xd[2] = {h->stage, h->stage + m * n}, *Yd[2] = {h->stage + 2 * m * n, h->stage + 3 * m * n};
+    // earlier work on the caller's stream (and an earlier call's copies) first
+    cudaEvent_t start = nullptr;
+    CK(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    CK(cudaEventRecord(start, st));
+    CK(cudaStreamWaitEvent(h->h2d, start, 0));
+    CK(cudaStreamWaitEvent(h->d2h, start, 0));
+    cudaEventDestroy(start);
+    auto h2d = [&](int i) -> cudaError_t {
+        const int sl = i & 1;
+        if (i >= 2) {
+            cudaError_t e = cudaStreamWaitEvent(h->h2d, h->computed[sl], 0);   // matrix i-2 no longer read
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = cudaMemcpy2DAsync(Xd[sl], sizeof(float) * n, hX[i], sizeof(float) * ldx, sizeof(float) * n,
+                                          m, cudaMemcpyHostToDevice, h->h2d);
+        if (e != cudaSuccess) return e;
+        return cudaEventRecord(h->in_ready[sl], h->h2d);
+    };
+    CK(h2d(0));
+    for (int i = 0; i < count; ++i) {
+        const int sl = i & 1;
+        if (i + 1 < count) CK(h2d(i + 1));
+        CK(cudaStreamWaitEvent(st, h->in_ready[sl], 0));
+        if (i >= 2) CK(cudaStreamWaitEvent(st, h->out_done[sl], 0));   // Y slot copied out
+        if ((r = cpa_svt(h, Xd[sl], m, n, n, sh, L, lambda_max, prec, sp, Yd[sl], n, stream)) != CPA_OK) return r;
+        CK(cudaEventRecord(h->computed[sl], st));
+        CK(cudaStreamWaitEvent(h->d2h, h->computed[sl], 0));
+        CK(cudaMemcpy2DAsync(hY[i], sizeof(float) * ldy, Yd[sl], sizeof(float) * n, sizeof(float) * n, m,
+                             cudaMemcpyDeviceToHost, h->d2h));
+        CK(cudaEventRecord(h->out_done[sl], h->d2h));
+    }
+    CK(cudaStreamWaitEvent(st, h->out_done[(count - 1) & 1], 0));
+    if (count >= 2) CK(cudaStreamWaitEvent(st, h->out_done[count & 1], 0));
     return CPA_OK;
 }
 

@@ -265,3 +265,36 @@ def test_recurrence_launch_forms_sampled(cpa, handle, shape, prec, series):
         sampled_rows_check(cpa, handle, X, s, 30, prec, [0, 1, p // 2, p - 2, p - 1], tol)
     finally:
         _lib.cpa_set_option(handle, _lib.OPT_SERIES, _lib.SERIES_FORWARD)
+
+
+def test_svt_host_sequence_matches_device_calls(cpa, handle):
+    """cpa_svt_host over host matrices (pinned and pageable, ragged row
+    strides, one and several matrices) gives what cpa_svt gives on the same
+    inputs, bit for bit (the same kernels run on the same values)."""
+    import torch
+    rng = np.random.default_rng(12)
+    m, n = 300, 170
+    Xs = [(rng.standard_normal((m, 4)) @ rng.standard_normal((4, n)) + 0.1 * rng.standard_normal((m, n)))
+          .astype(np.float32) for _ in range(5)]
+    shrink = {"kind": O.SOFT, "tau": 2.0}
+    # a fixed bound: the device bound sums across blocks in a varying order
+    lam = 1.05 * max(float(np.linalg.norm(X.astype(np.float64), 2)) ** 2 for X in Xs)
+    want = []
+    for X in Xs:
+        Y = cpa.cpa_svt(handle, to_dev(X), shrink, 20, lam, "bf16")
+        torch.cuda.synchronize()
+        want.append(Y.cpu().numpy())
+    for pinned in (True, False):
+        for count in (1, 2, 5):
+            hx = []
+            for X in Xs[:count]:
+                big = torch.zeros((m, n + 3), dtype=torch.float32, pin_memory=pinned)
+                big[:, :n] = torch.from_numpy(X)
+                hx.append(big[:, :n])
+            hy = [torch.full((m, n + 5), -7.0, dtype=torch.float32, pin_memory=pinned)[:, :n] for _ in range(count)]
+            cpa.cpa_svt_host(handle, hx, shrink, 20, lam, "bf16", Ys=hy)
+            torch.cuda.synchronize()
+            for i in range(count):
+                assert np.array_equal(hy[i].numpy(), want[i]), (pinned, count, i)
+    with pytest.raises(ValueError):
+        cpa.cpa_svt_host(handle, [to_dev(Xs[0])], shrink, 20)
