@@ -139,6 +139,8 @@ struct BatchSmem {
     double tab[4 * kMaxBatchTerms];
     double hs[kMaxBatchTerms];
     double scal[4];                      // theta, r, trace, lambda
+    double lam;                          // the bound, formed by thread 0
+    float s2;                            // 2 / lambda in FP32, formed by thread 0
     int next_it;                         // work item fetched by thread 0
 };
 
@@ -594,14 +596,21 @@ __global__ void __launch_bounds__(kThreads, 2)
                     const float dd = own ? a - th * vu : 0.f;
                     const float r2 = bsumf(dd * dd, S.redf, rs);
                     const float tr = bsumf(own ? S.g[row * (kP + 1) + row] : 0.f, S.redf, rs);
-                    lam = ((double)th + sqrt((double)fmaxf(r2, 0.f))) * (1.0 + kLambdaMargin);
-                    if (lam > (double)tr) lam = (double)tr;
-                    if (!isfinite(lam) || !isfinite(tr)) {
-                        if (tid == 0) atomicExch(status, (int)CPA_ERR_NONFINITE);
-                        lam = 1.0;
-                    } else if (!(lam > 0.0)) {
-                        lam = tr > 0.f ? (double)tr : 1.0;
+                    // one thread: FP64 square roots are long sequences on
+                    // this part's scarce FP64 pipe
+                    if (tid == 0) {
+                        double lb = ((double)th + sqrt((double)fmaxf(r2, 0.f))) * (1.0 + kLambdaMargin);
+                        if (lb > (double)tr) lb = (double)tr;
+                        if (!isfinite(lb) || !isfinite(tr)) {
+                            atomicExch(status, (int)CPA_ERR_NONFINITE);
+                            lb = 1.0;
+                        } else if (!(lb > 0.0)) {
+                            lb = tr > 0.f ? (double)tr : 1.0;
+                        }
+                        S.lam = lb;
                     }
+                    __syncthreads();
+                    lam = S.lam;
                 }
             }
         }
@@ -617,6 +626,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         // cos(pi m / 2L), m < 4L: evaluated for m <= L, the rest by symmetry
         // (cos(2 pi - x) = cos x, cos(pi - x) = -cos x)
         for (int e = tid; e <= L; e += kThreads) S.tab[e] = cospi((double)e / (2.0 * L));
+        if (tid == 0) S.s2 = (float)(2.0 / lam);
         __syncthreads();
         for (int e = L + 1 + tid; e < 4 * L; e += kThreads) {
             const int mm = e > 2 * L ? 4 * L - e : e;
@@ -640,7 +650,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         __syncthreads();
 
         // ---- shift: At = (2/lambda) G (operand), Psi_1 = At - Id, H = c0/2 Id + c1 Psi_1
-        const float s2 = (float)(2.0 / lam);
+        const float s2 = S.s2;
         const float c0h = (float)(0.5 * S.coef[0]), c1 = L > 1 ? (float)S.coef[1] : 0.f;
         Frag z1, z0, h;   // Psi_{k-1}, Psi_{k-2}, H in the accumulator layout
 #pragma unroll

@@ -182,11 +182,19 @@ __global__ void shift_kernel(const float *__restrict__ G, int64_t ldg, int p, co
                              const double *c, int L, float *A, float *Z1, float *H, int64_t ld,
                              __nv_bfloat16 *Athi, __nv_bfloat16 *Atlo, __nv_bfloat16 *Z1hi, __nv_bfloat16 *Z1lo,
                              int64_t ldb, int clenshaw, __nv_bfloat16 *Z0hi, __nv_bfloat16 *Z0lo) {
-    float s = (float)(2.0 / lam[0]);
-    float c0h = (float)(0.5 * c[0]);
-    float c1 = L > 1 ? (float)c[1] : 0.f;
+    // the scalars once per block: an FP64 division in every thread would
+    // queue hundreds of thousands of them on this part's scarce FP64 pipe
+    __shared__ float sc[5];
     const bool cl = clenshaw && L >= 3;
-    const float zc = cl ? (float)c[L - 2] : 0.f, za = cl ? (float)(2.0 * c[L - 1]) : 1.f;
+    if (threadIdx.x == 0) {
+        sc[0] = (float)(2.0 / lam[0]);
+        sc[1] = (float)(0.5 * c[0]);
+        sc[2] = L > 1 ? (float)c[1] : 0.f;
+        sc[3] = cl ? (float)c[L - 2] : 0.f;
+        sc[4] = cl ? (float)(2.0 * c[L - 1]) : 1.f;
+    }
+    __syncthreads();
+    const float s = sc[0], c0h = sc[1], c1 = sc[2], zc = sc[3], za = sc[4];
     // a block per row (grid-stride), threads across the row: no 64-bit
     // division per element
     for (int i = blockIdx.x; i < p; i += gridDim.x)
@@ -301,8 +309,9 @@ __device__ __forceinline__ void grid_barrier(unsigned int *count, unsigned int &
 }
 
 // All power iterations in one cooperative launch.  Iteration t: w_{t+1} =
-// G (w_t / |w_t|), one warp per row, |w_{t+1}|^2 accumulated in FP64 by
-// atomics into norm2[t+1]; a grid barrier separates iterations.  Block 0
+// G (w_t / |w_t|), one warp per row, |w_{t+1}|^2 summed in FP32 per block and
+// in FP64 across blocks (atomics into norm2[t+1]); a grid barrier separates
+// iterations; the scale 1/|w_t| is formed in FP32.  Block 0
 // then forms theta, r, the trace and lambda as power_final_kernel does.
 // Dynamic shared memory: when `cache`, every warp owns at most one row of
 // G and keeps it for all iterations (row stride p rounded up to 4); when
@@ -313,7 +322,7 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
                                                                double *norm2, unsigned int *bar, double margin,
                                                                double *out, int *err, int cache, int stage) {
     extern __shared__ __align__(16) float grow[];
-    __shared__ double wpart[16];   // per-warp |w|^2 partials
+    __shared__ float wpart[16];    // per-warp |w|^2 partials
     __shared__ float sscale;       // 1 / |v| of the current iterate
     unsigned int target = 0;
     const int lane = threadIdx.x & 31;
@@ -348,10 +357,11 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
     for (int t = 0; t <= iters; ++t) {
         const float *v = (t & 1) ? v1 : v0;
         float *w = (t & 1) ? v0 : v1;
-        // 1 / |v| once per block (FP64 is a scarce pipe: one thread)
+        // 1 / |v| once per block, in FP32 (FP64 square roots and divisions
+        // are long dependent sequences on this part's scarce FP64 pipe)
         if (threadIdx.x == 0) {
             const double nin = __ldcg(&norm2[t]);   // written by other blocks: read at L2
-            sscale = nin > 0.0 ? (float)(1.0 / sqrt(nin)) : 0.f;
+            sscale = nin > 0.0 ? __frcp_rn(__fsqrt_rn((float)nin)) : 0.f;
         }
         if (stage) {
             // written by other blocks before the barrier: read at L2
@@ -362,7 +372,7 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
         __syncthreads();
         const float scale = sscale;
         const float *vsrc = stage ? vs : v;
-        double part = 0.0;
+        float part = 0.f;
         for (int row = gwarp; row < p; row += nwarps) {
             const float *g = G + (int64_t)row * ldg;
             float acc = 0.f;
@@ -410,16 +420,17 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
             acc = warp_sumf(acc) * scale;
             if (lane == 0) {
                 w[row] = acc;
-                part += (double)acc * (double)acc;
+                part = fmaf(acc, acc, part);
             }
         }
-        // lane 0 of each warp holds its rows' part: one warp adds the 16
+        // lane 0 of each warp holds its rows' part (FP32: it only scales
+        // the next iterate); one warp adds the 16, one FP64 atomic per block
         if (lane == 0) wpart[threadIdx.x >> 5] = part;
         __syncthreads();
         if (threadIdx.x < 32) {
-            double q = threadIdx.x < (int)(blockDim.x >> 5) ? wpart[threadIdx.x] : 0.0;
-            q = warp_sum(q);
-            if (threadIdx.x == 0 && q != 0.0) atomicAdd(&norm2[t + 1], q);
+            float q = threadIdx.x < (int)(blockDim.x >> 5) ? wpart[threadIdx.x] : 0.f;
+            q = warp_sumf(q);
+            if (threadIdx.x == 0 && q != 0.f) atomicAdd(&norm2[t + 1], (double)q);
         }
         grid_barrier(bar, target, err);
     }
