@@ -479,12 +479,13 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
         set_scalar2_kernel<<<1, 1, 0, st>>>(w.out + 3, lambda_max, 0.0);
         CK(cudaGetLastError());
     } else {
+        // the bound's launch also forms the coefficients (FP64) in its last block
         StageScope sc(h, CPA_STAGE_BOUND, st, 1);
         CK(power_bound_persistent(w.G, w.ldp, (int)p, iters, w.v0, w.v1, w.norm2, (unsigned int *)w.flag,
-                                  w.flag + 1, w.out, st, h->num_sms));
+                                  w.flag + 1, w.out, st, h->num_sms, L, &sp_, w.coef));
     }
     // coefficients (FP64, on the device so the call stays asynchronous)
-    {
+    if (lambda_max > 0.0) {
         StageScope sc(h, CPA_STAGE_COEFF, st, 1);
         CK(device_coeffs(w.out + 3, 0.0, L, sp_, w.coef, st));
     }

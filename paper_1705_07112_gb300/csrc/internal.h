@@ -143,10 +143,13 @@ namespace cpa {
 cudaError_t power_bound(const float *G, int64_t ldg, int p, int iters, float *v0, float *v1, double *norm2,
                         double *out, cudaStream_t st);
 // The same bound with all iterations in one cooperative launch (grid
-// barrier between iterations).  bar, err: device scratch words.
+// barrier between iterations).  bar, err: device scratch words.  coef (L
+// doubles, optional): the block that forms lambda also forms the
+// coefficients on [0, lambda] for the response sp, as device_coeffs would.
 cudaError_t power_bound_persistent(const float *G, int64_t ldg, int p, int iters, float *v0, float *v1,
                                    double *norm2, unsigned int *bar, int *err, double *out, cudaStream_t st,
-                                   int num_sms);
+                                   int num_sms, int L = 0, const ShrinkParams *sp = nullptr,
+                                   double *coef = nullptr);
 cudaError_t device_coeffs(const double *lam_dev, double lam_host, int L, const ShrinkParams &s, double *c,
                           cudaStream_t st);
 // A = (2/lambda) G - Id, Z1 = A, H = c0/2 Id + c1 A (FP32).  For the

@@ -320,7 +320,8 @@ __device__ __forceinline__ void grid_barrier(unsigned int *count, unsigned int &
 __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__restrict__ G, int64_t ldg, int p,
                                                                int iters, uint64_t seed, float *v0, float *v1,
                                                                double *norm2, unsigned int *bar, double margin,
-                                                               double *out, int *err, int cache, int stage) {
+                                                               double *out, int *err, int cache, int stage,
+                                                               int L, ShrinkParams sp, double *coef) {
     extern __shared__ __align__(16) float grow[];
     __shared__ float wpart[16];    // per-warp |w|^2 partials
     __shared__ float sscale;       // 1 / |v| of the current iterate
@@ -479,6 +480,29 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
         out[2] = tr;
         out[3] = lam;
         out[4] = flag;
+        sh_th = lam;
+    }
+    if (!coef) return;
+    // the coefficients of Eq. chebychev_coeff_shifted on [0, lambda] in the
+    // same block (as coeffs_kernel computes them), in the shared memory the
+    // rows of G used: table cos(pi m / 2L), m < 4L, then h at the L nodes
+    __syncthreads();
+    const double lamv = sh_th;
+    double *tab = reinterpret_cast<double *>(grow);
+    double *hs = tab + 4 * L;
+    for (int m = threadIdx.x; m < 4 * L; m += blockDim.x) tab[m] = cospi((double)m / (2.0 * L));
+    __syncthreads();
+    for (int l = threadIdx.x; l < L; l += blockDim.x) hs[l] = response(sp, 0.5 * lamv * (tab[(2 * l + 1) % (4 * L)] + 1.0));
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = warp; k < L; k += nw) {
+        double acc = 0.0;
+        for (int l = lane; l < L; l += 32) {
+            const int m = (int)(((int64_t)k * (2 * l + 1)) % (4 * L));
+            acc += tab[m] * hs[l];
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) coef[k] = 2.0 / (double)L * acc;
     }
 }
 
@@ -486,7 +510,7 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
 
 cudaError_t power_bound_persistent(const float *G, int64_t ldg, int p, int iters, float *v0, float *v1,
                                    double *norm2, unsigned int *bar, int *err, double *out, cudaStream_t st,
-                                   int num_sms) {
+                                   int num_sms, int L, const ShrinkParams *sp, double *coef) {
     cudaError_t r = cudaMemsetAsync(bar, 0, sizeof(unsigned int), st);
     if (r != cudaSuccess) return r;
     r = cudaMemsetAsync(err, 0, sizeof(int), st);
@@ -501,7 +525,10 @@ cudaError_t power_bound_persistent(const float *G, int64_t ldg, int p, int iters
     const int cache = ((int64_t)grid * 16 >= p && cache_bytes <= budget) ? 1 : 0;
     const size_t stage_bytes = (size_t)p4 * sizeof(float);
     const int stage = (cache ? cache_bytes : 0) + stage_bytes <= budget ? 1 : 0;
-    const size_t smem = (cache ? cache_bytes : 0) + (stage ? stage_bytes : 0);
+    size_t smem = (cache ? cache_bytes : 0) + (stage ? stage_bytes : 0);
+    // the coefficient table and node values reuse the same shared memory
+    if (coef && (L < 1 || L > kMaxTerms || !sp)) return cudaErrorInvalidValue;
+    if (coef && smem < (size_t)5 * L * sizeof(double)) smem = (size_t)5 * L * sizeof(double);
     if (smem > 48 * 1024) {
         static bool attr = false;
         if (!attr) {
@@ -523,8 +550,9 @@ cudaError_t power_bound_persistent(const float *G, int64_t ldg, int p, int iters
     cfg.numAttrs = 1;
     const double margin = kLambdaMargin;
     const uint64_t seed = kStartSeed;
+    const ShrinkParams spv = sp ? *sp : ShrinkParams{};
     return cudaLaunchKernelEx(&cfg, power_persistent_kernel, G, ldg, p, iters, seed, v0, v1, norm2, bar, margin, out,
-                              err, cache, stage);
+                              err, cache, stage, coef ? L : 0, spv, coef);
 }
 
 cudaError_t power_bound(const float *G, int64_t ldg, int p, int iters, float *v0, float *v1,
