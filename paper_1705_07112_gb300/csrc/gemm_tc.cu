@@ -22,6 +22,10 @@
 //               shared-memory transpose so those stores are coalesced too.
 // Split precision (nsplit = 3) runs the K loop three times over
 // (A_hi,B_hi), (A_hi,B_lo), (A_lo,B_hi) into the same accumulator.
+// The recurrence runs all its steps in one cooperative launch with a grid
+// barrier per step; when each CTA owns at most one tile, the tile's FP32
+// state (Psi_{k-1}, Psi_{k-2}, H) stays in tensor memory between steps and
+// only the BF16 operand copies of each Psi_k go through global memory.
 //
 // Every mbarrier wait is bounded (~2 s of clock); on expiry the CTA raises
 // an error flag, stops issuing work, drains the TMA loads it started, frees
