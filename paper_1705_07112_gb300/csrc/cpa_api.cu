@@ -41,7 +41,7 @@ struct cpa_ctx {
     float *stage = nullptr;
     size_t stage_bytes = 0;
     cudaStream_t h2d = nullptr, d2h = nullptr;
-    cudaEvent_t in_ready[2] = {}, computed[2] = {}, out_done[2] = {};
+    cudaEvent_t in_ready[2] = {}, computed[2] = {}, out_done[2] = {}, start = nullptr;
 };
 
 namespace {
@@ -309,6 +309,7 @@ cpa_status cpa_destroy(cpa_handle h) {
         if (h->computed[i]) cudaEventDestroy(h->computed[i]);
         if (h->out_done[i]) cudaEventDestroy(h->out_done[i]);
     }
+    if (h->start) cudaEventDestroy(h->start);
     delete h;
     return CPA_OK;
 }
@@ -780,15 +781,13 @@ cpa_status cpa_svt_host(cpa_handle h, int count, const float *const *hX, int64_t
             CK(cudaEventCreateWithFlags(&h->computed[i], cudaEventDisableTiming));
             CK(cudaEventCreateWithFlags(&h->out_done[i], cudaEventDisableTiming));
         }
+        CK(cudaEventCreateWithFlags(&h->start, cudaEventDisableTiming));
     }
     float *Xd[2] = {h->stage, h->stage + m * n}, *Yd[2] = {h->stage + 2 * m * n, h->stage + 3 * m * n};
     // earlier work on the caller's stream (and an earlier call's copies) first
-    cudaEvent_t start = nullptr;
-    CK(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
-    CK(cudaEventRecord(start, st));
-    CK(cudaStreamWaitEvent(h->h2d, start, 0));
-    CK(cudaStreamWaitEvent(h->d2h, start, 0));
-    cudaEventDestroy(start);
+    CK(cudaEventRecord(h->start, st));
+    CK(cudaStreamWaitEvent(h->h2d, h->start, 0));
+    CK(cudaStreamWaitEvent(h->d2h, h->start, 0));
     auto h2d = [&](int i) -> cudaError_t {
         const int sl = i & 1;
         if (i >= 2) {
