@@ -179,8 +179,18 @@ CPA_API cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, 
 
 /* The Lambda_max used by the last cpa_svt on this handle (synchronises
  * `stream`).  Returns NONFINITE / BOUND if the device-computed bound was
- * not a positive finite number (the output of that call is then unusable). */
+ * not a positive finite number, TIMEOUT if a bounded device-side wait of
+ * that call gave up (the output of that call is then unusable). */
 CPA_API cpa_status cpa_get_lambda(cpa_handle h, double *lambda_out, void *stream);
+
+/* Device-side status of the last cpa_svt on this handle: synchronises
+ * `stream`, then returns CPA_OK, CPA_ERR_TIMEOUT (a bounded wait of one of
+ * its kernels gave up: a grid barrier between steps, or a wait inside a
+ * CTA; the kernels then stop, drain their copies in flight and release
+ * their tensor memory, so the handle and the context stay usable),
+ * CPA_ERR_NONFINITE or CPA_ERR_BOUND (the computed bound).  INVALID_ARG
+ * before the first cpa_svt. */
+CPA_API cpa_status cpa_sync_status(cpa_handle h, void *stream);
 
 /* The L coefficients used by the last cpa_svt (synchronises `stream`). */
 CPA_API cpa_status cpa_get_coeffs(cpa_handle h, double *c_out, int L, void *stream);
@@ -195,12 +205,25 @@ CPA_API cpa_status cpa_get_coeffs(cpa_handle h, double *c_out, int L, void *stre
  *     - b_{k+2} (k = L-1 .. 0), H_hat = (b_0 - b_2) / 2: the same L-2
  *     products, no running sum (less memory traffic per step).  Its
  *     intermediates are larger than the filter they sum to, so with plain
- *     BF16 operands (CPA_BF16) its error is about 50 times the forward
- *     recurrence's (4e-3 to 6e-3 relative at p = 1000 .. 2048, L = 30);
- *     with CPA_BF16X3 or CPA_FP32 it is within 2x.
+ *     BF16 operands its error was measured at about 50 times the forward
+ *     recurrence's (4e-3 to 6e-3 relative at p = 1000 .. 2048, L = 30),
+ *     above the BF16 path's 2e-3 bar: cpa_svt with this series and
+ *     CPA_BF16 returns CPA_ERR_UNSUPPORTED.  With CPA_BF16X3 or CPA_FP32
+ *     its error is within 2x of the forward recurrence's.
  * Returns CPA_ERR_INVALID_ARG for an unknown option or value.
  * ------------------------------------------------------------------------- */
-enum { CPA_OPT_SERIES = 1 };
+/* CPA_OPT_WAIT_KCYCLES: limit, in thousands of SM clock cycles, of the
+ *   waits at the grid barriers between the steps of the cooperative launches
+ *   (the power iteration and the tensor-core recurrence); 0 (the default)
+ *   means 4,000,000 (about 2 s at 2 GHz).  When a wait runs out the kernel
+ *   records CPA_ERR_TIMEOUT (read by cpa_sync_status, cpa_get_lambda or, for
+ *   cpa_lambda_bound, its return value), stops, drains its copies in flight
+ *   and frees its tensor memory: a failed call leaves the handle usable.
+ * CPA_OPT_STALL_TEST: 1 makes the first grid barrier of those launches wait
+ *   for one arrival more than the grid makes, so that it can end only by the
+ *   limit above; for tests of the timeout path.  0 (the default) is normal
+ *   operation. */
+enum { CPA_OPT_SERIES = 1, CPA_OPT_WAIT_KCYCLES = 2, CPA_OPT_STALL_TEST = 3 };
 enum { CPA_SERIES_FORWARD = 0, CPA_SERIES_CLENSHAW = 1 };
 CPA_API cpa_status cpa_set_option(cpa_handle h, int option, int value);
 
@@ -271,6 +294,9 @@ CPA_API cpa_status cpa_kernel_split_bf16(const float *X, int rows, int cols, int
  *   CPA_ERR_INVALID_ARG.
  *   The first call on each device looks up the array's device address
  *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   The address is kept for the life of the process: after a reset of the
+ *   device's primary context (cudaDeviceReset) it is stale, so do not use
+ *   this entry point on a device that the process has reset.
  *   Every call shares the one array: calls whose work overlaps on the GPU
  *   (other host threads, other streams) race on it and must be serialised
  *   by the caller.

@@ -21,6 +21,10 @@ Functions and the passage each follows:
 * ``cpa_clenshaw``        the same filter summed by Clenshaw's recurrence
 * ``cpa_vec``             the same filter applied to one vector
                           (Eq. prop_another_form), for sampled outputs at any size
+* ``cpa_block`` / ``filter_block``  the same vector form on a block of vectors
+                          at once (numpy's matmul as the product primitive),
+                          with the Gram matrix given through X or as a symmetric
+                          matrix S (a thresholded Phi)
 * ``lambda_bound``        power-iteration bound on Lambda_max (the paper names no
                           method; reading stated in the C source)
 * ``svd_jacobi``          one-sided Jacobi SVD
@@ -303,3 +307,46 @@ def approx_error_spectral(sv, s: Shrink, alpha: int, lam: float) -> float:
         hh = series_rec(ck, xh)
         tot += (sig * (hh - h(s, x))) ** 2
     return float(np.sqrt(tot))
+
+
+def _series_block(prod, s: Shrink, alpha: int, lam: float, V) -> np.ndarray:
+    """H_hat V for the shifted series of Algorithm 1 (Eqs.
+    chebychev_series_matrix_shift2 and recurrence_our_method applied to the
+    columns of V, as Eq. prop_another_form applies it to one vector):
+    Z_0 = V, Z_1 = B_hat V, Z_k = 2 B_hat Z_{k-1} - Z_{k-2}, B_hat Z =
+    (2/lam) prod(Z) - Z, H_hat V = c_0/2 Z_0 + sum_{k>=1} c_k Z_k.
+    prod(Z) is the product of the symmetric matrix with Z."""
+    if alpha < 1 or not (lam > 0.0):
+        raise ValueError("series: invalid arguments (alpha=%r, lam=%r)" % (alpha, lam))
+    c = coeffs(s, alpha, lam)
+    V = np.asarray(V, dtype=np.float64)
+    z0 = V
+    out = 0.5 * c[0] * z0
+    if alpha == 1:
+        return out
+    z1 = 2.0 / lam * prod(z0) - z0
+    out = out + c[1] * z1
+    for k in range(2, alpha):
+        z2 = 2.0 * (2.0 / lam * prod(z1) - z1) - z0
+        out = out + c[k] * z2
+        z0, z1 = z1, z2
+    return out
+
+
+def cpa_block(X, s: Shrink, alpha: int, lam: float, V) -> np.ndarray:
+    """H_hat(G) V, G the Gram matrix of the smaller side of X, for the p x k
+    block V (p = min(m, n)); G Z is formed as X^T (X Z) or X (X^T Z)."""
+    X = np.asarray(X, dtype=np.float64)
+    m, n = X.shape
+    V = np.asarray(V, dtype=np.float64)
+    if V.shape[0] != min(m, n):
+        raise ValueError("cpa_block: V must have min(m, n) rows")
+    prod = (lambda Z: X.T @ (X @ Z)) if m >= n else (lambda Z: X @ (X.T @ Z))
+    return _series_block(prod, s, alpha, lam, V)
+
+
+def filter_block(S, s: Shrink, alpha: int, lam: float, V) -> np.ndarray:
+    """H_hat(S) V for a symmetric p x p matrix S given explicitly (the
+    thresholded Phi of Eq. threshold_components), p x k block V."""
+    S = np.asarray(S, dtype=np.float64)
+    return _series_block(lambda Z: S @ Z, s, alpha, lam, V)

@@ -28,8 +28,9 @@ EXPORTS = ["cpa_create", "cpa_destroy", "cpa_status_string", "cpa_last_error", "
            "cpa_mlp_set_params", "cpa_mlp_get_params", "cpa_mlp_forward", "cpa_mlp_gradients",
            "cpa_mlp_train_step", "cpa_batch_features", "cpa_svt_batched_learned", "cpa_batch_read_choices",
            "cpa_admm_create", "cpa_admm_destroy", "cpa_admm_rpca", "cpa_set_option",
-           "cpa_completion_create", "cpa_completion_destroy", "cpa_completion_run"]
+           "cpa_completion_create", "cpa_completion_destroy", "cpa_completion_run", "cpa_sync_status"]
 OPT_SERIES, SERIES_FORWARD, SERIES_CLENSHAW = 1, 0, 1
+OPT_WAIT_KCYCLES, OPT_STALL_TEST = 2, 3
 STAGES = ["prep", "gram", "bound", "coeff", "shift", "recur", "apply", "sparse"]
 T_IDENTITY, T_HAAR1_LOWPASS, T_BLOCK_DCT8, T_DCT = 0, 1, 2, 3
 SPARSE_OFF, SPARSE_ABS, SPARSE_TOPK = 0, 1, 2
@@ -76,6 +77,7 @@ def load(path: str = LIB_PATH):
             "cpa_svt_host": (ctypes.c_int, [_vp, ctypes.c_int, _P(_vp), _i64, _i64, _i64, _P(CpaShrink),
                                             ctypes.c_int, _d, ctypes.c_int, _P(CpaSparsify), _P(_vp), _i64, _vp]),
             "cpa_get_lambda": (ctypes.c_int, [_vp, _P(_d), _vp]),
+            "cpa_sync_status": (ctypes.c_int, [_vp, _vp]),
             "cpa_get_coeffs": (ctypes.c_int, [_vp, _P(_d), ctypes.c_int, _vp]),
             "cpa_batch_create": (ctypes.c_int, [_vp, ctypes.c_int, _P(_i64), _P(_i32), _P(_i32), _P(_i32),
                                                 ctypes.c_int, _P(_vp)]),
@@ -289,6 +291,12 @@ def cpa_get_lambda(h: Handle, stream=None) -> float:
     out = ctypes.c_double()
     _check(load().cpa_get_lambda(h.ptr, ctypes.byref(out), _stream_ptr(stream)), "cpa_get_lambda")
     return out.value
+
+
+def cpa_sync_status(h: Handle, stream=None) -> int:
+    """Device-side status of the last cpa_svt on the handle (synchronises
+    the stream); returns the status code instead of raising."""
+    return int(load().cpa_sync_status(h.ptr, _stream_ptr(stream)))
 
 
 def cpa_get_coeffs(h: Handle, L: int, stream=None) -> np.ndarray:

@@ -30,6 +30,8 @@ struct cpa_ctx {
     int last_L = 0;
     bool have_last = false;
     int series = CPA_SERIES_FORWARD;   // how the filter's series is summed
+    WaitPolicy wait;                   // grid-barrier wait limit, test stall
+    int *d_err = nullptr;              // error word of the last cpa_svt's tensor-core kernels
     // diagnostics
     bool profiling = false;
     int64_t launches[CPA_NSTAGES] = {};
@@ -197,7 +199,7 @@ SvtWs carve(char *base, int64_t m, int64_t n, int L, int iters, int prec, bool s
     w.out = c.take<double>(8);
     w.norm2 = c.take<double>(iters + 2);
     w.coef = c.take<double>(std::max(L, 2));
-    w.flag = c.take<int>(8);
+    w.flag = c.take<int>(8);   // barrier and error words: 0, 1 bound; 2 recurrence; 3, 4 top-k; 5 tensor-core waits
     w.G = c.take<float>(pp);
     w.A = c.take<float>(pp);
     w.Z[0] = c.take<float>(pp);
@@ -355,6 +357,7 @@ cpa_status run_gram(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
     const int nsplit = 3;
     e.symmetric_upper = 1;
     e.sym_full_d = 1;   // G is read in full by the power iteration and the shift
+    e.err = w.flag + 5;
     TcOperand op;
     if (m >= n) {   // rows of X^T (n x m)
         op.hi = w.Xthi; op.lo = w.Xtlo; op.ld = w.ldm; op.rows = (int)n;
@@ -389,7 +392,7 @@ cpa_status cpa_lambda_bound(cpa_handle h, const float *dX, int64_t m, int64_t n,
     int64_t p = std::min(m, n);
     if ((s = run_gram(h, dX, m, n, ldx, w, CPA_FP32, st)) != CPA_OK) return s;
     CK(power_bound_persistent(w.G, w.ldp, (int)p, iters, w.v0, w.v1, w.norm2, (unsigned int *)w.flag, w.flag + 1,
-                              w.out, st, h->num_sms));
+                              w.out, st, h->num_sms, 0, nullptr, nullptr, h->wait));
     CK(cudaMemcpyAsync(h->h_pin, w.out, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (h->h_pin[4] != 0.0) return (cpa_status)(int)h->h_pin[4];
@@ -420,12 +423,20 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
         return CPA_ERR_INVALID_ARG;
     if (prec != CPA_FP32 && h->cc < 100) return CPA_ERR_UNSUPPORTED;
     if (prec == CPA_TF32) return CPA_ERR_UNSUPPORTED;
+    // Clenshaw's intermediates are larger than the filter they sum to, so a
+    // plain BF16 operand per step costs about fifty times the forward
+    // recurrence's error, above the BF16 path's 2e-3 bar: not offered
+    if (h->series == CPA_SERIES_CLENSHAW && prec == CPA_BF16) return CPA_ERR_UNSUPPORTED;
     if ((s = set_device(h)) != CPA_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     const int iters = kDefaultPowerIters;
     SvtWs w = carve(nullptr, m, n, L, iters, prec, sparse);
     if ((s = ensure_ws(h, w.bytes, st)) != CPA_OK) return s;
     w = carve(h->ws, m, n, L, iters, prec, sparse);
+    // the call's error word (timeouts of the tensor-core kernels' waits),
+    // read back by cpa_get_lambda and cpa_sync_status
+    h->d_err = w.flag + 5;
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
     const int64_t p = std::min(m, n);
     const bool tc = prec != CPA_FP32;
     // Gram and final product: always split.  Recurrence: split in BF16X3
@@ -483,7 +494,7 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
         // the bound's launch also forms the coefficients (FP64) in its last block
         StageScope sc(h, CPA_STAGE_BOUND, st, 1);
         CK(power_bound_persistent(w.G, w.ldp, (int)p, iters, w.v0, w.v1, w.norm2, (unsigned int *)w.flag,
-                                  w.flag + 1, w.out, st, h->num_sms, L, &sp_, w.coef));
+                                  w.flag + 1, w.out, st, h->num_sms, L, &sp_, w.coef, h->wait));
     }
     // coefficients (FP64, on the device so the call stays asynchronous)
     if (lambda_max > 0.0) {
@@ -519,10 +530,11 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
         e.coef = w.coef;
         e.ldb = w.ldk;
         e.symmetric_upper = 1;
+        e.err = w.flag + 5;
         TcOperand a;
         a.hi = w.Ahi; a.lo = w.Alo; a.ld = w.ldk; a.rows = (int)p;
         CK(gemm_tc_recurrence((int)p, a, nsplit_rec, e, 2, L, w.Z, w.Zhi, w.Zlo, (unsigned int *)(w.flag + 2), st,
-                              h->num_sms, clenshaw, L, &closed, (int)w.ldk));
+                              h->num_sms, clenshaw, L, &closed, (int)w.ldk, h->wait));
     }
     for (int k = 2; k < L && !tc; ++k) {
         StageScope sc(h, CPA_STAGE_RECUR, st, 1);
@@ -560,6 +572,7 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
             e.Dhi = w.Zhi[cur];
             e.Dlo = w.Zlo[cur];
             e.ldb = w.ldk;
+            e.err = w.flag + 5;
             TcOperand a, b;
             a.hi = w.Ahi; a.lo = w.Alo; a.ld = w.ldk; a.rows = (int)p;
             b.hi = w.Zhi[prev]; b.lo = w.Zlo[prev]; b.ld = w.ldk; b.rows = (int)p;
@@ -594,6 +607,7 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
     Epilogue e;
     e.D = dY;
     e.ldd = ldy;
+    e.err = w.flag + 5;
     if (!tc) {
         if (m >= n)
             CK(gemm_f32((int)m, (int)n, (int)n, dX, ldx, true, Hf, w.ldp, true, e, st));
@@ -624,17 +638,39 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
     return CPA_OK;
 }
 
+// Reads {theta, r, trace, lambda, status} of the last cpa_svt and its
+// tensor-core error word into the handle's pinned slots (synchronises).
+static cpa_status read_last(cpa_ctx *h, cudaStream_t st) {
+    CK(cudaMemcpyAsync(h->h_pin, h->d_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h->h_pin + 5, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return CPA_OK;
+}
+
+static cpa_status last_status(const cpa_ctx *h) {
+    int err = 0;
+    memcpy(&err, h->h_pin + 5, sizeof(int));
+    if (err != 0) return (cpa_status)err;
+    if (h->h_pin[4] != 0.0) return (cpa_status)(int)h->h_pin[4];
+    if (!(h->h_pin[3] > 0.0)) return CPA_ERR_BOUND;
+    return CPA_OK;
+}
+
 cpa_status cpa_get_lambda(cpa_handle h, double *lambda_out, void *stream) {
     if (!h || !lambda_out || !h->have_last) return CPA_ERR_INVALID_ARG;
     cpa_status s = set_device(h);
     if (s != CPA_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    CK(cudaMemcpyAsync(h->h_pin, h->d_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    if ((s = read_last(h, (cudaStream_t)stream)) != CPA_OK) return s;
     *lambda_out = h->h_pin[3];
-    if (h->h_pin[4] != 0.0) return (cpa_status)(int)h->h_pin[4];
-    if (!(h->h_pin[3] > 0.0)) return CPA_ERR_BOUND;
-    return CPA_OK;
+    return last_status(h);
+}
+
+cpa_status cpa_sync_status(cpa_handle h, void *stream) {
+    if (!h || !h->have_last) return CPA_ERR_INVALID_ARG;
+    cpa_status s = set_device(h);
+    if (s != CPA_OK) return s;
+    if ((s = read_last(h, (cudaStream_t)stream)) != CPA_OK) return s;
+    return last_status(h);
 }
 
 cpa_status cpa_get_coeffs(cpa_handle h, double *c_out, int L, void *stream) {
@@ -656,6 +692,16 @@ cpa_status cpa_set_option(cpa_handle h, int option, int value) {
     if (option == CPA_OPT_SERIES) {
         if (value != CPA_SERIES_FORWARD && value != CPA_SERIES_CLENSHAW) return CPA_ERR_INVALID_ARG;
         h->series = value;
+        return CPA_OK;
+    }
+    if (option == CPA_OPT_WAIT_KCYCLES) {
+        if (value < 0) return CPA_ERR_INVALID_ARG;
+        h->wait.wait_cycles = (long long)value * 1000LL;
+        return CPA_OK;
+    }
+    if (option == CPA_OPT_STALL_TEST) {
+        if (value != 0 && value != 1) return CPA_ERR_INVALID_ARG;
+        h->wait.stall = value;
         return CPA_OK;
     }
     return CPA_ERR_INVALID_ARG;

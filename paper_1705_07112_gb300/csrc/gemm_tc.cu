@@ -229,6 +229,11 @@ struct MultiStep {
     // last step also applies the closing H = (b_0 - b_2) / 2).  The FP32
     // ring arrays are then not written during the launch.
     int resident = 0;
+    // grid-barrier wait limit in clock cycles; stall: the first barrier
+    // expects one arrival more than the grid makes (tests of the timeout
+    // path: it then ends only by the limit, every CTA stops after its step)
+    long long wait_cycles = kDefaultWaitCycles;
+    int stall = 0;
 };
 
 __device__ __forceinline__ void fence_proxy_async_global() {
@@ -938,14 +943,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 __threadfence();
                 asm volatile("bar.sync 1, 128;" ::: "memory");
                 if (threadIdx.x == 64) {
-                    target += gridDim.x;
+                    target += gridDim.x + ((ms.stall && k == ms.k_first) ? 1u : 0u);
                     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ms.bar) : "memory");
                     const long long t0 = clock64();
                     while (true) {
                         unsigned int v;
                         asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ms.bar) : "memory");
                         if (v >= target) break;
-                        if (clock64() - t0 > kWaitCycles) {
+                        if (clock64() - t0 > ms.wait_cycles) {
                             *abort_flag = 1;
                             break;
                         }
@@ -1029,18 +1034,43 @@ bool make_block_map(CUtensorMap *map, const void *ptr, CUtensorMapDataType type,
     return r == CUDA_SUCCESS;
 }
 
-int *g_err_dev = nullptr;
+// Fallback error word of each device, for calls that pass none (one word
+// per device: a kernel must never be handed another GPU's memory).
+constexpr int kMaxDevices = 64;
+int *g_err_dev[kMaxDevices] = {};
+std::mutex g_err_mu;
+
+cudaError_t device_err_word(int **out) {
+    int dev = 0;
+    cudaError_t r = cudaGetDevice(&dev);
+    if (r != cudaSuccess) return r;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_err_mu);
+    if (!g_err_dev[dev]) {
+        int *p = nullptr;
+        r = cudaMalloc(&p, sizeof(int));
+        if (r != cudaSuccess) return r;
+        r = cudaMemset(p, 0, sizeof(int));
+        if (r != cudaSuccess) {
+            cudaFree(p);
+            return r;
+        }
+        g_err_dev[dev] = p;
+    }
+    *out = g_err_dev[dev];
+    return cudaSuccess;
+}
 
 template <int BN>
 cudaError_t launch(int M, int N, int K, const TcOperand &A, const TcOperand &B, int nsplit, const Epilogue &e,
                    const MultiStep &ms, cudaStream_t st, int num_sms) {
     using S = Smem<BN>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t r = cudaFuncSetAttribute(gemm_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             S::kBytes);
-        if (r != cudaSuccess) return r;
-        attr_set = true;
+    cudaError_t ra = ensure_smem_limit((const void *)gemm_tc_kernel<BN>, S::kBytes);
+    if (ra != cudaSuccess) return ra;
+    int *err = e.err;
+    if (!err) {
+        ra = device_err_word(&err);
+        if (ra != cudaSuccess) return ra;
     }
     TileMaps maps;
     memset(&maps, 0, sizeof(maps));
@@ -1076,7 +1106,7 @@ cudaError_t launch(int M, int N, int K, const TcOperand &A, const TcOperand &B, 
     const int tiles = count_tiles((M + BM - 1) / BM, (N + BN - 1) / BN, e.symmetric_upper, BN);
     const int grid = tiles < num_sms ? tiles : num_sms;
     if (!ms.multi) {
-        gemm_tc_kernel<BN><<<grid, kThreads, S::kBytes, st>>>(maps, M, N, K, nsplit, g, e, ms, g_err_dev);
+        gemm_tc_kernel<BN><<<grid, kThreads, S::kBytes, st>>>(maps, M, N, K, nsplit, g, e, ms, err);
         return cudaGetLastError();
     }
     cudaError_t r = cudaMemsetAsync(ms.bar, 0, sizeof(unsigned int), st);
@@ -1091,7 +1121,7 @@ cudaError_t launch(int M, int N, int K, const TcOperand &A, const TcOperand &B, 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<BN>, maps, M, N, K, nsplit, g, e, ms, g_err_dev);
+    return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<BN>, maps, M, N, K, nsplit, g, e, ms, err);
 }
 
 template <int BN>
@@ -1102,17 +1132,6 @@ cudaError_t launch(int M, int N, int K, const TcOperand &A, const TcOperand &B, 
 }
 
 }  // namespace
-
-cudaError_t gemm_tc_error_flag(int **flag) {
-    if (!g_err_dev) {
-        cudaError_t r = cudaMalloc(&g_err_dev, sizeof(int));
-        if (r != cudaSuccess) return r;
-        r = cudaMemset(g_err_dev, 0, sizeof(int));
-        if (r != cudaSuccess) return r;
-    }
-    *flag = g_err_dev;
-    return cudaSuccess;
-}
 
 // Tile width by a small cost model: waves of CTAs times the tile's cost,
 // which grows with BN plus a fixed per-tile overhead of about 64 columns.
@@ -1147,7 +1166,7 @@ cudaError_t dispatch_bn(int bn, F f) {
 cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epilogue &e, int k_first, int k_end,
                                float *const z[2], __nv_bfloat16 *const zhi[2], __nv_bfloat16 *const zlo[2],
                                unsigned int *bar, cudaStream_t st, int num_sms, int clenshaw, int L, int *closed,
-                               int kpad) {
+                               int kpad, const WaitPolicy &wp) {
     if (closed) *closed = 0;
     if (p <= 0 || k_end <= k_first) return cudaSuccess;
     if (!load_encode()) return cudaErrorNotSupported;
@@ -1157,11 +1176,10 @@ cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epil
     for (int i = 0; i < 2; ++i)
         if (((uintptr_t)z[i] % 16) || ((uintptr_t)zhi[i] % 16) || (zlo[i] && ((uintptr_t)zlo[i] % 16)))
             return cudaErrorInvalidValue;
-    int *flag;
-    cudaError_t r = gemm_tc_error_flag(&flag);
-    if (r != cudaSuccess) return r;
     MultiStep ms;
     ms.multi = 1;
+    ms.wait_cycles = wait_limit(wp);
+    ms.stall = wp.stall;
     ms.k_first = k_first;
     ms.k_end = k_end;
     for (int i = 0; i < 2; ++i) {
@@ -1211,9 +1229,6 @@ cudaError_t gemm_tc(int M, int N, int K, const TcOperand &A, const TcOperand &B,
     } else if (e.C || e.C2 || e.H || e.Dhi || e.Dlo) {
         return cudaErrorInvalidValue;   // general outputs carry only D
     }
-    int *flag;
-    cudaError_t r = gemm_tc_error_flag(&flag);
-    if (r != cudaSuccess) return r;
     return dispatch_bn(choose_bn(M, N, e.symmetric_upper, num_sms), [&](auto bn) {
         return launch<decltype(bn)::value>(M, N, K, A, B, nsplit, e, st, num_sms);
     });

@@ -80,7 +80,30 @@ struct Epilogue {
     // diagonal term read on the device: diag + dcoef[dk] - (dk2 >= 0 ? dcoef[dk2] : 0)
     const double *dcoef = nullptr;
     int dk = 0, dk2 = -1;
+    // device word that receives CPA_ERR_TIMEOUT when a bounded wait of the
+    // tensor-core kernel gives up (null: a word of the current device)
+    int *err = nullptr;
 };
+
+// Bounded waits of the cooperative launches (the power iteration's and the
+// recurrence's grid barriers).  wait_cycles: clock cycles a block waits at a
+// grid barrier before it records CPA_ERR_TIMEOUT (0: the default, about 2 s
+// at 2 GHz).  stall != 0: the first grid barrier waits for one arrival more
+// than the grid makes, so it can only end by that limit (for tests of the
+// timeout path; the waits inside a CTA keep their own fixed limit).
+struct WaitPolicy {
+    long long wait_cycles = 0;
+    int stall = 0;
+};
+constexpr long long kDefaultWaitCycles = 4000000000LL;
+__host__ __device__ inline long long wait_limit(const WaitPolicy &w) {
+    return w.wait_cycles > 0 ? w.wait_cycles : kDefaultWaitCycles;
+}
+
+// Raises the dynamic shared-memory limit of `func` to `bytes` on the current
+// device.  The attribute belongs to the device, so it is set once per
+// (device, kernel, size) under a lock, not once per process.
+cudaError_t ensure_smem_limit(const void *func, int bytes);
 
 // The diagonal term of an epilogue (host value plus the device coefficients).
 __device__ __forceinline__ float epilogue_diag(const Epilogue &e) {
@@ -119,7 +142,7 @@ cudaError_t gemm_tc(int M, int N, int K, const TcOperand &A, const TcOperand &B,
 cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epilogue &e, int k_first, int k_end,
                                float *const z[2], __nv_bfloat16 *const zhi[2], __nv_bfloat16 *const zlo[2],
                                unsigned int *bar, cudaStream_t st, int num_sms, int clenshaw = 0, int L = 0,
-                               int *closed = nullptr, int kpad = 0);
+                               int *closed = nullptr, int kpad = 0, const WaitPolicy &wp = WaitPolicy());
 
 // Sparsity-based reduction helpers (sparsify.cu).
 cudaError_t make_transform(int type, int p, float *T, int64_t ld, cudaStream_t st, int num_sms);
@@ -149,7 +172,7 @@ cudaError_t power_bound(const float *G, int64_t ldg, int p, int iters, float *v0
 cudaError_t power_bound_persistent(const float *G, int64_t ldg, int p, int iters, float *v0, float *v1,
                                    double *norm2, unsigned int *bar, int *err, double *out, cudaStream_t st,
                                    int num_sms, int L = 0, const ShrinkParams *sp = nullptr,
-                                   double *coef = nullptr);
+                                   double *coef = nullptr, const WaitPolicy &wp = WaitPolicy());
 cudaError_t device_coeffs(const double *lam_dev, double lam_host, int L, const ShrinkParams &s, double *c,
                           cudaStream_t st);
 // A = (2/lambda) G - Id, Z1 = A, H = c0/2 Id + c1 A (FP32).  For the

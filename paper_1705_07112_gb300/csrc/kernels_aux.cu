@@ -3,10 +3,38 @@
 // B_hat = (2/Lambda_max) G - Id with the initial sum, and FP32 -> BF16 hi/lo
 // splitting of tensor-core operands.
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "internal.h"
 
 namespace cpa {
+
+cudaError_t ensure_smem_limit(const void *func, int bytes) {
+    struct Entry {
+        int dev;
+        const void *func;
+        int bytes;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> done;
+    int dev = 0;
+    cudaError_t r = cudaGetDevice(&dev);
+    if (r != cudaSuccess) return r;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Entry &e : done)
+        if (e.dev == dev && e.func == func && e.bytes >= bytes) return cudaSuccess;
+    r = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (r != cudaSuccess) return r;
+    for (Entry &e : done)
+        if (e.dev == dev && e.func == func) {
+            e.bytes = bytes;
+            return cudaSuccess;
+        }
+    done.push_back(Entry{dev, func, bytes});
+    return cudaSuccess;
+}
+
 namespace {
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -285,12 +313,15 @@ __global__ void check_finite_kernel(const float *X, int64_t rows, int64_t cols, 
 
 // Software grid barrier for a cooperative launch: a monotone arrival
 // counter (zeroed before the launch); each block's thread 0 adds one and
-// waits for the count of the current round.  The wait is bounded (~2 s);
-// on expiry it records CPA_ERR_TIMEOUT in *err and lets the block go on.
-__device__ __forceinline__ void grid_barrier(unsigned int *count, unsigned int &target, int *err) {
+// waits for the count of the current round.  The wait is bounded (`limit`
+// clock cycles); on expiry it records CPA_ERR_TIMEOUT in *err and lets the
+// block go on.  extra: arrivals expected beyond the grid's own (a stalled
+// barrier for tests of the timeout path).
+__device__ __forceinline__ void grid_barrier(unsigned int *count, unsigned int &target, int *err, long long limit,
+                                             unsigned int extra = 0) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        target += gridDim.x;
+        target += gridDim.x + extra;
         // release: this block's prior writes (made visible to the thread by
         // the CTA barrier) are ordered before the arrival
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
@@ -299,7 +330,7 @@ __device__ __forceinline__ void grid_barrier(unsigned int *count, unsigned int &
             unsigned int v;
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
             if (v >= target) break;
-            if (clock64() - t0 > 4000000000LL) {
+            if (clock64() - t0 > limit) {
                 atomicExch(err, (int)CPA_ERR_TIMEOUT);
                 break;
             }
@@ -321,7 +352,8 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
                                                                int iters, uint64_t seed, float *v0, float *v1,
                                                                double *norm2, unsigned int *bar, double margin,
                                                                double *out, int *err, int cache, int stage,
-                                                               int L, ShrinkParams sp, double *coef) {
+                                                               int L, ShrinkParams sp, double *coef,
+                                                               long long wait_cycles, int stall) {
     extern __shared__ __align__(16) float grow[];
     __shared__ float wpart[16];    // per-warp |w|^2 partials
     __shared__ float sscale;       // 1 / |v| of the current iterate
@@ -353,7 +385,7 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
         const float *g = G + (int64_t)gwarp * ldg;
         for (int j = lane; j < p4; j += 32) myrow[j] = j < p ? __ldg(g + j) : 0.f;
     }
-    grid_barrier(bar, target, err);
+    grid_barrier(bar, target, err, wait_cycles, stall ? 1u : 0u);
     const bool vec = (ldg & 3) == 0 && (p & 3) == 0 && ((uintptr_t)G & 15) == 0;
     for (int t = 0; t <= iters; ++t) {
         const float *v = (t & 1) ? v1 : v0;
@@ -433,7 +465,7 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
             q = warp_sumf(q);
             if (threadIdx.x == 0 && q != 0.f) atomicAdd(&norm2[t + 1], (double)q);
         }
-        grid_barrier(bar, target, err);
+        grid_barrier(bar, target, err, wait_cycles);
     }
     // after iters+1 products: v = buffer of step iters (unnormalised, norm2[iters]),
     // w = G v / |v| in the other buffer
@@ -510,7 +542,7 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
 
 cudaError_t power_bound_persistent(const float *G, int64_t ldg, int p, int iters, float *v0, float *v1,
                                    double *norm2, unsigned int *bar, int *err, double *out, cudaStream_t st,
-                                   int num_sms, int L, const ShrinkParams *sp, double *coef) {
+                                   int num_sms, int L, const ShrinkParams *sp, double *coef, const WaitPolicy &wp) {
     cudaError_t r = cudaMemsetAsync(bar, 0, sizeof(unsigned int), st);
     if (r != cudaSuccess) return r;
     r = cudaMemsetAsync(err, 0, sizeof(int), st);
@@ -530,13 +562,8 @@ cudaError_t power_bound_persistent(const float *G, int64_t ldg, int p, int iters
     if (coef && (L < 1 || L > kMaxTerms || !sp)) return cudaErrorInvalidValue;
     if (coef && smem < (size_t)5 * L * sizeof(double)) smem = (size_t)5 * L * sizeof(double);
     if (smem > 48 * 1024) {
-        static bool attr = false;
-        if (!attr) {
-            cudaError_t ra = cudaFuncSetAttribute(power_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)budget);
-            if (ra != cudaSuccess) return ra;
-            attr = true;
-        }
+        cudaError_t ra = ensure_smem_limit((const void *)power_persistent_kernel, (int)budget);
+        if (ra != cudaSuccess) return ra;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -552,7 +579,7 @@ cudaError_t power_bound_persistent(const float *G, int64_t ldg, int p, int iters
     const uint64_t seed = kStartSeed;
     const ShrinkParams spv = sp ? *sp : ShrinkParams{};
     return cudaLaunchKernelEx(&cfg, power_persistent_kernel, G, ldg, p, iters, seed, v0, v1, norm2, bar, margin, out,
-                              err, cache, stage, coef ? L : 0, spv, coef);
+                              err, cache, stage, coef ? L : 0, spv, coef, wait_limit(wp), wp.stall);
 }
 
 cudaError_t power_bound(const float *G, int64_t ldg, int p, int iters, float *v0, float *v1,
@@ -577,13 +604,8 @@ cudaError_t power_bound(const float *G, int64_t ldg, int p, int iters, float *v0
 cudaError_t device_coeffs(const double *lam_dev, double lam_host, int L, const ShrinkParams &s, double *c,
                           cudaStream_t st) {
     const size_t smem = (size_t)5 * L * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t r = cudaFuncSetAttribute(coeffs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             5 * kMaxTerms * (int)sizeof(double));
-        if (r != cudaSuccess) return r;
-        attr = true;
-    }
+    cudaError_t r = ensure_smem_limit((const void *)coeffs_kernel, 5 * kMaxTerms * (int)sizeof(double));
+    if (r != cudaSuccess) return r;
     coeffs_kernel<<<1, 1024, smem, st>>>(lam_dev, lam_host, L, s, c);
     return cudaGetLastError();
 }

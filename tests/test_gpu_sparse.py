@@ -133,3 +133,66 @@ def test_sparsify_argument_errors(cpa, handle):
     for bad in [(5, 0, 0.0), (0, 3, 0.0), (0, 1, -1.0), (0, 2, 0.0), (0, 2, 1.5)]:
         with pytest.raises(cpa.CpaError):
             cpa.cpa_svt(handle, X, {"kind": O.SOFT, "tau": 1.0}, 5, 10.0, "fp32", sparsify=bad)
+
+
+_PHI_CACHE = {}
+
+
+def _big_case(tkind):
+    """The smooth 1100 x 1024 matrix (p = 1024: the multi-block top-k search
+    and the large-size transforms run) and the oracle's Phi for transform
+    tkind, computed once per transform."""
+    if tkind not in _PHI_CACHE:
+        rng = np.random.default_rng(4242 + tkind)
+        X = smooth_matrix(rng, 1100, 1024)
+        if tkind == 0:
+            X[:550, 512:] = 0.0
+            X[550:, :512] = 0.0
+        T = transform(tkind, 1024)
+        _PHI_CACHE[tkind] = (X, T, O.phi(X, T if tkind else None))
+    return _PHI_CACHE[tkind]
+
+
+def wide_gap(Phi, lo_frac=0.0005, hi_frac=0.5):
+    """eps in the widest multiplicative gap of |Phi| within a rank window
+    (vectorised form of gap_threshold for large p)."""
+    a = np.sort(np.abs(Phi).ravel())[::-1]
+    lo, hi = max(1, int(lo_frac * a.size)), int(hi_frac * a.size)
+    seg = a[lo - 1:hi]
+    pos = seg[1:] > 0
+    if not np.all(pos):   # exact zeros (block-structured Phi): keep every nonzero
+        k = lo + int(np.argmin(pos))
+        return 0.5 * a[k - 1], k, math.inf
+    r = seg[:-1] / seg[1:]
+    j = int(np.argmax(r))
+    k = lo + j
+    return math.sqrt(a[k - 1] * a[k]), k, float(r[j])
+
+
+@pytest.mark.parametrize("tkind", [0, 1, 2, 3])
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_sparsify_full_size_sampled(cpa, handle, tkind, mode, prec):
+    """p = 1024 with every transform and both threshold modes: sampled rows
+    of X T^T H_hat(Phi_) T against the oracle (Phi from the C oracle, the
+    series on the sampled rows by the oracle's block vector form)."""
+    import torch
+    X, T, Phi = _big_case(tkind)
+    p = 1024
+    eps, k, ratio = wide_gap(Phi)
+    assert ratio > 1.02
+    arg = eps if mode == 1 else (k - 0.5) / (p * p)
+    Phib = np.where(np.abs(Phi) >= eps, Phi, 0.0)
+    lam = 1.05 * np.max(np.abs(np.linalg.eigvalsh(Phib)))
+    s = O.Shrink(O.SOFT, 0.1 * math.sqrt(lam))
+    L = 15
+    rows = [0, 1, 550, 1098, 1099]
+    want = (T.T @ O.filter_block(Phib, s, L, lam, T @ X[rows].T)).T
+    Xd = torch.from_numpy(X.astype(np.float32)).cuda()
+    Y = cpa.cpa_svt(handle, Xd, {"kind": O.SOFT, "tau": s.tau}, L, lam, prec, sparsify=(tkind, mode, arg))
+    torch.cuda.synchronize()
+    got = Y.cpu().numpy().astype(np.float64)
+    scale = np.linalg.norm(got) / np.sqrt(len(got))
+    for j, i in enumerate(rows):
+        err = np.linalg.norm(got[i] - want[j]) / max(np.linalg.norm(want[j]), scale)
+        assert err <= TOL[prec], (tkind, mode, prec, i, err, k)

@@ -196,14 +196,63 @@ def test_rpca_frame_full_size_sampled(cpa, handle, prec):
     sampled_rows_check(cpa, handle, w.X, s, w.L, prec, [0, 1, 511, 1022, 1023], TOL[prec])
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
-def test_video_background_full_size_sampled(cpa, handle, prec):
+@pytest.fixture(scope="module")
+def video_background():
+    """The 4096 x 8192 video-background matrix, its oracle bound and, per
+    kind, the oracle's columns of H_hat(X X^T) X at 16 spread columns."""
     w = inputs.video_background()
-    s = O.Shrink(O.SOFT, w.shrink.tau)
-    sampled_rows_check(cpa, handle, w.X, s, w.L, prec, [0, 8191], TOL[prec])
+    X64 = w.X.astype(np.float64)
+    lam = oracle_lambda(X64)
+    cols = np.linspace(0, X64.shape[1] - 1, 16).astype(int)
+    want = {}
+    for kind in (O.SOFT, O.HARD):
+        s = O.Shrink(kind, w.shrink.tau)
+        want[kind] = O.cpa_block(X64, s, w.L, lam, X64[:, cols])
+    return w, lam, cols, want
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
+@pytest.mark.parametrize("kind", [O.SOFT, O.HARD])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "bf16x3"])
+def test_video_background_full_size_sampled(cpa, handle, video_background, kind, prec):
+    """The large configuration at full size (4096 x 8192, L = 50), hard and
+    soft thresholding at tau = 30.7, every precision: 16 columns spread over
+    the matrix against the oracle's block vector form."""
+    w, lam, cols, want = video_background
+    s = O.Shrink(kind, w.shrink.tau)
+    Y = run(cpa, handle, w.X, s, w.L, lam, prec)
+    scale = np.linalg.norm(Y) / np.sqrt(Y.shape[1])
+    got = Y[:, cols]
+    for j in range(len(cols)):
+        err = np.linalg.norm(got[:, j] - want[kind][:, j]) / max(np.linalg.norm(want[kind][:, j]), scale)
+        assert err <= TOL[prec], (kind, prec, cols[j], err)
+
+
+def test_svt_host_full_frame_matches_oracle(cpa, handle):
+    """The end-to-end host-buffer path at the size the bench times it (the
+    1024 x 1024 frame, BF16, resident-state recurrence): two host matrices
+    through cpa_svt_host, sampled rows against the oracle's block vector
+    form, with the bound given and with the bound computed on the device."""
+    import torch
+    ws = [inputs.rpca_frame(seed_index=i) for i in range(2)]
+    s = O.Shrink(O.SOFT, ws[0].shrink.tau)
+    rows = [0, 1, 333, 777, 1022, 1023]
+    hx = [torch.from_numpy(w.X).pin_memory() for w in ws]
+    for given in (True, False):
+        lams = [oracle_lambda(w.X.astype(np.float64)) for w in ws]
+        lam_arg = max(lams) if given else 0.0
+        hy = cpa.cpa_svt_host(handle, hx, {"kind": O.SOFT, "tau": s.tau}, ws[0].L, lam_arg, "bf16")
+        torch.cuda.synchronize()
+        for w, lam, Y in zip(ws, lams, hy):
+            X64 = w.X.astype(np.float64)
+            want = O.cpa_block(X64, s, w.L, max(lams) if given else lam, X64[rows].T).T
+            Yn = Y.numpy().astype(np.float64)
+            scale = np.linalg.norm(Yn) / np.sqrt(len(Yn))
+            for k, i in enumerate(rows):
+                err = np.linalg.norm(Yn[i] - want[k]) / max(np.linalg.norm(want[k]), scale)
+                assert err <= TOL["bf16"], (given, i, err)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
 def test_clenshaw_series_matches_oracle(cpa, handle, prec):
     """The series summed by Clenshaw's recurrence (CPA_OPT_SERIES) against
     the oracle's Algorithm 1 at the same L and Lambda_max, across shapes
@@ -232,25 +281,31 @@ def test_clenshaw_series_matches_oracle(cpa, handle, prec):
         _lib.cpa_set_option(handle, 99, 0)
 
 
+def test_clenshaw_with_plain_bf16_is_refused(cpa, handle):
+    """Clenshaw's sum with one BF16 rounding of its operand per step misses
+    the BF16 path's 2e-3 bar (its intermediates grow with the number of
+    remaining terms and the closing difference cancels them): the library
+    refuses that combination instead of returning a result off the bar."""
+    from paper_1705_07112_gb300 import _lib
+    X = to_dev(np.ones((40, 30), dtype=np.float32))
+    _lib.cpa_set_option(handle, _lib.OPT_SERIES, _lib.SERIES_CLENSHAW)
+    try:
+        with pytest.raises(_lib.CpaError) as ei:
+            cpa.cpa_svt(handle, X, {"kind": O.SOFT, "tau": 1.0}, 10, 0.0, "bf16")
+        assert ei.value.status == 7   # CPA_ERR_UNSUPPORTED
+    finally:
+        _lib.cpa_set_option(handle, _lib.OPT_SERIES, _lib.SERIES_FORWARD)
+
+
 # The recurrence launch takes different forms by size: one tile per CTA with
 # the state in tensor memory at BN = 32 (p up to 1024) or BN = 64 (p about
 # 1088 to 1280), several tiles per CTA with the state in global memory at
 # BN = 128 / 256; operand loads grouped two slices per TMA instruction when
 # p is a multiple of 128, one slice otherwise.  Each form against the
-# oracle's vector form on sampled rows, forward and Clenshaw's sum.
-# Clenshaw's sum in plain BF16 misses the 2e-3 bar at these sizes: measured
-# on sampled rows at L = 30, 4.3e-3 to 6.0e-3 for p = 1000 .. 2048 against
-# 0.7e-4 to 1.2e-4 for the forward recurrence (BF16X3: 1.5e-5 against
-# 0.8e-5).  Its intermediates b_k sum second-kind polynomials whose size
-# grows with the number of remaining terms, and H = (b_0 - b_2)/2 cancels
-# them, so the BF16 rounding of the operand b_{k+1} is amplified; the
-# forward recurrence's T_k stay in [-1, 1].  The bar asserted for it is the
-# measured behaviour with margin, 1e-2; the forward recurrence stays the
-# default and the only series quoted at BF16.
-CLENSHAW_BF16_TOL = 1e-2
+# oracle's vector form on sampled rows, forward and Clenshaw's sum (the
+# latter in BF16X3: plain BF16 operands are refused for it).
 @pytest.mark.parametrize("shape", [(1152, 1300), (1400, 1088), (2048, 2100)])
-@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
-@pytest.mark.parametrize("series", ["forward", "clenshaw"])
+@pytest.mark.parametrize("prec,series", [("bf16", "forward"), ("bf16x3", "forward"), ("bf16x3", "clenshaw")])
 def test_recurrence_launch_forms_sampled(cpa, handle, shape, prec, series):
     from paper_1705_07112_gb300 import _lib
     rng = np.random.default_rng(shape[0] + shape[1])
@@ -261,8 +316,7 @@ def test_recurrence_launch_forms_sampled(cpa, handle, shape, prec, series):
     _lib.cpa_set_option(handle, _lib.OPT_SERIES,
                         _lib.SERIES_CLENSHAW if series == "clenshaw" else _lib.SERIES_FORWARD)
     try:
-        tol = CLENSHAW_BF16_TOL if (series == "clenshaw" and prec == "bf16") else TOL[prec]
-        sampled_rows_check(cpa, handle, X, s, 30, prec, [0, 1, p // 2, p - 2, p - 1], tol)
+        sampled_rows_check(cpa, handle, X, s, 30, prec, [0, 1, p // 2, p - 2, p - 1], TOL[prec])
     finally:
         _lib.cpa_set_option(handle, _lib.OPT_SERIES, _lib.SERIES_FORWARD)
 

@@ -305,6 +305,46 @@ def test_lambda_bound_properties():
     assert abs(r1["theta"] - s2) < 1e-9 * s2 and r1["resid"] < 1e-6 * s2
 
 
+def test_lambda_bound_exact_two_eigenvalue_closed_form():
+    """The bound's value, not only its inequalities.  X = Q1 diag(s) Q2^T
+    with two nonzero singular values and a start vector a q1 + b q2 in the
+    span of their right singular vectors q1, q2: after t normalised
+    products v = (alpha, beta) in that basis with alpha : beta =
+    a mu1^t : b mu2^t (mu = s^2), so theta = alpha^2 mu1 + beta^2 mu2 and
+    G v - theta v = (mu1 - mu2) alpha beta (beta, -alpha), whose norm is
+    r = |mu1 - mu2| |alpha beta|.  The bound is min((theta + r) (1 +
+    margin), mu1 + mu2).  A dropped residual, a dropped or doubled margin,
+    an off-by-one iteration count or a wrong clamp each miss by far more
+    than the 1e-12 asserted."""
+    rng = np.random.default_rng(31)
+    m, n = 9, 6
+    Q1, Q2 = rand_orth(rng, m), rand_orth(rng, n)
+    for (s1, s2, a, b, t, margin) in [(3.0, 2.0, 0.3, 0.9, 0, 0.01), (3.0, 2.0, 0.3, 0.9, 1, 0.01),
+                                      (3.0, 2.0, 0.3, 0.9, 4, 0.01), (5.0, 4.5, -0.7, 0.2, 2, 0.01),
+                                      (2.0, 1.0, 1.0, 1.0, 3, 0.05), (1.5, 1.4, 0.01, 1.0, 1, 0.0)]:
+        S = np.zeros((m, n))
+        S[0, 0], S[1, 1] = s1, s2
+        X = Q1 @ S @ Q2.T
+        v0 = a * Q2[:, 0] + b * Q2[:, 1]
+        mu1, mu2 = s1 * s1, s2 * s2
+        al, be = a * mu1 ** t, b * mu2 ** t
+        nrm = np.hypot(al, be)
+        al, be = al / nrm, be / nrm
+        theta = al * al * mu1 + be * be * mu2
+        r = abs(mu1 - mu2) * abs(al * be)
+        want = min((theta + r) * (1.0 + margin), mu1 + mu2)
+        got = O.lambda_bound(X, t, margin, v0)
+        assert abs(got["theta"] - theta) <= 1e-12 * mu1, (t, got, theta)
+        assert abs(got["resid"] - r) <= 1e-12 * mu1, (t, got, r)
+        assert abs(got["trace"] - (mu1 + mu2)) <= 1e-12 * mu1
+        assert abs(got["lam"] - want) <= 1e-12 * mu1, (t, got["lam"], want)
+    # the trace clamp: a rank-one X gives theta = mu, r = 0, and (1 + margin)
+    # mu exceeds the trace mu, so the bound is the trace itself
+    X1 = np.outer(Q1[:, 0], Q2[:, 0]) * 2.5
+    got = O.lambda_bound(X1, 2, 0.01, Q2[:, 0] + 0.5 * Q2[:, 3])
+    assert abs(got["lam"] - 6.25) <= 1e-12 * 6.25 and abs(got["theta"] - 6.25) <= 1e-12 * 6.25
+
+
 def test_start_vector_is_splitmix64():
     # SplitMix64 reference outputs for seed 0 (the published generator's
     # first outputs), top 53 bits scaled to [0,1) minus 1/2.
@@ -408,3 +448,37 @@ def test_clenshaw_sum_equals_the_forward_recurrence():
         ck = O.coeffs(s, 12, 9.0)
         y = O.cpa_clenshaw(np.array([[x]]), s, 12, 9.0)[0, 0]
         assert abs(y - x * O.series_cos(ck, 2 * x * x / 9.0 - 1)) < 1e-13
+
+
+def test_block_vector_form_matches_the_c_oracle():
+    """cpa_block (numpy matmul as the product) against the C oracle's
+    one-vector form and dense Algorithm 1, both orientations, all kinds;
+    filter_block on an explicit thresholded Phi against the dense
+    Algorithm 1 with the same transform and entry threshold."""
+    rng = np.random.default_rng(19)
+    for (m, n) in [(23, 11), (11, 23), (9, 9)]:
+        X = rng.standard_normal((m, n))
+        p = min(m, n)
+        lam = 1.02 * np.linalg.norm(X, 2) ** 2
+        for s in (O.Shrink(O.SOFT, 1.1), O.Shrink(O.HARD, 1.3), O.Shrink(O.WSOFT, 0.0, 2.0, 1e-8, 0.5)):
+            for alpha in (1, 2, 3, 14):
+                V = rng.standard_normal((p, 4))
+                B = O.cpa_block(X, s, alpha, lam, V)
+                for j in range(4):
+                    want = O.cpa_vec(X, s, alpha, lam, V[:, j])
+                    assert np.allclose(B[:, j], want, rtol=0, atol=1e-12 * max(1.0, np.abs(want).max()))
+                Y = O.cpa(X, s, alpha, lam)
+                # rows (m >= n) or columns (m < n) of X H or H X
+                Yb = O.cpa_block(X, s, alpha, lam, X.T if m >= n else X)
+                assert np.allclose(Yb.T if m >= n else Yb, Y, rtol=0, atol=1e-11 * np.abs(Y).max())
+    X = rng.standard_normal((20, 12))
+    T = rand_orth(rng, 12)
+    Phi = O.phi(X, T)
+    eps = np.sort(np.abs(Phi).ravel())[-40]
+    Phib = np.where(np.abs(Phi) >= eps, Phi, 0.0)
+    lam = 1.05 * np.max(np.abs(np.linalg.eigvalsh(Phib)))
+    s = O.Shrink(O.SOFT, 0.3 * np.sqrt(lam))
+    Y = O.cpa(X, s, 11, lam, T=T, eps_thr=eps)
+    # X T^T H(Phi_) T, row i = (T^T H T x_i)^T
+    Yb = (T.T @ O.filter_block(Phib, s, 11, lam, T @ X.T)).T
+    assert np.allclose(Yb, Y, rtol=0, atol=1e-11 * np.abs(Y).max())
