@@ -325,7 +325,7 @@ def run_gpu_batched(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        cpa.cpa_svt_batched(h, plan, X, shr, prec=args.prec, Y=Y, stream=stream)
+        cpa.cpa_svt_batched_plan(h, plan, X, shr, prec=args.prec, Y=Y, stream=stream)
 
     for _ in range(args.warmup):
         step()
@@ -334,7 +334,7 @@ def run_gpu_batched(args, world, rank, local):
     if not args.no_graph:
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            cpa.cpa_svt_batched(h, plan, X, shr, prec=args.prec, Y=Y, stream=torch.cuda.current_stream(dev))
+            cpa.cpa_svt_batched_plan(h, plan, X, shr, prec=args.prec, Y=Y, stream=torch.cuda.current_stream(dev))
         for _ in range(3):
             g.replay()
         torch.cuda.synchronize()

@@ -345,7 +345,7 @@ CPA_API cpa_status cpa_mlp_train_step(cpa_mlp m, const float *dX, const float *d
  * A plan uploads the descriptor table once (shapes, offsets, per-matrix L);
  * the same plan can be run many times on new data, and a run can be captured
  * in a CUDA graph.  Supported shapes: 1 <= min(m,n) <= 64, max(m,n) <= 128,
- * 1 <= L <= 128 (patch groups; larger matrices go through cpa_svt).
+ * 1 <= L <= 1024 (patch groups; larger matrices go through cpa_svt).
  * ------------------------------------------------------------------------- */
 typedef struct cpa_batch_ctx *cpa_batch;
 
@@ -367,7 +367,7 @@ CPA_API cpa_status cpa_batch_destroy(cpa_batch b);
  * run of a plan and whenever they change: such a run synchronises `stream`
  * first and cannot be captured in a CUDA graph; runs with unchanged
  * parameters only launch the kernel (capturable). */
-CPA_API cpa_status cpa_svt_batched(cpa_handle h, cpa_batch b, const float *dX, const cpa_shrink *s,
+CPA_API cpa_status cpa_svt_batched_plan(cpa_handle h, cpa_batch b, const float *dX, const cpa_shrink *s,
                            int s_count, const double *lambda, int iters, int prec, float *dY,
                            void *stream);
 
@@ -401,12 +401,14 @@ CPA_API cpa_status cpa_batch_read_lambdas(cpa_batch b, double *host_out, void *s
  *   L = ceil(exp(y1) L_scale), at least L_min; L_fallback above L_max;
  *   Lambda_max = the 20-step power-iteration bound of cpa_lambda_bound, or,
  *     with use_lambda != 0, the prediction theta_4 exp(max(y0, 0))
- *     (1 + margin) (a prediction below sigma_max^2 makes the series
- *     diverge: opt in only with a network whose errors are known to be
- *     small); a non-finite prediction falls back to the bound and
- *     L_fallback.
- * L_scale > 0, margin >= 0, 1 <= L_min <= L_max <= 128, 1 <= L_fallback <=
- * 128, else CPA_ERR_INVALID_ARG.  cpa_batch_read_choices returns the L used
+ *     (1 + margin), never below the residual-corrected estimate
+ *     (theta_4 + r_4)(1 + margin) (a bound below sigma_max^2 makes the
+ *     series grow outside [-1, 1]; clamped predictions count as
+ *     fallbacks).  With use_lambda only the features' four power products
+ *     run, and a non-finite prediction falls back to the bound of those
+ *     products, min((theta_5 + r_5)(1 + 0.01), trace G), with L_fallback.
+ * L_scale > 0, margin >= 0, 1 <= L_min <= L_max <= 1024, 1 <= L_fallback <=
+ * 1024, else CPA_ERR_INVALID_ARG.  cpa_batch_read_choices returns the L used
  * per matrix and the number of fallbacks of the last learned run. */
 CPA_API cpa_status cpa_batch_features(cpa_handle h, cpa_batch b, const float *dX, const cpa_shrink *s, int s_count,
                                       float *dF, double *dTheta, void *stream);
@@ -415,6 +417,71 @@ CPA_API cpa_status cpa_svt_batched_learned(cpa_handle h, cpa_batch b, cpa_mlp ne
                                            int L_fallback, int use_lambda, double margin, int prec, float *dY,
                                            void *stream);
 CPA_API cpa_status cpa_batch_read_choices(cpa_batch b, int *host_L, int *host_fallbacks, void *stream);
+
+/* The same learned choice for one matrix of any size (no counterpart in the
+ * paper), inside the single-matrix shrinkage: cpa_svt with (Lambda_max, L)
+ * chosen on the device.  The features are those of cpa_batch_features
+ * computed from the Gram matrix of the call (FP32, power steps from the
+ * same start vectors, |G|_F^2 and the trace summed in FP64); the network,
+ * its output clamps and the decision rule are those of
+ * cpa_svt_batched_learned with the rule's fields, L_fallback <= L_max <=
+ * 4096.  Without use_lambda the 20-step bound of cpa_lambda_bound is used.
+ * The coefficients of the chosen L are formed on the device in FP64 and the
+ * recurrence reads L from device memory, so the call is asynchronous on
+ * `stream` for CPA_BF16 / CPA_BF16X3 (CPA_FP32 synchronises once to read L).
+ * The forward series only (CPA_ERR_UNSUPPORTED under CPA_SERIES_CLENSHAW).
+ * cpa_get_order returns the L and the fallback flag (1 when the predicted
+ * order exceeded L_max or the predicted bound was clamped or non-finite)
+ * of the last learned call; cpa_get_lambda its Lambda_max. */
+typedef struct {
+    double L_scale;   /* > 0: L = ceil(exp(y1) L_scale)                       */
+    double margin;    /* >= 0: relative margin of the predicted bound          */
+    int L_min, L_max, L_fallback;   /* 1 <= L_min <= L_max, 1 <= L_fallback <= L_max */
+    int use_lambda;   /* serve the predicted bound (else the 20-step bound)    */
+} cpa_learn_rule;
+CPA_API cpa_status cpa_svt_learned(cpa_handle h, cpa_mlp net, const float *dX, int64_t m, int64_t n, int64_t ldx,
+                                   const cpa_shrink *s, const cpa_learn_rule *rule, int prec, float *dY,
+                                   int64_t ldy, void *stream);
+CPA_API cpa_status cpa_get_order(cpa_handle h, int *L_out, int *fallback, void *stream);
+/* ---------------------------------------------------------------------------
+ * Batches given member by member: device pointers, shapes, leading
+ * dimensions (elements, row-major) and orders per matrix, following the
+ * problem statement of Algorithm 1 for each member.  Members with
+ * min(m, n) <= 64, max(m, n) <= 128 and L <= 1024 (patch groups) run in one
+ * persistent launch of the batched kernel; the others run through the
+ * single-matrix path one after another on `stream`.  Asynchronous; the
+ * descriptor table is uploaded on `stream` from pinned staging owned by the
+ * handle (a later call waits until the previous upload has been read).
+ * Members' X and Y must not overlap.  Errors: INVALID_ARG (any member),
+ * UNSUPPORTED (precision), errors of cpa_svt pass through.
+ *
+ * cpa_svt_batched: plain CPA.  s: one shrink (s_count = 1) or one per
+ *   member; L: host array of count orders or NULL (L0 for all); lambda:
+ *   host array of count bounds (> 0) or NULL (each computed on the device
+ *   with the definition of cpa_lambda_bound).
+ * cpa_serve_learned: the learned choice of (Lambda_max, L) per member (no
+ *   counterpart in the paper): the batched kernel's learned mode for the
+ *   patch-sized members (orders clamped to 1024) and cpa_svt_learned for the
+ *   others, the same network and rule for all.  cpa_serve_read returns, for
+ *   the last learned call on the handle, each member's L and Lambda_max
+ *   (host arrays of count, either may be NULL) and the number of members
+ *   that took a fallback (synchronises `stream`).
+ * ------------------------------------------------------------------------- */
+CPA_API cpa_status cpa_svt_batched(cpa_handle h, int count, const float *const *dX, const int64_t *m,
+                                   const int64_t *n, const int64_t *ldx, const cpa_shrink *s, int s_count,
+                                   const int *L, int L0, const double *lambda, int prec, float *const *dY,
+                                   const int64_t *ldy, void *stream);
+CPA_API cpa_status cpa_serve_learned(cpa_handle h, cpa_mlp net, int count, const float *const *dX,
+                                     const int64_t *m, const int64_t *n, const int64_t *ldx, const cpa_shrink *s,
+                                     int s_count, const cpa_learn_rule *rule, int prec, float *const *dY,
+                                     const int64_t *ldy, void *stream);
+CPA_API cpa_status cpa_serve_read(cpa_handle h, int count, int *host_L, double *host_lambda, int *host_fallbacks,
+                                  void *stream);
+
+/* The 12 features and theta_4 of one matrix of any size (definition of
+ * cpa_batch_features) into device memory dF[12], dTheta[1]; asynchronous. */
+CPA_API cpa_status cpa_learn_features(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t ldx,
+                                      const cpa_shrink *s, float *dF, double *dTheta, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Background-modelling ADMM around the shrinkage (Appendix B, Eq.

@@ -32,6 +32,14 @@ Functions and the passage each follows:
 * ``shrink_exact``        exact shrinkage via SVD, Eq. sing_shrink_exact
 * ``shrink_exact_evd``    exact shrinkage via EVD, Eq. sing_shrink_exact_from_eig2
 * ``start_vector``        SplitMix64 start vector for the power iteration
+* ``singular_values``     singular values through LAPACK (a library primitive,
+                          for spectra of large matrices)
+* ``shrink_exact_lapack`` exact shrinkage U diag(g(sigma)) V^T (Eq.
+                          sing_shrink_exact) with LAPACK's SVD as the
+                          decomposition step, for judging results at large sizes
+* ``spectral_errors``     |G_hat(X) - G(X)|_F / |G(X)|_F of the FP64 CPA for many
+                          orders at once from the singular values (the
+                          spectral error identity)
 """
 from __future__ import annotations
 
@@ -350,3 +358,43 @@ def filter_block(S, s: Shrink, alpha: int, lam: float, V) -> np.ndarray:
     thresholded Phi of Eq. threshold_components), p x k block V."""
     S = np.asarray(S, dtype=np.float64)
     return _series_block(lambda Z: S @ Z, s, alpha, lam, V)
+
+
+def singular_values(X) -> np.ndarray:
+    """Singular values of X in descending order, LAPACK's SVD (gesdd)."""
+    return np.linalg.svd(np.asarray(X, dtype=np.float64), compute_uv=False)
+
+
+def shrink_exact_lapack(X, s: Shrink) -> np.ndarray:
+    """U diag(g(sigma_i)) V^T (Eq. sing_shrink_exact), the thin SVD from
+    LAPACK, g from the scalar response of Eq. filter_response_ours."""
+    X = np.asarray(X, dtype=np.float64)
+    U, sv, Vt = np.linalg.svd(X, full_matrices=False)
+    gs = np.array([g(s, x) for x in sv])
+    return (U * gs) @ Vt
+
+
+def spectral_errors(sv, s: Shrink, lam: float, alphas) -> np.ndarray:
+    """Relative Frobenius error of the FP64 CPA against the exact shrinkage
+    for every alpha in `alphas`, from the singular values alone: X H_hat(X^T X)
+    and the exact shrinkage share singular vectors, so the difference has
+    singular values sigma_i |h_hat(sigma_i^2) - h(sigma_i^2)| (as in
+    approx_error_spectral).  When the exact shrinkage is 0 the error is
+    relative to |X|_F."""
+    sv = np.asarray(sv, dtype=np.float64)
+    x = sv * sv
+    hx = np.array([h(s, v) for v in x])
+    exact = float(np.sqrt(np.sum((sv * hx) ** 2)))
+    den = exact if exact > 0 else float(np.sqrt(np.sum(x)))
+    t = 2.0 * x / lam - 1.0
+    out = []
+    for alpha in alphas:
+        ck = coeffs(s, int(alpha), lam)
+        # the shifted series at t by the three-term recurrence (Eq. chebyche2)
+        z0, z1 = np.ones_like(t), t
+        hh = 0.5 * ck[0] * z0 + (ck[1] * z1 if alpha > 1 else 0.0)
+        for k in range(2, int(alpha)):
+            z0, z1 = z1, 2.0 * t * z1 - z0
+            hh = hh + ck[k] * z1
+        out.append(float(np.sqrt(np.sum((sv * (hh - hx)) ** 2))) / den)
+    return np.array(out)

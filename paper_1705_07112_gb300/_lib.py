@@ -22,13 +22,14 @@ PREC = {"fp32": FP32, "tf32": TF32, "bf16": BF16, "bf16x3": BF16X3}
 # every function include/cpa.h declares
 EXPORTS = ["cpa_create", "cpa_destroy", "cpa_status_string", "cpa_last_error", "cpa_coeffs",
            "cpa_lambda_bound", "cpa_svt", "cpa_svt_host", "cpa_get_lambda", "cpa_get_coeffs", "cpa_batch_create",
-           "cpa_batch_destroy", "cpa_svt_batched", "cpa_batch_lambdas", "cpa_profile_enable",
+           "cpa_batch_destroy", "cpa_svt_batched_plan", "cpa_svt_batched", "cpa_batch_lambdas", "cpa_profile_enable",
            "cpa_profile_read", "cpa_kernel_gemm_bf16", "cpa_kernel_split_bf16", "cpa_batch_read_lambdas",
            "cpa_lambda_bound_noalloc", "cpa_mlp_create", "cpa_mlp_destroy", "cpa_mlp_param_count",
            "cpa_mlp_set_params", "cpa_mlp_get_params", "cpa_mlp_forward", "cpa_mlp_gradients",
            "cpa_mlp_train_step", "cpa_batch_features", "cpa_svt_batched_learned", "cpa_batch_read_choices",
            "cpa_admm_create", "cpa_admm_destroy", "cpa_admm_rpca", "cpa_set_option",
-           "cpa_completion_create", "cpa_completion_destroy", "cpa_completion_run", "cpa_sync_status"]
+           "cpa_completion_create", "cpa_completion_destroy", "cpa_completion_run", "cpa_sync_status",
+           "cpa_svt_learned", "cpa_get_order", "cpa_learn_features", "cpa_serve_learned", "cpa_serve_read"]
 OPT_SERIES, SERIES_FORWARD, SERIES_CLENSHAW = 1, 0, 1
 OPT_WAIT_KCYCLES, OPT_STALL_TEST = 2, 3
 STAGES = ["prep", "gram", "bound", "coeff", "shift", "recur", "apply", "sparse"]
@@ -43,6 +44,11 @@ class CpaShrink(ctypes.Structure):
 
 class CpaSparsify(ctypes.Structure):
     _fields_ = [("transform", ctypes.c_int), ("mode", ctypes.c_int), ("eps_or_frac", ctypes.c_double)]
+
+
+class CpaLearnRule(ctypes.Structure):
+    _fields_ = [("L_scale", ctypes.c_double), ("margin", ctypes.c_double), ("L_min", ctypes.c_int),
+                ("L_max", ctypes.c_int), ("L_fallback", ctypes.c_int), ("use_lambda", ctypes.c_int)]
 
 
 class CpaError(RuntimeError):
@@ -78,11 +84,22 @@ def load(path: str = LIB_PATH):
                                             ctypes.c_int, _d, ctypes.c_int, _P(CpaSparsify), _P(_vp), _i64, _vp]),
             "cpa_get_lambda": (ctypes.c_int, [_vp, _P(_d), _vp]),
             "cpa_sync_status": (ctypes.c_int, [_vp, _vp]),
+            "cpa_svt_learned": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _P(CpaShrink), _P(CpaLearnRule),
+                                               ctypes.c_int, _vp, _i64, _vp]),
+            "cpa_get_order": (ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_int), _vp]),
+            "cpa_svt_batched": (ctypes.c_int, [_vp, ctypes.c_int, _P(_vp), _P(_i64), _P(_i64), _P(_i64),
+                                               _P(CpaShrink), ctypes.c_int, _P(ctypes.c_int), ctypes.c_int,
+                                               _P(_d), ctypes.c_int, _P(_vp), _P(_i64), _vp]),
+            "cpa_serve_learned": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _P(_vp), _P(_i64), _P(_i64), _P(_i64),
+                                                 _P(CpaShrink), ctypes.c_int, _P(CpaLearnRule), ctypes.c_int,
+                                                 _P(_vp), _P(_i64), _vp]),
+            "cpa_serve_read": (ctypes.c_int, [_vp, ctypes.c_int, _P(ctypes.c_int), _P(_d), _P(ctypes.c_int), _vp]),
+            "cpa_learn_features": (ctypes.c_int, [_vp, _vp, _i64, _i64, _i64, _P(CpaShrink), _vp, _vp, _vp]),
             "cpa_get_coeffs": (ctypes.c_int, [_vp, _P(_d), ctypes.c_int, _vp]),
             "cpa_batch_create": (ctypes.c_int, [_vp, ctypes.c_int, _P(_i64), _P(_i32), _P(_i32), _P(_i32),
                                                 ctypes.c_int, _P(_vp)]),
             "cpa_batch_destroy": (ctypes.c_int, [_vp]),
-            "cpa_svt_batched": (ctypes.c_int, [_vp, _vp, _vp, _P(CpaShrink), ctypes.c_int, _vp, ctypes.c_int,
+            "cpa_svt_batched_plan": (ctypes.c_int, [_vp, _vp, _vp, _P(CpaShrink), ctypes.c_int, _vp, ctypes.c_int,
                                                ctypes.c_int, _vp, _vp]),
             "cpa_batch_lambdas": (_vp, [_vp]),
             "cpa_batch_read_lambdas": (ctypes.c_int, [_vp, _P(_d), _vp]),
@@ -381,7 +398,7 @@ class BatchPlan:
         return out
 
 
-def cpa_svt_batched(h: Handle, plan: BatchPlan, X, shrink, lambdas=None, iters: int = 20, prec="bf16x3", Y=None,
+def cpa_svt_batched_plan(h: Handle, plan: BatchPlan, X, shrink, lambdas=None, iters: int = 20, prec="bf16x3", Y=None,
                     stream=None):
     """Batched shrinkage of the packed matrices in X (flat float32 CUDA
     tensor); shrink: one spec or a list with one per matrix; lambdas: None
@@ -398,8 +415,8 @@ def cpa_svt_batched(h: Handle, plan: BatchPlan, X, shrink, lambdas=None, iters: 
             raise ValueError("lambdas must be a float64 CUDA tensor of plan.count values")
         lam = ctypes.c_void_p(lambdas.data_ptr())
     p = PREC[prec] if isinstance(prec, str) else int(prec)
-    _check(load().cpa_svt_batched(h.ptr, plan.ptr, ctypes.c_void_p(X.data_ptr()), arr, k, lam, int(iters),
-                                  p, ctypes.c_void_p(Y.data_ptr()), _stream_ptr(stream)), "cpa_svt_batched")
+    _check(load().cpa_svt_batched_plan(h.ptr, plan.ptr, ctypes.c_void_p(X.data_ptr()), arr, k, lam, int(iters),
+                                       p, ctypes.c_void_p(Y.data_ptr()), _stream_ptr(stream)), "cpa_svt_batched_plan")
     return Y
 
 
@@ -610,3 +627,119 @@ class Completion:
 
 def cpa_set_option(h: Handle, option: int, value: int):
     _check(load().cpa_set_option(h.ptr, int(option), int(value)), "cpa_set_option")
+
+
+def learn_rule(L_scale=1.0, margin=0.02, L_min=4, L_max=1024, L_fallback=50, use_lambda=True) -> CpaLearnRule:
+    return CpaLearnRule(float(L_scale), float(margin), int(L_min), int(L_max), int(L_fallback),
+                        1 if use_lambda else 0)
+
+
+def cpa_svt_learned(h: Handle, net, X, shrink, rule: CpaLearnRule, prec="bf16x3", Y=None, stream=None):
+    """cpa_svt with (Lambda_max, L) chosen on the device by the predictor
+    network `net` (an MLP of widths 12, 64, 64, 2)."""
+    import torch
+    ptr, m, n, ld = _matrix(X, "X")
+    if Y is None:
+        Y = torch.empty((m, n), dtype=torch.float32, device=X.device)
+    yptr, ym, yn, ldy = _matrix(Y, "Y")
+    if (ym, yn) != (m, n):
+        raise ValueError("Y shape mismatch")
+    s = _as_shrink(shrink)
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    _check(load().cpa_svt_learned(h.ptr, net.ptr, ctypes.c_void_p(ptr), m, n, ld, ctypes.byref(s),
+                                  ctypes.byref(rule), p, ctypes.c_void_p(yptr), ldy, _stream_ptr(stream)),
+           "cpa_svt_learned")
+    return Y
+
+
+def cpa_get_order(h: Handle, stream=None):
+    L, fb = ctypes.c_int(), ctypes.c_int()
+    _check(load().cpa_get_order(h.ptr, ctypes.byref(L), ctypes.byref(fb), _stream_ptr(stream)), "cpa_get_order")
+    return L.value, fb.value
+
+
+def cpa_learn_features(h: Handle, X, shrink, F=None, theta=None, stream=None):
+    """The 12 predictor features and theta_4 of one matrix (device tensors)."""
+    import torch
+    ptr, m, n, ld = _matrix(X, "X")
+    if F is None:
+        F = torch.empty(12, dtype=torch.float32, device=X.device)
+    if theta is None:
+        theta = torch.empty(1, dtype=torch.float64, device=X.device)
+    s = _as_shrink(shrink)
+    _check(load().cpa_learn_features(h.ptr, ctypes.c_void_p(ptr), m, n, ld, ctypes.byref(s),
+                                     ctypes.c_void_p(F.data_ptr()), ctypes.c_void_p(theta.data_ptr()),
+                                     _stream_ptr(stream)), "cpa_learn_features")
+    return F, theta
+
+
+class MemberList:
+    """Marshalled member arrays of a pointer-form batch (device pointers,
+    shapes, leading dimensions, shrinks), built once and reused."""
+
+    def __init__(self, Xs, Ys, shrinks):
+        if len(Xs) != len(Ys):
+            raise ValueError("Xs and Ys must have the same length")
+        self.count = len(Xs)
+        xs, ys, ms, ns, lx, ly = [], [], [], [], [], []
+        for X, Y in zip(Xs, Ys):
+            xp, m, n, ld = _matrix(X, "X")
+            yp, ym, yn, ldy = _matrix(Y, "Y")
+            if (ym, yn) != (m, n):
+                raise ValueError("Y shape mismatch")
+            xs.append(xp)
+            ys.append(yp)
+            ms.append(m)
+            ns.append(n)
+            lx.append(ld)
+            ly.append(ldy)
+        c = self.count
+        self.X = (_vp * c)(*[ctypes.c_void_p(v) for v in xs])
+        self.Y = (_vp * c)(*[ctypes.c_void_p(v) for v in ys])
+        self.m = (_i64 * c)(*ms)
+        self.n = (_i64 * c)(*ns)
+        self.ldx = (_i64 * c)(*lx)
+        self.ldy = (_i64 * c)(*ly)
+        self.shapes = list(zip(ms, ns))
+        if isinstance(shrinks, (list, tuple)):
+            if len(shrinks) != c:
+                raise ValueError("one shrink per member, or a single one")
+            self.shrink = (CpaShrink * c)(*[_as_shrink(x) for x in shrinks])
+            self.s_count = c
+        else:
+            self.shrink = (CpaShrink * 1)(_as_shrink(shrinks))
+            self.s_count = 1
+
+
+def cpa_svt_batched(h: Handle, members: MemberList, L=None, L0: int = 24, lambdas=None, prec="bf16x3",
+                    stream=None):
+    """Plain CPA of every member (pointer form): patch-sized members in one
+    persistent launch, the others through cpa_svt.  L: list of orders or
+    None (L0); lambdas: list of host bounds or None (computed)."""
+    c = members.count
+    Ls = (ctypes.c_int * c)(*[int(v) for v in L]) if L is not None else None
+    lam = (ctypes.c_double * c)(*[float(v) for v in lambdas]) if lambdas is not None else None
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    _check(load().cpa_svt_batched(h.ptr, c, members.X, members.m, members.n, members.ldx, members.shrink,
+                                  members.s_count, Ls, int(L0), lam, p, members.Y, members.ldy, _stream_ptr(stream)),
+           "cpa_svt_batched")
+
+
+def cpa_serve_learned(h: Handle, net, members: MemberList, rule: CpaLearnRule, prec="bf16x3", stream=None):
+    """The learned choice of (Lambda_max, L) for every member (pointer form)."""
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    _check(load().cpa_serve_learned(h.ptr, net.ptr, members.count, members.X, members.m, members.n, members.ldx,
+                                    members.shrink, members.s_count, ctypes.byref(rule), p, members.Y,
+                                    members.ldy, _stream_ptr(stream)), "cpa_serve_learned")
+
+
+def cpa_serve_read(h: Handle, count: int, stream=None):
+    """(L per member, Lambda_max per member, fallback count) of the last
+    cpa_serve_learned call on the handle."""
+    L = np.zeros(count, dtype=np.int32)
+    lam = np.zeros(count, dtype=np.float64)
+    fb = ctypes.c_int()
+    _check(load().cpa_serve_read(h.ptr, int(count), L.ctypes.data_as(_P(ctypes.c_int)),
+                                 lam.ctypes.data_as(_P(_d)), ctypes.byref(fb), _stream_ptr(stream)),
+           "cpa_serve_read")
+    return L, lam, fb.value

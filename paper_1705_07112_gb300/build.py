@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcpa.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["cpa_api.cu", "gemm_simt.cu", "gemm_tc.cu", "kernels_aux.cu", "batched.cu", "noalloc.cu", "sparsify.cu", "mlp.cu", "admm.cu", "completion.cu"]
+SOURCES = ["cpa_api.cu", "gemm_simt.cu", "gemm_tc.cu", "kernels_aux.cu", "batched.cu", "noalloc.cu", "sparsify.cu", "mlp.cu", "admm.cu", "completion.cu", "learned.cu"]
 
 
 def nvcc() -> str:

@@ -38,12 +38,17 @@ constexpr int kQ = 128;         // maximum max(m, n)
 constexpr int kLdB = kP + 8;    // BF16 row stride of 64-wide tiles (conflict-free ldmatrix)
 constexpr int kLdX = kQ + 8;    // BF16 row stride of X tiles
 constexpr int kThreads = 128;
-constexpr int kMaxBatchTerms = 128;
+constexpr int kMaxBatchTerms = 1024;
 constexpr uint64_t kEdgeSeedXor = 0x5EEDULL;   // start vector of the lower-edge feature
 
 struct BatchDesc {
     int64_t off;   // element offset of X (and Y) in the packed buffers
     int m, n, L, pad;
+    // per-matrix operands (pointer form): X and Y with their own row
+    // strides; null x: the packed buffers at `off` with row stride n
+    const float *x;
+    float *y;
+    int64_t ldx, ldy;
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -135,14 +140,28 @@ struct BatchSmem {
     float g[kP * (kP + 1)];              // G (FP32), then H for the final product
     float v[2][kP];                      // power-iteration vectors
     float redf[8];                       // bsumf partials, two sets of four
-    double coef[kMaxBatchTerms];
-    double tab[4 * kMaxBatchTerms];
-    double hs[kMaxBatchTerms];
+    float coef[kMaxBatchTerms];          // c_k (summed in FP64, kept in FP32: the recurrence's epilogue
+                                         // arithmetic); before that, the predictor's scratch
     double scal[4];                      // theta, r, trace, lambda
     double lam;                          // the bound, formed by thread 0
     float s2;                            // 2 / lambda in FP32, formed by thread 0
     int next_it;                         // work item fetched by thread 0
 };
+
+// The coefficient sums' FP64 scratch, in the Psi_{k-1} buffers' lo halves
+// (free until the shift): a table of cos(pi m / 2L) for m = 0..L and the
+// response at the L nodes, 2L + 1 doubles.
+static_assert((2 * kMaxBatchTerms + 1) * sizeof(double) <= 2 * kP * kLdB * sizeof(__nv_bfloat16),
+              "coefficient scratch");
+__device__ __forceinline__ double *coef_tab(BatchSmem &S) { return reinterpret_cast<double *>(&S.zlo[0][0]); }
+
+// cos(pi m / 2L) for any integer m >= 0 from the table of m = 0..L:
+// cos(2 pi - x) = cos x and cos(pi - x) = -cos x.
+__device__ __forceinline__ double cos_from_tab(const double *tab, int m, int L) {
+    m %= 4 * L;
+    if (m > 2 * L) m = 4 * L - m;
+    return m > L ? -tab[2 * L - m] : tab[m];
+}
 
 // Block sum (4 warps) of one float per thread.  The warp partials go through
 // one of two sets of shared slots, alternating with `slot`, so one barrier
@@ -342,7 +361,7 @@ __device__ __noinline__ Choice learned_phase(BatchSmem &S, int idx, int p, int q
         fro = bsumf(fro, S.redf, rs);
         const float tr = bsumf(own ? S.g[row * (kP + 1) + row] : 0.f, S.redf, rs);
         // one feature per thread (threads 0..11): ratio in FP64, log in FP32
-        float *fv = reinterpret_cast<float *>(S.tab);
+        float *fv = S.coef;   // free until the coefficients are formed
         if (tid < kFeatures) {
             const double tiny = 1e-30;
             const double E = tr > 0.f ? (double)tr : 1.0;
@@ -441,7 +460,10 @@ __device__ __noinline__ Choice learned_phase(BatchSmem &S, int idx, int p, int q
             yv[tid] = a;
         }
         __syncthreads();
-        // decision rule, taken by thread 0 and broadcast
+        // decision rule, taken by thread 0 and broadcast.  The predicted
+        // bound is never taken below the residual-corrected estimate
+        // (theta_4 + r_4)(1 + margin): below sigma_max^2 the series grows
+        // outside [-1, 1]; such predictions count as fallbacks
         if (tid == 0) {
             const double y0 = (double)yv[0], y1 = (double)yv[1];
             const double Lf = ceil(exp(y1) * la.L_scale);
@@ -452,9 +474,13 @@ __device__ __noinline__ Choice learned_phase(BatchSmem &S, int idx, int p, int q
             bool ok_lam = true;
             if (la.use_lambda) {
                 const double lp = (double)th4 * exp(fmax(y0, 0.0)) * (1.0 + la.margin);
-                ok_lam = isfinite(lp) && lp > 0.0;
-                if (ok_lam) lc = lp;
-                else Lc = la.L_fallback;
+                const double floor_lam = ((double)th4 + (double)r4) * (1.0 + la.margin);
+                ok_lam = isfinite(lp) && lp > 0.0 && lp >= floor_lam;
+                if (isfinite(lp) && lp > 0.0) {
+                    lc = fmax(lp, floor_lam);
+                } else {
+                    Lc = la.L_fallback;   // non-finite prediction: the bound and the fallback order
+                }
             }
             la.L_out[idx] = Lc;
             if (!ok_L || !ok_lam) atomicAdd(la.nfallback, 1);
@@ -463,7 +489,7 @@ __device__ __noinline__ Choice learned_phase(BatchSmem &S, int idx, int p, int q
         }
         __syncthreads();
         const Choice c{S.scal[0], S.next_it};
-        __syncthreads();   // S.tab and S.next_it are rewritten by the caller
+        __syncthreads();   // S.coef and S.next_it are rewritten by the caller
         return c;
 }
 
@@ -496,8 +522,9 @@ __global__ void __launch_bounds__(kThreads, 2)
         const bool tall = m >= n;           // Gram X^T X (p = n) or X X^T (p = m)
         const int p = tall ? n : m, q = tall ? m : n;
         const int q16 = (q + 15) & ~15, p16 = (p + 15) & ~15;
-        const float *Xg = X + d.off;
-        float *Yg = Y + d.off;
+        const float *Xg = d.x ? d.x : X + d.off;
+        float *Yg = d.x ? d.y : Y + d.off;
+        const int64_t ldxm = d.x ? d.ldx : n, ldym = d.x ? d.ldy : n;
         const ShrinkParams sp = shr[shr_stride ? idx : 0];
 
         // ---- Xp (p x q, zero padded to multiples of 16) into shared memory:
@@ -522,7 +549,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const int e = base + k * kThreads + tid;
-                    v[k] = e < mn ? __ldg(Xg + e) : 0.f;
+                    const int i = e / n, j = e - i * n;
+                    v[k] = e < mn ? __ldg(Xg + (int64_t)i * ldxm + j) : 0.f;
                 }
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
@@ -569,7 +597,9 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
             float nrm2 = bsumf(s0, S.redf, rs);
             int cur = 0;
-            const int its = FEAT ? 4 : iters;
+            // the learned choice with the predicted bound needs only the
+            // features' four products; its fallback bound is theirs
+            const int its = (FEAT || (LEARN && la.use_lambda)) ? 4 : iters;
             for (int t = 0; t <= its; ++t) {
                 // w = G (v / |v|): two threads per row
                 const float sc = nrm2 > 0.f ? 1.f / sqrtf(nrm2) : 0.f;
@@ -623,35 +653,35 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (tid == 0) lam_out[idx] = lam;
 
         // ---- coefficients (Eq. chebychev_coeff_shifted), FP64, from the table
-        // cos(pi m / 2L), m < 4L: evaluated for m <= L, the rest by symmetry
-        // (cos(2 pi - x) = cos x, cos(pi - x) = -cos x)
-        for (int e = tid; e <= L; e += kThreads) S.tab[e] = cospi((double)e / (2.0 * L));
-        if (tid == 0) S.s2 = (float)(2.0 / lam);
-        __syncthreads();
-        for (int e = L + 1 + tid; e < 4 * L; e += kThreads) {
-            const int mm = e > 2 * L ? 4 * L - e : e;
-            S.tab[e] = mm > L ? -S.tab[2 * L - mm] : S.tab[mm];
-        }
-        __syncthreads();
-        for (int l = tid; l < L; l += kThreads) S.hs[l] = response(sp, 0.5 * lam * (S.tab[(2 * l + 1) % (4 * L)] + 1.0));
-        __syncthreads();
-        for (int k = tid; k < L; k += kThreads) {
-            // table index k (2l + 1) mod 4L, advanced by 2k per node
-            const int M4 = 4 * L;
-            int ix = k;
-            double a = 0.0;
-            for (int l = 0; l < L; ++l) {
-                a += S.tab[ix] * S.hs[l];
-                ix += 2 * k;
-                if (ix >= M4) ix -= M4;
+        // cos(pi m / 2L), m = 0..L (other m by symmetry), in the free Psi
+        // buffers; kept in FP32 for the recurrence's epilogue
+        {
+            double *tab = coef_tab(S), *hs = tab + (L + 1);
+            for (int e = tid; e <= L; e += kThreads) tab[e] = cospi((double)e / (2.0 * L));
+            if (tid == 0) S.s2 = (float)(2.0 / lam);
+            __syncthreads();
+            for (int l = tid; l < L; l += kThreads) hs[l] = response(sp, 0.5 * lam * (cos_from_tab(tab, 2 * l + 1, L) + 1.0));
+            __syncthreads();
+            for (int k = tid; k < L; k += kThreads) {
+                // table index k (2l + 1) mod 4L, advanced by 2k per node
+                const int M4 = 4 * L;
+                int ix = k % M4;
+                const int step = (2 * k) % M4;
+                double a = 0.0;
+                for (int l = 0; l < L; ++l) {
+                    int mm = ix > 2 * L ? M4 - ix : ix;
+                    a += (mm > L ? -tab[2 * L - mm] : tab[mm]) * hs[l];
+                    ix += step;
+                    if (ix >= M4) ix -= M4;
+                }
+                S.coef[k] = (float)(2.0 / (double)L * a);
             }
-            S.coef[k] = 2.0 / (double)L * a;
+            __syncthreads();
         }
-        __syncthreads();
 
         // ---- shift: At = (2/lambda) G (operand), Psi_1 = At - Id, H = c0/2 Id + c1 Psi_1
         const float s2 = S.s2;
-        const float c0h = (float)(0.5 * S.coef[0]), c1 = L > 1 ? (float)S.coef[1] : 0.f;
+        const float c0h = 0.5f * S.coef[0], c1 = L > 1 ? S.coef[1] : 0.f;
         Frag z1, z0, h;   // Psi_{k-1}, Psi_{k-2}, H in the accumulator layout
 #pragma unroll
         for (int nt = 0; nt < 8; ++nt)
@@ -693,7 +723,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 fma_tile(acc, [&](int i, int kk) { return af[i * kLdB + kk]; },
                          [&](int kk, int j) { return zf[kk * kLdB + j]; }, p, w, lane);
             }
-            const float ck = (float)S.coef[k];
+            const float ck = S.coef[k];
 #pragma unroll
             for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
@@ -747,9 +777,9 @@ __global__ void __launch_bounds__(kThreads, 2)
                     const int r = frag_row(w, lane, e), c = 64 * b + frag_col(nt, lane, e);
                     if (r < p && c < q) {
                         if (tall)
-                            Yg[(int64_t)c * n + r] = acc.v[nt][e];
+                            Yg[(int64_t)c * ldym + r] = acc.v[nt][e];
                         else
-                            Yg[(int64_t)r * n + c] = acc.v[nt][e];
+                            Yg[(int64_t)r * ldym + c] = acc.v[nt][e];
                     }
                 }
         }
@@ -806,7 +836,7 @@ cpa_status cpa_batch_create(cpa_handle h, int count, const int64_t *off, const i
         if (mi < 1 || ni < 1 || std::min(mi, ni) > kP || std::max(mi, ni) > kQ || off[i] < 0 || Li < 1 ||
             Li > kMaxBatchTerms)
             return CPA_ERR_INVALID_ARG;
-        desc[i] = BatchDesc{off[i], mi, ni, Li, 0};
+        desc[i] = BatchDesc{off[i], mi, ni, Li, 0, nullptr, nullptr, 0, 0};
         max_L = std::max(max_L, Li);
         total = std::max(total, off[i] + (int64_t)mi * ni);
     }
@@ -905,20 +935,38 @@ cpa_status upload_shrink(cpa_batch b, const cpa_shrink *s, int s_count, cudaStre
     return CPA_OK;
 }
 
+// Device buffers of one batched launch.
+struct BatchRun {
+    const BatchDesc *desc;
+    const int *order;
+    int count;
+    const ShrinkParams *shrink;
+    double *lambda_out;
+    int *status;
+    int num_sms;
+};
+
 template <bool TC, bool FEAT, bool LEARN>
-cpa_status launch_batched(cpa_batch b, const float *dX, float *dY, int s_count, const double *lambda, int iters,
-                          const int *L_override, float *feat, double *theta, const LearnArgs &la, cudaStream_t st) {
+cpa_status launch_run(const BatchRun &b, const float *dX, float *dY, int s_count, const double *lambda, int iters,
+                      const int *L_override, float *feat, double *theta, const LearnArgs &la, cudaStream_t st) {
     const size_t smem = sizeof(BatchSmem);
     auto kern = batched_kernel<TC, FEAT, LEARN>;
-    BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BCK(ensure_smem_limit((const void *)kern, (int)smem));
     int per_sm = 0;
     BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
     if (per_sm < 1) per_sm = 1;
-    const int grid = std::min(b->count, b->num_sms * per_sm);
-    kern<<<grid, kThreads, smem, st>>>(b->d_desc, b->d_order, b->count, dX, dY, b->d_shrink, s_count > 1 ? 1 : 0,
-                                       lambda, b->d_lambda, iters, b->d_status, L_override, feat, theta, la);
+    const int grid = std::min(b.count, b.num_sms * per_sm);
+    kern<<<grid, kThreads, smem, st>>>(b.desc, b.order, b.count, dX, dY, b.shrink, s_count > 1 ? 1 : 0, lambda,
+                                       b.lambda_out, iters, b.status, L_override, feat, theta, la);
     BCK(cudaGetLastError());
     return CPA_OK;
+}
+
+template <bool TC, bool FEAT, bool LEARN>
+cpa_status launch_batched(cpa_batch b, const float *dX, float *dY, int s_count, const double *lambda, int iters,
+                          const int *L_override, float *feat, double *theta, const LearnArgs &la, cudaStream_t st) {
+    const BatchRun r{b->d_desc, b->d_order, b->count, b->d_shrink, b->d_lambda, b->d_status, b->num_sms};
+    return launch_run<TC, FEAT, LEARN>(r, dX, dY, s_count, lambda, iters, L_override, feat, theta, la, st);
 }
 
 cpa_status check_io(cpa_batch b, const float *dX, const float *dY) {
@@ -958,7 +1006,7 @@ cpa_status ensure_learned_buffers(cpa_batch b) {
 
 extern "C" {
 
-cpa_status cpa_svt_batched(cpa_handle h, cpa_batch b, const float *dX, const cpa_shrink *s, int s_count,
+cpa_status cpa_svt_batched_plan(cpa_handle h, cpa_batch b, const float *dX, const cpa_shrink *s, int s_count,
                            const double *lambda, int iters, int prec, float *dY, void *stream) {
     return run_batched(h, b, dX, s, s_count, lambda, iters, prec, dY, stream);
 }
@@ -1015,3 +1063,146 @@ cpa_status cpa_batch_read_choices(cpa_batch b, int *host_L, int *host_fallbacks,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Pointer form: a batch given as per-matrix device pointers, shapes, leading
+// dimensions and orders (the patch-sized members of cpa_svt_batched and
+// cpa_serve_learned).  The handle owns one PtrPlan: device descriptor
+// buffers grown on demand and pinned host staging, uploaded on the call's
+// stream; an event orders the reuse of the staging across calls.
+
+namespace cpa {
+
+struct PtrPlan {
+    int device = 0, num_sms = 0, cap = 0;
+    BatchDesc *d_desc = nullptr, *h_desc = nullptr;
+    int *d_order = nullptr, *h_order = nullptr;
+    ShrinkParams *d_shrink = nullptr, *h_shrink = nullptr;
+    double *d_lam_in = nullptr, *h_lam = nullptr, *d_lam_out = nullptr;
+    int *d_status = nullptr, *d_L = nullptr, *d_nfb = nullptr;
+    cudaEvent_t staged = nullptr;
+};
+
+namespace {
+void ptr_plan_free(PtrPlan *pp) {
+    cudaFree(pp->d_desc);
+    cudaFree(pp->d_order);
+    cudaFree(pp->d_shrink);
+    cudaFree(pp->d_lam_in);
+    cudaFree(pp->d_lam_out);
+    cudaFree(pp->d_status);
+    cudaFree(pp->d_L);
+    cudaFree(pp->d_nfb);
+    cudaFreeHost(pp->h_desc);
+    cudaFreeHost(pp->h_order);
+    cudaFreeHost(pp->h_shrink);
+    cudaFreeHost(pp->h_lam);
+    pp->d_desc = pp->h_desc = nullptr;
+    pp->d_order = pp->h_order = nullptr;
+    pp->d_shrink = pp->h_shrink = nullptr;
+    pp->d_lam_in = pp->h_lam = pp->d_lam_out = nullptr;
+    pp->d_status = pp->d_L = pp->d_nfb = nullptr;
+    pp->cap = 0;
+}
+
+cpa_status ptr_plan_reserve(PtrPlan *pp, int count, cudaStream_t st) {
+    if (count <= pp->cap) return CPA_OK;
+    BCK(cudaStreamSynchronize(st));
+    if (pp->staged) BCK(cudaEventSynchronize(pp->staged));
+    ptr_plan_free(pp);
+    const int c = std::max(count, 256);
+    cudaError_t e = cudaMalloc(&pp->d_desc, sizeof(BatchDesc) * c);
+    if (e == cudaSuccess) e = cudaMalloc(&pp->d_order, sizeof(int) * c);
+    if (e == cudaSuccess) e = cudaMalloc(&pp->d_shrink, sizeof(ShrinkParams) * c);
+    if (e == cudaSuccess) e = cudaMalloc(&pp->d_lam_in, sizeof(double) * c);
+    if (e == cudaSuccess) e = cudaMalloc(&pp->d_lam_out, sizeof(double) * c);
+    if (e == cudaSuccess) e = cudaMalloc(&pp->d_status, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&pp->d_L, sizeof(int) * c);
+    if (e == cudaSuccess) e = cudaMalloc(&pp->d_nfb, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&pp->h_desc, sizeof(BatchDesc) * c);
+    if (e == cudaSuccess) e = cudaMallocHost(&pp->h_order, sizeof(int) * c);
+    if (e == cudaSuccess) e = cudaMallocHost(&pp->h_shrink, sizeof(ShrinkParams) * c);
+    if (e == cudaSuccess) e = cudaMallocHost(&pp->h_lam, sizeof(double) * c);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ptr_plan_free(pp);
+        return CPA_ERR_NO_MEMORY;
+    }
+    pp->cap = c;
+    return CPA_OK;
+}
+}  // namespace
+
+PtrPlan *ptr_plan_create(int device, int num_sms) {
+    PtrPlan *pp = new PtrPlan();
+    pp->device = device;
+    pp->num_sms = num_sms;
+    return pp;
+}
+
+void ptr_plan_destroy(PtrPlan *pp) {
+    if (!pp) return;
+    if (pp->staged) {
+        cudaEventSynchronize(pp->staged);
+        cudaEventDestroy(pp->staged);
+    }
+    ptr_plan_free(pp);
+    delete pp;
+}
+
+cpa_status ptr_plan_run(PtrPlan *pp, int count, const PtrItem *items, const double *lambda_host, int prec,
+                        const float *net, const cpa_learn_rule *rule, cudaStream_t st) {
+    if (count <= 0) return CPA_OK;
+    cpa_status r = ptr_plan_reserve(pp, count, st);
+    if (r != CPA_OK) return r;
+    if (!pp->staged) BCK(cudaEventCreateWithFlags(&pp->staged, cudaEventDisableTiming));
+    BCK(cudaEventSynchronize(pp->staged));   // the previous call's upload has read the staging
+    std::vector<double> work(count);
+    for (int i = 0; i < count; ++i) {
+        const PtrItem &it = items[i];
+        pp->h_desc[i] = BatchDesc{0, it.m, it.n, it.L, 0, it.x, it.y, it.ldx, it.ldy};
+        pp->h_shrink[i] = it.shrink;
+        pp->h_order[i] = i;
+        const double p = std::min(it.m, it.n), q = std::max(it.m, it.n);
+        work[i] = (it.L - 2) * p * p * p + 2.0 * p * p * q;
+        if (lambda_host) pp->h_lam[i] = lambda_host[i];
+    }
+    std::stable_sort(pp->h_order, pp->h_order + count, [&](int a, int b) { return work[a] > work[b]; });
+    BCK(cudaMemcpyAsync(pp->d_desc, pp->h_desc, sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync(pp->d_order, pp->h_order, sizeof(int) * count, cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync(pp->d_shrink, pp->h_shrink, sizeof(ShrinkParams) * count, cudaMemcpyHostToDevice, st));
+    if (lambda_host)
+        BCK(cudaMemcpyAsync(pp->d_lam_in, pp->h_lam, sizeof(double) * count, cudaMemcpyHostToDevice, st));
+    BCK(cudaEventRecord(pp->staged, st));
+    BCK(cudaMemsetAsync(pp->d_status, 0, 2 * sizeof(int), st));
+    const BatchRun run{pp->d_desc, pp->d_order, count, pp->d_shrink, pp->d_lam_out, pp->d_status, pp->num_sms};
+    const bool tc = prec != CPA_FP32;
+    if (net) {
+        BCK(cudaMemsetAsync(pp->d_nfb, 0, sizeof(int), st));
+        LearnArgs la{net, rule->L_scale, rule->margin, rule->L_min, std::min(rule->L_max, kMaxBatchTerms),
+                     std::min(rule->L_fallback, kMaxBatchTerms), rule->use_lambda ? 1 : 0, pp->d_L, pp->d_nfb};
+        if (tc)
+            return launch_run<true, false, true>(run, nullptr, nullptr, count, nullptr, kDefaultPowerIters, nullptr,
+                                                 nullptr, nullptr, la, st);
+        return launch_run<false, false, true>(run, nullptr, nullptr, count, nullptr, kDefaultPowerIters, nullptr,
+                                              nullptr, nullptr, la, st);
+    }
+    const LearnArgs none{};
+    const double *lam = lambda_host ? pp->d_lam_in : nullptr;
+    if (tc)
+        return launch_run<true, false, false>(run, nullptr, nullptr, count, lam, kDefaultPowerIters, nullptr, nullptr,
+                                              nullptr, none, st);
+    return launch_run<false, false, false>(run, nullptr, nullptr, count, lam, kDefaultPowerIters, nullptr, nullptr,
+                                           nullptr, none, st);
+}
+
+// Device arrays of the last run: the bound and (learned runs) the order of
+// each member, in the order of the items passed; the fallback count.
+const double *ptr_plan_lambdas(const PtrPlan *pp) { return pp->d_lam_out; }
+const int *ptr_plan_orders(const PtrPlan *pp) { return pp->d_L; }
+const int *ptr_plan_fallbacks(const PtrPlan *pp) { return pp->d_nfb; }
+const int *ptr_plan_status(const PtrPlan *pp) { return pp->d_status; }
+
+int batched_max_terms() { return kMaxBatchTerms; }
+
+}  // namespace cpa

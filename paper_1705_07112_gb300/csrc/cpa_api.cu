@@ -32,6 +32,16 @@ struct cpa_ctx {
     int series = CPA_SERIES_FORWARD;   // how the filter's series is summed
     WaitPolicy wait;                   // grid-barrier wait limit, test stall
     int *d_err = nullptr;              // error word of the last cpa_svt's tensor-core kernels
+    bool have_learn = false;           // the last call chose its order on the device
+    int *d_L = nullptr;                // {L, fallback} of that call
+    // pointer-form batches (cpa_svt_batched, cpa_serve_learned): the
+    // patch-sized members' launch, and per-member choices of the larger
+    // members of the last learned call ({L, fallback} pairs, bounds)
+    PtrPlan *pplan = nullptr;
+    int *d_big_L = nullptr;
+    double *d_big_lam = nullptr;
+    int big_cap = 0;
+    std::vector<int> serve_small, serve_big;   // member indices of the last learned call
     // diagnostics
     bool profiling = false;
     int64_t launches[CPA_NSTAGES] = {};
@@ -187,10 +197,16 @@ struct SvtWs {
     // up to 128, the columns beyond p kept zero so the products run over a
     // contraction length that the grouped operand loads take whole
     int64_t ldk = 0;
+    // learned order: lower-edge vectors, FP64 accumulators and coefficient
+    // scratch, the chosen {L, fallback}
+    float *u0 = nullptr, *u1 = nullptr;
+    double *lacc = nullptr, *ltab = nullptr;
+    int *Lsel = nullptr;
     size_t bytes = 0;
 };
 
-SvtWs carve(char *base, int64_t m, int64_t n, int L, int iters, int prec, bool sparse = false) {
+SvtWs carve(char *base, int64_t m, int64_t n, int L, int iters, int prec, bool sparse = false, bool learn = false,
+            bool gram_only = false) {
     SvtWs w;
     int64_t p = std::min(m, n);
     w.ldp = round_up(p, 8);
@@ -200,6 +216,14 @@ SvtWs carve(char *base, int64_t m, int64_t n, int L, int iters, int prec, bool s
     w.norm2 = c.take<double>(iters + 2);
     w.coef = c.take<double>(std::max(L, 2));
     w.flag = c.take<int>(8);   // barrier and error words: 0, 1 bound; 2 recurrence; 3, 4 top-k; 5 tensor-core waits
+    if (learn) {
+        const size_t nacc = learn_scratch_doubles(L);
+        w.lacc = c.take<double>(nacc + 2 * (size_t)L + 8);
+        w.ltab = w.lacc + nacc;
+        w.u0 = c.take<float>(round_up(p, 4));
+        w.u1 = c.take<float>(round_up(p, 4));
+        w.Lsel = c.take<int>(4);
+    }
     w.G = c.take<float>(pp);
     w.A = c.take<float>(pp);
     w.Z[0] = c.take<float>(pp);
@@ -207,6 +231,17 @@ SvtWs carve(char *base, int64_t m, int64_t n, int L, int iters, int prec, bool s
     w.H = c.take<float>(pp);
     w.v0 = c.take<float>(round_up(p, 4));
     w.v1 = c.take<float>(round_up(p, 4));
+    if (gram_only && prec != CPA_FP32) {
+        // the Gram step's operands only (features of a matrix)
+        w.ldn = round_up(n, 8);
+        w.ldm = round_up(m, 8);
+        w.Xhi = c.take<__nv_bfloat16>((size_t)(m * w.ldn));
+        w.Xlo = c.take<__nv_bfloat16>((size_t)(m * w.ldn));
+        w.Xthi = c.take<__nv_bfloat16>((size_t)(n * w.ldm));
+        w.Xtlo = c.take<__nv_bfloat16>((size_t)(n * w.ldm));
+        w.bytes = c.off;
+        return w;
+    }
     if (sparse) {
         w.T = c.take<float>(pp);
         w.eps = c.take<float>(4);
@@ -312,6 +347,9 @@ cpa_status cpa_destroy(cpa_handle h) {
         if (h->out_done[i]) cudaEventDestroy(h->out_done[i]);
     }
     if (h->start) cudaEventDestroy(h->start);
+    ptr_plan_destroy(h->pplan);
+    if (h->d_big_L) cudaFree(h->d_big_L);
+    if (h->d_big_lam) cudaFree(h->d_big_lam);
     delete h;
     return CPA_OK;
 }
@@ -400,9 +438,94 @@ cpa_status cpa_lambda_bound(cpa_handle h, const float *dX, int64_t m, int64_t n,
     return CPA_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The learned choice of (Lambda_max, L): the network's parameters and the
+// decision rule.
+struct LearnCall {
+    const float *P;
+    cpa_learn_rule rule;
+};
+
+cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t ldx, const cpa_shrink *sh, int L,
+                    double lambda_max, int prec, const cpa_sparsify *sp, float *dY, int64_t ldy, void *stream,
+                    const LearnCall *learn);
+
+}  // namespace
+
+extern "C" {
+
 cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t ldx, const cpa_shrink *sh,
                    int L, double lambda_max, int prec, const cpa_sparsify *sp, float *dY, int64_t ldy,
                    void *stream) {
+    return svt_impl(h, dX, m, n, ldx, sh, L, lambda_max, prec, sp, dY, ldy, stream, nullptr);
+}
+
+cpa_status cpa_svt_learned(cpa_handle h, cpa_mlp net, const float *dX, int64_t m, int64_t n, int64_t ldx,
+                           const cpa_shrink *sh, const cpa_learn_rule *rule, int prec, float *dY, int64_t ldy,
+                           void *stream) {
+    if (!h || !net || !rule) return CPA_ERR_INVALID_ARG;
+    const cpa_learn_rule &r = *rule;
+    if (!(r.L_scale > 0.0) || !std::isfinite(r.L_scale) || !(r.margin >= 0.0) || !std::isfinite(r.margin) ||
+        r.L_min < 1 || r.L_max < r.L_min || r.L_max > kMaxTerms || r.L_fallback < 1 || r.L_fallback > r.L_max)
+        return CPA_ERR_INVALID_ARG;
+    int dims[4], dev = -1;
+    const float *P = mlp_device_params(net, dims, &dev);
+    if (!P || dims[0] != 12 || dims[1] != 64 || dims[2] != 64 || dims[3] != 2 || dev != h->device)
+        return CPA_ERR_INVALID_ARG;   // the 12 -> 64 -> 64 -> 2 predictor, on the handle's device
+    if (h->series != CPA_SERIES_FORWARD) return CPA_ERR_UNSUPPORTED;
+    LearnCall lc{P, r};
+    return svt_impl(h, dX, m, n, ldx, sh, r.L_max, 0.0, prec, nullptr, dY, ldy, stream, &lc);
+}
+
+cpa_status cpa_get_order(cpa_handle h, int *L_out, int *fallback, void *stream) {
+    if (!h || !h->have_learn || (!L_out && !fallback)) return CPA_ERR_INVALID_ARG;
+    cpa_status s = set_device(h);
+    if (s != CPA_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    int *pin = reinterpret_cast<int *>(h->h_pin + 8);
+    CK(cudaMemcpyAsync(pin, h->d_L, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (L_out) *L_out = pin[0];
+    if (fallback) *fallback = pin[1];
+    return CPA_OK;
+}
+
+cpa_status cpa_learn_features(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t ldx,
+                              const cpa_shrink *sh, float *dF, double *dTheta, void *stream) {
+    if (!h || !dF || !dTheta) return CPA_ERR_INVALID_ARG;
+    cpa_status s = validate_matrix(dX, m, n, ldx);
+    if (s != CPA_OK) return s;
+    if ((s = check_shrink(sh)) != CPA_OK) return s;
+    if ((s = set_device(h)) != CPA_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int prec = h->cc >= 100 ? CPA_BF16X3 : CPA_FP32;
+    SvtWs w = carve(nullptr, m, n, 2, 4, prec, false, true, true);
+    if ((s = ensure_ws(h, w.bytes, st)) != CPA_OK) return s;
+    w = carve(h->ws, m, n, 2, 4, prec, false, true, true);
+    const int64_t p = std::min(m, n);
+    if (prec != CPA_FP32) {
+        CK(split_bf16(dX, (int)m, (int)n, ldx, false, w.Xhi, w.Xlo, w.ldn, st));
+        CK(split_bf16(dX, (int)m, (int)n, ldx, true, w.Xthi, w.Xtlo, w.ldm, st));
+    }
+    CK(cudaMemsetAsync(w.flag + 5, 0, sizeof(int), st));
+    if ((s = run_gram(h, dX, m, n, ldx, w, prec, st)) != CPA_OK) return s;
+    ShrinkParams sp_ = to_params(sh);
+    CK(learn_bound(w.G, w.ldp, (int)p, (int)std::max(m, n), sp_, nullptr, 1.0, 0.0, 1, 2, 1, 0, 1,
+                   kDefaultPowerIters, w.v0, w.v1, w.u0, w.u1, w.lacc, w.ltab, (unsigned int *)w.flag, w.flag + 1,
+                   w.out, w.Lsel, dF, dTheta, w.coef, st, h->num_sms, h->wait));
+    return CPA_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t ldx, const cpa_shrink *sh, int L,
+                    double lambda_max, int prec, const cpa_sparsify *sp, float *dY, int64_t ldy, void *stream,
+                    const LearnCall *learn) {
     if (!h || !dY || ldy < n || L < 1 || L > kMaxTerms) return CPA_ERR_INVALID_ARG;
     cpa_status s = validate_matrix(dX, m, n, ldx);
     if (s != CPA_OK) return s;
@@ -430,9 +553,9 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
     if ((s = set_device(h)) != CPA_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     const int iters = kDefaultPowerIters;
-    SvtWs w = carve(nullptr, m, n, L, iters, prec, sparse);
+    SvtWs w = carve(nullptr, m, n, L, iters, prec, sparse, learn != nullptr);
     if ((s = ensure_ws(h, w.bytes, st)) != CPA_OK) return s;
-    w = carve(h->ws, m, n, L, iters, prec, sparse);
+    w = carve(h->ws, m, n, L, iters, prec, sparse, learn != nullptr);
     // the call's error word (timeouts of the tensor-core kernels' waits),
     // read back by cpa_get_lambda and cpa_sync_status
     h->d_err = w.flag + 5;
@@ -486,7 +609,16 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
         }
     }
     // interval bound
-    if (lambda_max > 0.0) {
+    if (learn) {
+        // features, network, decision and the chosen order's coefficients in
+        // one launch; L stays on the device for the recurrence
+        StageScope sc(h, CPA_STAGE_BOUND, st, 1);
+        const cpa_learn_rule &r = learn->rule;
+        CK(learn_bound(w.G, w.ldp, (int)p, (int)std::max(m, n), sp_, learn->P, r.L_scale, r.margin, r.L_min, r.L_max,
+                       r.L_fallback, r.use_lambda, 0, iters, w.v0, w.v1, w.u0, w.u1, w.lacc, w.ltab,
+                       (unsigned int *)w.flag, w.flag + 1, w.out, w.Lsel, nullptr, nullptr, w.coef, st, h->num_sms,
+                       h->wait));
+    } else if (lambda_max > 0.0) {
         StageScope sc(h, CPA_STAGE_BOUND, st, 1);
         set_scalar2_kernel<<<1, 1, 0, st>>>(w.out + 3, lambda_max, 0.0);
         CK(cudaGetLastError());
@@ -497,7 +629,7 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
                                   w.flag + 1, w.out, st, h->num_sms, L, &sp_, w.coef, h->wait));
     }
     // coefficients (FP64, on the device so the call stays asynchronous)
-    if (lambda_max > 0.0) {
+    if (lambda_max > 0.0 && !learn) {
         StageScope sc(h, CPA_STAGE_COEFF, st, 1);
         CK(device_coeffs(w.out + 3, 0.0, L, sp_, w.coef, st));
     }
@@ -511,8 +643,8 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
     }
     // recurrence with fused accumulation: Psi_k = 2 B_hat Psi_{k-1} - Psi_{k-2}, H += c_k Psi_k.
     // Ring: Psi_k overwrites Psi_{k-2} in slot k&1; Psi_0 = Id is implicit.
-    // The tensor-core path multiplies by At = (2/lambda) G and applies the
-    // shift exactly in the FP32 epilogue:  Psi_k = 2 At Psi_{k-1} - 2 Psi_{k-1} - Psi_{k-2}.
+    // Both paths multiply by At = (2/lambda) G and apply the shift exactly
+    // in the FP32 epilogue:  Psi_k = 2 At Psi_{k-1} - 2 Psi_{k-1} - Psi_{k-2}.
     int closed = 0;   // Clenshaw's closing step already applied by the launch
     if (tc && L > 2) {
         // every step in one cooperative launch (grid barrier between steps)
@@ -534,7 +666,14 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
         TcOperand a;
         a.hi = w.Ahi; a.lo = w.Alo; a.ld = w.ldk; a.rows = (int)p;
         CK(gemm_tc_recurrence((int)p, a, nsplit_rec, e, 2, L, w.Z, w.Zhi, w.Zlo, (unsigned int *)(w.flag + 2), st,
-                              h->num_sms, clenshaw, L, &closed, (int)w.ldk, h->wait));
+                              h->num_sms, clenshaw, L, &closed, (int)w.ldk, h->wait, learn ? w.Lsel : nullptr));
+    }
+    if (learn && !tc) {
+        // the CUDA-core recurrence is driven from the host: read the order
+        int *pin = reinterpret_cast<int *>(h->h_pin + 8);
+        CK(cudaMemcpyAsync(pin, w.Lsel, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        L = std::max(1, std::min(L, pin[0]));
     }
     for (int k = 2; k < L && !tc; ++k) {
         StageScope sc(h, CPA_STAGE_RECUR, st, 1);
@@ -564,6 +703,12 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
             e.H = nullptr;
         }
         if (!tc) {
+            // A holds At = (2/lambda) G: the -Id of B_hat is applied here
+            // exactly, -2 Psi_{k-1} (FP32 rounding of B_hat's diagonal near
+            // -1 would move the eigenvalues near the interval's ends)
+            e.C2 = w.Z[prev];
+            e.ldc2 = w.ldp;
+            e.s_c2 = -2.f;
             CK(gemm_f32((int)p, (int)p, (int)p, w.A, w.ldp, true, w.Z[prev], w.ldp, true, e, st));
         } else {
             e.C2 = w.Z[prev];                  // Psi_{k-1}
@@ -633,10 +778,16 @@ cpa_status cpa_svt(cpa_handle h, const float *dX, int64_t m, int64_t n, int64_t 
     }
     h->d_out = w.out;
     h->d_coef = w.coef;
-    h->last_L = L;
+    h->last_L = learn ? learn->rule.L_max : L;
     h->have_last = true;
+    h->have_learn = learn != nullptr;
+    h->d_L = learn ? w.Lsel : nullptr;
     return CPA_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 // Reads {theta, r, trace, lambda, status} of the last cpa_svt and its
 // tensor-core error word into the handle's pinned slots (synchronises).
@@ -860,6 +1011,193 @@ cpa_status cpa_svt_host(cpa_handle h, int count, const float *const *hX, int64_t
     }
     CK(cudaStreamWaitEvent(st, h->out_done[(count - 1) & 1], 0));
     if (count >= 2) CK(cudaStreamWaitEvent(st, h->out_done[count & 1], 0));
+    return CPA_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Pointer-form batches: patch-sized members (min(m, n) <= 64, max(m, n) <=
+// 128, L within the batched kernel's limit) in one persistent launch, the
+// others through the single-matrix path one after another on the stream
+// (largest first, so the workspace is sized once).
+
+namespace {
+
+bool patch_sized(int64_t m, int64_t n, int L) {
+    return std::min(m, n) <= 64 && std::max(m, n) <= 128 && L <= batched_max_terms();
+}
+
+cpa_status check_members(int count, const float *const *dX, const int64_t *m, const int64_t *n, const int64_t *ldx,
+                         const cpa_shrink *s, int s_count, float *const *dY, const int64_t *ldy) {
+    if (count < 0 || (count > 0 && (!dX || !m || !n || !ldx || !s || !dY || !ldy)) ||
+        (s_count != 1 && s_count != count))
+        return CPA_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i) {
+        if (validate_matrix(dX[i], m[i], n[i], ldx[i]) != CPA_OK || !dY[i] || ldy[i] < n[i])
+            return CPA_ERR_INVALID_ARG;
+        if (check_shrink(&s[s_count > 1 ? i : 0]) != CPA_OK) return CPA_ERR_INVALID_ARG;
+    }
+    return CPA_OK;
+}
+
+cpa_status ensure_pplan(cpa_ctx *h) {
+    if (!h->pplan) h->pplan = ptr_plan_create(h->device, h->num_sms);
+    return h->pplan ? CPA_OK : CPA_ERR_NO_MEMORY;
+}
+
+std::vector<int> by_size_desc(const std::vector<int> &idx, const int64_t *m, const int64_t *n) {
+    std::vector<int> v = idx;
+    std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
+        const int64_t pa = std::min(m[a], n[a]), pb = std::min(m[b], n[b]);
+        return pa != pb ? pa > pb : std::max(m[a], n[a]) > std::max(m[b], n[b]);
+    });
+    return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+cpa_status cpa_svt_batched(cpa_handle h, int count, const float *const *dX, const int64_t *m, const int64_t *n,
+                           const int64_t *ldx, const cpa_shrink *s, int s_count, const int *L, int L0,
+                           const double *lambda, int prec, float *const *dY, const int64_t *ldy, void *stream) {
+    if (!h) return CPA_ERR_INVALID_ARG;
+    cpa_status r = check_members(count, dX, m, n, ldx, s, s_count, dY, ldy);
+    if (r != CPA_OK) return r;
+    if (prec < CPA_FP32 || prec > CPA_BF16X3) return CPA_ERR_INVALID_ARG;
+    if (prec == CPA_TF32 || (prec != CPA_FP32 && h->cc < 100)) return CPA_ERR_UNSUPPORTED;
+    for (int i = 0; i < count; ++i) {
+        const int Li = L ? L[i] : L0;
+        if (Li < 1 || Li > kMaxTerms || (lambda && !(std::isfinite(lambda[i]))))
+            return CPA_ERR_INVALID_ARG;
+    }
+    if (count == 0) return CPA_OK;
+    if ((r = set_device(h)) != CPA_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int> small, big;
+    for (int i = 0; i < count; ++i) (patch_sized(m[i], n[i], L ? L[i] : L0) ? small : big).push_back(i);
+    if (!small.empty()) {
+        if ((r = ensure_pplan(h)) != CPA_OK) return r;
+        std::vector<PtrItem> items(small.size());
+        std::vector<double> lam(small.size());
+        bool all_given = lambda != nullptr;
+        for (size_t k = 0; k < small.size(); ++k) {
+            const int i = small[k];
+            items[k] = PtrItem{dX[i], dY[i], ldx[i], ldy[i], (int)m[i], (int)n[i], L ? L[i] : L0,
+                               to_params(&s[s_count > 1 ? i : 0])};
+            if (lambda) {
+                lam[k] = lambda[i];
+                if (!(lambda[i] > 0.0)) all_given = false;
+            }
+        }
+        // the batched kernel takes bounds for all members or none
+        if ((r = ptr_plan_run(h->pplan, (int)small.size(), items.data(), all_given ? lam.data() : nullptr, prec,
+                              nullptr, nullptr, st)) != CPA_OK)
+            return r;
+    }
+    for (int i : by_size_desc(big, m, n)) {
+        r = svt_impl(h, dX[i], m[i], n[i], ldx[i], &s[s_count > 1 ? i : 0], L ? L[i] : L0,
+                     lambda ? lambda[i] : 0.0, prec, nullptr, dY[i], ldy[i], stream, nullptr);
+        if (r != CPA_OK) return r;
+    }
+    return CPA_OK;
+}
+
+cpa_status cpa_serve_learned(cpa_handle h, cpa_mlp net, int count, const float *const *dX, const int64_t *m,
+                             const int64_t *n, const int64_t *ldx, const cpa_shrink *s, int s_count,
+                             const cpa_learn_rule *rule, int prec, float *const *dY, const int64_t *ldy,
+                             void *stream) {
+    if (!h || !net || !rule) return CPA_ERR_INVALID_ARG;
+    cpa_status r = check_members(count, dX, m, n, ldx, s, s_count, dY, ldy);
+    if (r != CPA_OK) return r;
+    const cpa_learn_rule &ru = *rule;
+    if (!(ru.L_scale > 0.0) || !std::isfinite(ru.L_scale) || !(ru.margin >= 0.0) || !std::isfinite(ru.margin) ||
+        ru.L_min < 1 || ru.L_max < ru.L_min || ru.L_max > kMaxTerms || ru.L_fallback < 1 || ru.L_fallback > ru.L_max)
+        return CPA_ERR_INVALID_ARG;
+    if (prec < CPA_FP32 || prec > CPA_BF16X3 || prec == CPA_TF32) return CPA_ERR_UNSUPPORTED;
+    int dims[4], dev = -1;
+    const float *P = mlp_device_params(net, dims, &dev);
+    if (!P || dims[0] != 12 || dims[1] != 64 || dims[2] != 64 || dims[3] != 2 || dev != h->device)
+        return CPA_ERR_INVALID_ARG;
+    if (h->series != CPA_SERIES_FORWARD) return CPA_ERR_UNSUPPORTED;
+    if ((r = set_device(h)) != CPA_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    h->serve_small.clear();
+    h->serve_big.clear();
+    for (int i = 0; i < count; ++i) (patch_sized(m[i], n[i], 1) ? h->serve_small : h->serve_big).push_back(i);
+    if (!h->serve_small.empty()) {
+        if ((r = ensure_pplan(h)) != CPA_OK) return r;
+        std::vector<PtrItem> items(h->serve_small.size());
+        for (size_t k = 0; k < items.size(); ++k) {
+            const int i = h->serve_small[k];
+            items[k] = PtrItem{dX[i], dY[i], ldx[i], ldy[i], (int)m[i], (int)n[i], 1,
+                               to_params(&s[s_count > 1 ? i : 0])};
+        }
+        if ((r = ptr_plan_run(h->pplan, (int)items.size(), items.data(), nullptr, prec, P, rule, st)) != CPA_OK)
+            return r;
+    }
+    const int nb = (int)h->serve_big.size();
+    if (nb > h->big_cap) {
+        CK(cudaStreamSynchronize(st));
+        if (h->d_big_L) cudaFree(h->d_big_L);
+        if (h->d_big_lam) cudaFree(h->d_big_lam);
+        h->d_big_L = nullptr;
+        h->d_big_lam = nullptr;
+        h->big_cap = 0;
+        if (cudaMalloc(&h->d_big_L, sizeof(int) * 2 * nb) != cudaSuccess ||
+            cudaMalloc(&h->d_big_lam, sizeof(double) * nb) != cudaSuccess) {
+            cudaGetLastError();
+            return CPA_ERR_NO_MEMORY;
+        }
+        h->big_cap = nb;
+    }
+    h->serve_big = by_size_desc(h->serve_big, m, n);
+    LearnCall lc{P, ru};
+    for (int k = 0; k < nb; ++k) {
+        const int i = h->serve_big[k];
+        r = svt_impl(h, dX[i], m[i], n[i], ldx[i], &s[s_count > 1 ? i : 0], ru.L_max, 0.0, prec, nullptr, dY[i],
+                     ldy[i], stream, &lc);
+        if (r != CPA_OK) return r;
+        // keep this member's choice: the next call reuses the workspace
+        CK(cudaMemcpyAsync(h->d_big_L + 2 * k, h->d_L, 2 * sizeof(int), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(h->d_big_lam + k, h->d_out + 3, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    h->have_learn = false;
+    return CPA_OK;
+}
+
+cpa_status cpa_serve_read(cpa_handle h, int count, int *host_L, double *host_lambda, int *host_fallbacks,
+                          void *stream) {
+    if (!h || count != (int)(h->serve_small.size() + h->serve_big.size())) return CPA_ERR_INVALID_ARG;
+    cpa_status r = set_device(h);
+    if (r != CPA_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ns = (int)h->serve_small.size(), nb = (int)h->serve_big.size();
+    std::vector<int> sL(ns), bL(2 * nb);
+    std::vector<double> sl(ns), bl(nb);
+    int nfb_small = 0;
+    if (ns) {
+        CK(cudaMemcpyAsync(sL.data(), ptr_plan_orders(h->pplan), sizeof(int) * ns, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(sl.data(), ptr_plan_lambdas(h->pplan), sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&nfb_small, ptr_plan_fallbacks(h->pplan), sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
+    if (nb) {
+        CK(cudaMemcpyAsync(bL.data(), h->d_big_L, sizeof(int) * 2 * nb, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(bl.data(), h->d_big_lam, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    int nfb = nfb_small;
+    for (int k = 0; k < ns; ++k) {
+        if (host_L) host_L[h->serve_small[k]] = sL[k];
+        if (host_lambda) host_lambda[h->serve_small[k]] = sl[k];
+    }
+    for (int k = 0; k < nb; ++k) {
+        if (host_L) host_L[h->serve_big[k]] = bL[2 * k];
+        if (host_lambda) host_lambda[h->serve_big[k]] = bl[k];
+        nfb += bL[2 * k + 1];
+    }
+    if (host_fallbacks) *host_fallbacks = nfb;
     return CPA_OK;
 }
 

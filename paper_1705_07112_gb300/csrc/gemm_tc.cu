@@ -234,6 +234,9 @@ struct MultiStep {
     // path: it then ends only by the limit, every CTA stops after its step)
     long long wait_cycles = kDefaultWaitCycles;
     int stall = 0;
+    // number of terms chosen on the device (learned order): the launch runs
+    // the steps k_first <= k < min(k_end, *L_dev); null: k_end as given
+    const int *L_dev = nullptr;
 };
 
 __device__ __forceinline__ void fence_proxy_async_global() {
@@ -701,6 +704,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
+    // last step + 1 (the terms of a learned order are read from the device)
+    const int k_end = ms.L_dev ? max(ms.k_first, min(ms.k_end, __ldg(ms.L_dev))) : ms.k_end;
     const int sym = e.symmetric_upper;
     const int ntiles = count_tiles(tiles_m, tiles_n, sym, BN);
     const int kb_per = (K + BK - 1) / BK;
@@ -742,7 +747,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             int stage = 0;
             uint32_t phase = 0, sphase = 0;
             uint32_t armed_mask = 0, armed_phase = 0;   // per stage: armed at least once / phase it was armed in
-            for (int k = ms.k_first; k < ms.k_end && !*abort_flag; ++k) {
+            for (int k = ms.k_first; k < k_end && !*abort_flag; ++k) {
                 if (ms.multi && k > ms.k_first) {
                     // the previous step's outputs are complete in every CTA
                     if (!mbar_wait(stepbar, sphase, abort_flag)) break;
@@ -797,7 +802,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t tphase[2] = {0, 0};
             int local = 0;
             bool ok = true;
-            for (int k = ms.k_first; k < ms.k_end && ok && !*abort_flag; ++k) {
+            for (int k = ms.k_first; k < k_end && ok && !*abort_flag; ++k) {
                 for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++local) {
                     const int buf = local & 1;
                     if (!mbar_wait(&tempty[buf], tphase[buf] ^ 1, abort_flag)) {
@@ -845,7 +850,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int local = 0;
         unsigned int target = 0;
         bool alive = true;
-        for (int k = ms.k_first; k < ms.k_end && alive; ++k) {
+        for (int k = ms.k_first; k < k_end && alive; ++k) {
             Epilogue es_e = e;
             const int par = ms.multi ? (k & 1) : 0;
             bool final_to_h = false;
@@ -875,7 +880,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // resident state: slot par takes Psi_k over Psi_{k-2}, slot par^1
             // holds Psi_{k-1}, then H
             const bool res = BN <= 64 && ms.multi && ms.resident;
-            const bool first = (k == ms.k_first), last = (k + 1 == ms.k_end);
+            const bool first = (k == ms.k_first), last = (k + 1 == k_end);
             const uint32_t sC = (uint32_t)(2 * BN + par * BN), sC2 = (uint32_t)(2 * BN + (par ^ 1) * BN),
                            sH = (uint32_t)(4 * BN);
             const bool close = res && final_to_h;
@@ -933,7 +938,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[buf]);
             }
-            if (ms.multi && k + 1 < ms.k_end && alive) {
+            if (ms.multi && k + 1 < k_end && alive) {
                 // step k done in this CTA: stores complete and ordered for the
                 // async proxy, then one grid-wide barrier, then the producer
                 // may load step k+1's operands
@@ -1166,7 +1171,7 @@ cudaError_t dispatch_bn(int bn, F f) {
 cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epilogue &e, int k_first, int k_end,
                                float *const z[2], __nv_bfloat16 *const zhi[2], __nv_bfloat16 *const zlo[2],
                                unsigned int *bar, cudaStream_t st, int num_sms, int clenshaw, int L, int *closed,
-                               int kpad, const WaitPolicy &wp) {
+                               int kpad, const WaitPolicy &wp, const int *L_dev) {
     if (closed) *closed = 0;
     if (p <= 0 || k_end <= k_first) return cudaSuccess;
     if (!load_encode()) return cudaErrorNotSupported;
@@ -1180,6 +1185,8 @@ cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epil
     ms.multi = 1;
     ms.wait_cycles = wait_limit(wp);
     ms.stall = wp.stall;
+    ms.L_dev = L_dev;
+    if (L_dev && clenshaw) return cudaErrorInvalidValue;   // Clenshaw's sum runs from the last term down
     ms.k_first = k_first;
     ms.k_end = k_end;
     for (int i = 0; i < 2; ++i) {

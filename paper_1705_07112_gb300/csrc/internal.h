@@ -142,7 +142,8 @@ cudaError_t gemm_tc(int M, int N, int K, const TcOperand &A, const TcOperand &B,
 cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epilogue &e, int k_first, int k_end,
                                float *const z[2], __nv_bfloat16 *const zhi[2], __nv_bfloat16 *const zlo[2],
                                unsigned int *bar, cudaStream_t st, int num_sms, int clenshaw = 0, int L = 0,
-                               int *closed = nullptr, int kpad = 0, const WaitPolicy &wp = WaitPolicy());
+                               int *closed = nullptr, int kpad = 0, const WaitPolicy &wp = WaitPolicy(),
+                               const int *L_dev = nullptr);
 
 // Sparsity-based reduction helpers (sparsify.cu).
 cudaError_t make_transform(int type, int p, float *T, int64_t ld, cudaStream_t st, int num_sms);
@@ -175,9 +176,10 @@ cudaError_t power_bound_persistent(const float *G, int64_t ldg, int p, int iters
                                    double *coef = nullptr, const WaitPolicy &wp = WaitPolicy());
 cudaError_t device_coeffs(const double *lam_dev, double lam_host, int L, const ShrinkParams &s, double *c,
                           cudaStream_t st);
-// A = (2/lambda) G - Id, Z1 = A, H = c0/2 Id + c1 A (FP32).  For the
-// tensor-core path also At = (2/lambda) G as BF16 hi/lo (the operand of every
-// recurrence product; the -Id is applied exactly in the FP32 epilogue) and
+// B_hat = (2/lambda) G - Id: Z1 = B_hat, H = c0/2 Id + c1 B_hat (FP32), and
+// the operand of every recurrence product At = (2/lambda) G without the -Id
+// (the recurrence's epilogue applies it exactly): in A as FP32 for the
+// CUDA-core path, as BF16 hi/lo in Athi/Atlo for the tensor-core path, with
 // Z1 as BF16 hi/lo; their columns p .. ldb-1, and those of the ring's other
 // BF16 slot Z0hi/Z0lo when given, are set to zero.
 cudaError_t shift_init(const float *G, int64_t ldg, int p, const double *lam, const double *c, int L, float *A,
@@ -194,6 +196,45 @@ cudaError_t split_sym_lower(const float *S, int p, int64_t lds, __nv_bfloat16 *h
                             cudaStream_t st);
 cudaError_t check_finite(const float *X, int64_t rows, int64_t cols, int64_t ldx, int *flag, cudaStream_t st,
                          int num_sms);
+
+// Learned choice of (Lambda_max, L) for one matrix (learned.cu): features of
+// the Gram matrix G (p x p, q the other side), the predictor network P
+// (12 -> 64 -> 64 -> 2), the decision rule of cpa_svt_batched_learned and
+// the coefficients of the chosen L on [0, Lambda_max] (c_k = 0 for
+// L <= k < L_max).  out = {theta, r, trace, lambda, status}, L_out = {L,
+// fallback}.  feat_only: write the 12 features and theta_4 and stop.
+// v0, v1, u0, u1: round_up(p, 4) floats each; acc: learn_scratch_doubles
+// (with tabg after it: 2 L_max + 8 doubles).
+size_t learn_scratch_doubles(int L_max);
+cudaError_t learn_bound(const float *G, int64_t ldg, int p, int q, const ShrinkParams &sp, const float *P,
+                        double L_scale, double margin, int L_min, int L_max, int L_fallback, int use_lambda,
+                        int feat_only, int iters, float *v0, float *v1, float *u0, float *u1, double *acc,
+                        double *tabg, unsigned int *bar, int *err, double *out, int *L_out, float *feat,
+                        double *theta_out, double *coef, cudaStream_t st, int num_sms, const WaitPolicy &wp);
+
+// Pointer form of the batched launch (batched.cu).  One member: device X
+// (m x n, row stride ldx) and Y (row stride ldy), order L, its shrinkage.
+// Members must satisfy min(m, n) <= 64, max(m, n) <= 128, L <=
+// batched_max_terms().  lambda_host: NULL (bounds computed on the device)
+// or count values.  net != NULL: the learned choice with `rule` (orders
+// clamped to batched_max_terms()).
+struct PtrItem {
+    const float *x;
+    float *y;
+    int64_t ldx, ldy;
+    int m, n, L;
+    ShrinkParams shrink;
+};
+struct PtrPlan;
+PtrPlan *ptr_plan_create(int device, int num_sms);
+void ptr_plan_destroy(PtrPlan *pp);
+cpa_status ptr_plan_run(PtrPlan *pp, int count, const PtrItem *items, const double *lambda_host, int prec,
+                        const float *net, const cpa_learn_rule *rule, cudaStream_t st);
+const double *ptr_plan_lambdas(const PtrPlan *pp);
+const int *ptr_plan_orders(const PtrPlan *pp);
+const int *ptr_plan_fallbacks(const PtrPlan *pp);
+const int *ptr_plan_status(const PtrPlan *pp);
+int batched_max_terms();
 
 // Device view of a predictor network: its parameter array, widths
 // {in, h1, h2, out} and device (nullptr for a null handle).

@@ -203,8 +203,10 @@ __device__ __forceinline__ void put_split(__nv_bfloat16 *hi, __nv_bfloat16 *lo, 
     if (lo) lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-// A = (2/lambda) G - Id;  Z1 = A;  H = c0/2 Id + c1 A  (the initial sum of
-// Algorithm 1).  Tensor-core path: At = (2/lambda) G and Z1 as BF16 hi/lo.
+// B_hat = (2/lambda) G - Id;  Z1 = B_hat;  H = c0/2 Id + c1 B_hat  (the
+// initial sum of Algorithm 1).  The product operand is At = (2/lambda) G
+// without the -Id, which the recurrence's epilogue applies exactly: FP32 in
+// A (CUDA-core path), BF16 hi/lo (tensor-core path); Z1 also as BF16 hi/lo.
 // Clenshaw's sum (L >= 3): Z1 = b_{L-2} = c_{L-2} Id + 2 c_{L-1} A instead.
 __global__ void shift_kernel(const float *__restrict__ G, int64_t ldg, int p, const double *lam,
                              const double *c, int L, float *A, float *Z1, float *H, int64_t ld,
@@ -230,7 +232,7 @@ __global__ void shift_kernel(const float *__restrict__ G, int64_t ldg, int p, co
         float at = s * G[(int64_t)i * ldg + j];
         float a = at - (i == j ? 1.f : 0.f);
         const float z1 = za * a + (i == j ? zc : 0.f);
-        if (A) A[(int64_t)i * ld + j] = a;
+        if (A) A[(int64_t)i * ld + j] = at;
         if (Z1) Z1[(int64_t)i * ld + j] = z1;
         H[(int64_t)i * ld + j] = c1 * a + (i == j ? c0h : 0.f);
         if (Athi) put_split(Athi, Atlo, (int64_t)i * ldb + j, at);

@@ -24,6 +24,14 @@ Laboratory video of Section V, are not available; these stand in for them):
 * ``block_completion`` Section V-E's synthetic matrix J - blkdiag(0.5 1 1^T, n)
                        (rank n, entries 0.5 and 1) with a random x % of its
                        entries set to zero and marked unobserved.
+* ``served_mix``       the learned predictor's serving mix: half patch-group
+                       shapes (64 x U{40..80}), half sides log-uniform in
+                       [64, 2048]; rank-r signal (unit-norm Gaussian factor
+                       columns, singular values g_i times the noise edge
+                       s (sqrt m + sqrt n), g_i log-uniform in [1.5, 40]) plus
+                       N(0, s^2), s log-uniform in [0.01, 0.2]; hard, soft or
+                       weighted soft thresholding (a third each) at f times
+                       the noise edge, f uniform in [1.2, 3].
 """
 from __future__ import annotations
 
@@ -191,3 +199,62 @@ def block_completion(seed_index=0, size=1000, rank=100, frac_zero=0.10):
     mask = mask.reshape(size, size)
     I = np.where(mask == 1, D, 0.0)
     return D.astype(np.float32), I.astype(np.float32), mask
+
+
+# ---------------------------------------------------------------------------
+# The learned predictor's serving mix (mixed sizes and kinds)
+
+SERVED_CONFIG = 5
+
+
+@dataclass
+class ServedMatrix:
+    X: np.ndarray          # float32 m x n
+    shrink: ShrinkSpec
+    family: int            # 0: patch-group shape, 1: log-uniform sides
+    rank: int
+    sigma: float           # noise standard deviation
+
+
+def served_matrix(rng: np.random.Generator, family: int) -> ServedMatrix:
+    """One matrix of the serving mix (recipe in the module docstring)."""
+    if family == 0:
+        m, n = 64, int(rng.integers(40, 81))
+        r = int(rng.integers(1, 9))
+    else:
+        lo, hi = math.log(64.0), math.log(2048.0)
+        m = int(round(math.exp(rng.uniform(lo, hi))))
+        n = int(round(math.exp(rng.uniform(lo, hi))))
+        r = int(rng.integers(1, min(50, min(m, n) // 4) + 1))
+    s = float(math.exp(rng.uniform(math.log(0.01), math.log(0.2))))
+    edge = s * (math.sqrt(m) + math.sqrt(n))
+    g = np.sort(np.exp(rng.uniform(math.log(1.5), math.log(40.0), size=r)))[::-1]
+    A = rng.standard_normal((m, r))
+    A /= np.linalg.norm(A, axis=0)
+    B = rng.standard_normal((r, n))
+    B /= np.linalg.norm(B, axis=1)[:, None]
+    X = (A * (g * edge)) @ B + s * rng.standard_normal((m, n))
+    f = float(rng.uniform(1.2, 3.0))
+    kind = int(rng.integers(0, 3))
+    if kind == 0:
+        spec = ShrinkSpec(HARD, f * edge)
+    elif kind == 1:
+        spec = ShrinkSpec(SOFT, f * edge)
+    else:
+        noise = max(m, n) * s * s
+        c = f * edge * s * math.sqrt(min(m, n) + 2.0 * math.sqrt(m * n))
+        spec = ShrinkSpec(WSOFT, 0.0, c, 1e-8, noise)
+    return ServedMatrix(X.astype(np.float32), spec, family, r, s)
+
+
+def served_one(seed_index: int, i: int, patch_fraction: float = 0.5) -> ServedMatrix:
+    """Matrix i of the serving mix of seed_index; each matrix has its own
+    generator, so any one can be regenerated alone."""
+    rng = rng_for(SERVED_CONFIG, seed_index * 1000003 + i)
+    family = 0 if rng.random() < patch_fraction else 1
+    return served_matrix(rng, family)
+
+
+def served_mix(count: int, seed_index: int = 0, patch_fraction: float = 0.5) -> list:
+    """`count` matrices of the serving mix, seeded by seed_index."""
+    return [served_one(seed_index, i, patch_fraction) for i in range(count)]

@@ -86,7 +86,7 @@ def test_batched_edge_shapes_given_lambda(cpa, handle, prec, kind):
             specs.append(O.Shrink(O.WSOFT, 0.0, c=0.05 * sig * sig, eps=1e-8, noise=0.01 * sig * sig))
     Ls = [1, 2, 3, 24, 24, 24, 17, 17, 30, 30, 5, 24, 24, 9, 24]
     plan = cpa.BatchPlan(handle, shapes, L=Ls)
-    Y = cpa.cpa_svt_batched(handle, plan, pack(mats), [dict(kind=s.kind, tau=s.tau, c=s.c, eps=s.eps,
+    Y = cpa.cpa_svt_batched_plan(handle, plan, pack(mats), [dict(kind=s.kind, tau=s.tau, c=s.c, eps=s.eps,
                                                             noise=s.noise) for s in specs],
                             lambdas=torch.tensor(lams, dtype=torch.float64, device="cuda"), prec=prec)
     torch.cuda.synchronize()
@@ -103,7 +103,7 @@ def test_batched_computed_lambda(cpa, handle, prec):
     shapes = [m.shape for m in mats]
     plan = cpa.BatchPlan(handle, shapes, L0=12)
     s = O.Shrink(O.SOFT, 0.5)
-    Y = cpa.cpa_svt_batched(handle, plan, pack(mats), dict(kind=O.SOFT, tau=0.5), prec=prec)
+    Y = cpa.cpa_svt_batched_plan(handle, plan, pack(mats), dict(kind=O.SOFT, tau=0.5), prec=prec)
     torch.cuda.synchronize()
     lam_gpu = plan.lambdas()
     for i, (Xm, Ym) in enumerate(zip(mats, unpack(Y, shapes))):
@@ -123,7 +123,7 @@ def test_patch_groups_full_batch_sampled(cpa, handle, prec):
     specs = [dict(kind=spec.kind, tau=spec.tau, c=spec.c, eps=spec.eps,
                   noise=inputs.patch_group_noise(sh, sigma)) for sh in shapes]
     plan = cpa.BatchPlan(handle, shapes, L0=L)
-    Y = cpa.cpa_svt_batched(handle, plan, pack(mats), specs, prec=prec)
+    Y = cpa.cpa_svt_batched_plan(handle, plan, pack(mats), specs, prec=prec)
     torch.cuda.synchronize()
     lam_gpu = plan.lambdas()
     ys = unpack(Y, shapes)
@@ -143,3 +143,69 @@ def test_batch_plan_argument_errors(cpa, handle):
         cpa.BatchPlan(handle, [(64, 129)])         # max(m, n) > 128
     with pytest.raises(cpa.CpaError):
         cpa.BatchPlan(handle, [(8, 8)], L0=0)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_batched_long_series(cpa, handle, prec):
+    """Orders above 128 (up to the kernel's limit of 1024): the coefficient
+    sums run in the free Psi buffers; every member against the oracle."""
+    import torch
+    mats = [m.astype(np.float32).astype(np.float64) for m in edge_batch(seed=11)][:8]
+    shapes = [m.shape for m in mats]
+    Ls = [129, 200, 333, 512, 700, 1000, 1024, 300]
+    specs = []
+    for m in mats:
+        sig = np.sqrt(oracle_lambda(m) / 1.01)
+        specs.append(dict(kind=O.SOFT, tau=0.2 * sig))
+    plan = cpa.BatchPlan(handle, shapes, L=Ls)
+    Y = cpa.cpa_svt_batched_plan(handle, plan, pack(mats), specs, prec=prec)
+    torch.cuda.synchronize()
+    lam_gpu = plan.lambdas()
+    for i, (Xm, y) in enumerate(zip(mats, unpack(Y, shapes))):
+        s = O.Shrink(O.SOFT, specs[i]["tau"])
+        ref = O.cpa(Xm, s, Ls[i], float(lam_gpu[i]))
+        # FP32 arithmetic over up to 1024 terms: the recurrence's rounding
+        # grows with the order, checked against the same 1e-5 bar
+        assert rel(y, ref) <= TOL[prec], (i, Xm.shape, Ls[i], rel(y, ref))
+    with pytest.raises(cpa.CpaError):
+        cpa.BatchPlan(handle, [(8, 8)], L0=1025)
+    plan.close()
+
+
+def test_pointer_form_matches_plan_and_oracle(cpa, handle):
+    """cpa_svt_batched (per-member device pointers, shapes, strides and
+    orders): patch-sized members (one persistent launch) give exactly what
+    the plan form gives; larger members (the single-matrix path) match
+    the oracle; members are strided views of larger buffers."""
+    import torch
+    rng = np.random.default_rng(21)
+    shapes = [(64, 40), (64, 80), (30, 100), (200, 150), (90, 300), (64, 64), (1, 9)]
+    Ls = [24, 50, 10, 30, 17, 200, 5]
+    mats, Xs, Ys = [], [], []
+    for (m, n) in shapes:
+        r = max(1, min(m, n) // 6)
+        A = (rng.standard_normal((m, r)) @ rng.standard_normal((r, n)) + 0.05 * rng.standard_normal((m, n)))
+        A = A.astype(np.float32)
+        mats.append(A.astype(np.float64))
+        big = torch.zeros((m, n + 5), device="cuda")
+        big[:, :n] = torch.from_numpy(A).cuda()
+        Xs.append(big[:, :n])
+        Ys.append(torch.full((m, n + 3), -3.0, device="cuda")[:, :n])
+    lams = [oracle_lambda(A) for A in mats]
+    specs = [dict(kind=O.SOFT, tau=0.2 * np.sqrt(l / 1.01)) for l in lams]
+    for prec, tol in (("bf16x3", TOL["bf16x3"]), ("fp32", TOL["fp32"])):
+        members = cpa.MemberList(Xs, Ys, specs)
+        cpa.cpa_svt_batched(handle, members, L=Ls, lambdas=lams, prec=prec)
+        torch.cuda.synchronize()
+        small = [i for i, (m, n) in enumerate(shapes) if min(m, n) <= 64 and max(m, n) <= 128]
+        plan = cpa.BatchPlan(handle, [shapes[i] for i in small], L=[Ls[i] for i in small])
+        lam_t = torch.tensor([lams[i] for i in small], dtype=torch.float64, device="cuda")
+        Yp = cpa.cpa_svt_batched_plan(handle, plan, pack([mats[i] for i in small]), [specs[i] for i in small],
+                                      lambdas=lam_t, prec=prec)
+        torch.cuda.synchronize()
+        for k, y in zip(small, unpack(Yp, [shapes[i] for i in small])):
+            assert np.array_equal(Ys[k].cpu().numpy().astype(np.float64), y), (prec, shapes[k])
+        for i, A in enumerate(mats):
+            ref = O.cpa(A, O.Shrink(O.SOFT, specs[i]["tau"]), Ls[i], lams[i])
+            assert rel(Ys[i].cpu().numpy().astype(np.float64), ref) <= tol, (prec, shapes[i], rel(Ys[i].cpu().numpy(), ref))
+        plan.close()

@@ -84,12 +84,19 @@ def test_decision_rule_matches_explicit_choices(lib, use_lambda):
                                      L_fallback=L_fb, use_lambda=use_lambda, margin=margin, prec="bf16x3")
     Ls, nfb = lib.cpa_batch_read_choices(plan)
     assert np.array_equal(Ls, L_exp)
-    assert nfb == int(np.sum(Lf > L_max))
-    ref_plan = lib.BatchPlan(h, shapes, L=[int(v) for v in L_exp])
     lam = None
+    clamped = np.zeros(len(mats), dtype=bool)
     if use_lambda:
-        lam = torch.from_numpy(th * np.exp(np.maximum(y[:, 0], 0.0)) * (1.0 + margin)).cuda()
-    Y2 = lib.cpa_svt_batched(h, ref_plan, X, sd, lambdas=lam, prec="bf16x3")
+        # the predicted bound, never below (theta_4 + r_4)(1 + margin)
+        r4 = np.array([D.O.lambda_bound(m.astype(np.float64), 3, 0.0,
+                                        D.O.start_vector(D.START_SEED, min(m.shape)))["resid"] for m in mats])
+        lp = th * np.exp(np.maximum(y[:, 0], 0.0)) * (1.0 + margin)
+        fl = (th + r4) * (1.0 + margin)
+        clamped = lp < fl
+        lam = torch.from_numpy(np.maximum(lp, fl)).cuda()
+    assert nfb == int(np.sum((Lf > L_max) | clamped))
+    ref_plan = lib.BatchPlan(h, shapes, L=[int(v) for v in L_exp])
+    Y2 = lib.cpa_svt_batched_plan(h, ref_plan, X, sd, lambdas=lam, prec="bf16x3")
     torch.cuda.synchronize()
     if use_lambda:   # Lambda_max rounded on the device vs the host: ulps
         assert torch.allclose(Y1, Y2, rtol=1e-5, atol=1e-6)
@@ -99,7 +106,7 @@ def test_decision_rule_matches_explicit_choices(lib, use_lambda):
     with pytest.raises(lib.CpaError):
         lib.cpa_svt_batched_learned(h, plan, net, X, sd, L_scale=0.0)
     with pytest.raises(lib.CpaError):
-        lib.cpa_svt_batched_learned(h, plan, net, X, sd, L_max=129)
+        lib.cpa_svt_batched_learned(h, plan, net, X, sd, L_max=1025)
     other = lib.MLP((12, 32, 64, 2), seed=1)
     with pytest.raises(lib.CpaError):
         lib.cpa_svt_batched_learned(h, plan, other, X, sd)
@@ -172,9 +179,9 @@ def test_learned_predictor_gains_over_fixed_order(lib):
     Ls, nfb = lib.cpa_batch_read_choices(lplan)
     L_eq = int(math.ceil(Ls.mean()))
     fplan = lib.BatchPlan(h, shapes, L0=L_eq)
-    err_f = errors(lib.cpa_svt_batched(h, fplan, X, specs, prec="bf16x3"))
+    err_f = errors(lib.cpa_svt_batched_plan(h, fplan, X, specs, prec="bf16x3"))
     bplan = lib.BatchPlan(h, shapes, L0=50)
-    err_b = errors(lib.cpa_svt_batched(h, bplan, X, specs, prec="bf16x3"))
+    err_b = errors(lib.cpa_svt_batched_plan(h, bplan, X, specs, prec="bf16x3"))
     ok_l, ok_f, ok_b = (float(np.mean(e <= D.TOL)) for e in (err_l, err_f, err_b))
 
     # throughput on the evaluation set tiled 10 times (6,000 matrices)
@@ -197,7 +204,7 @@ def test_learned_predictor_gains_over_fixed_order(lib):
         return e0.elapsed_time(e1) / reps / 1e3
 
     t_l = timed(lambda: lib.cpa_svt_batched_learned(h, lp, net, Xt, tiled_s, L_scale=L_scale, prec="bf16x3"))
-    t_b = timed(lambda: lib.cpa_svt_batched(h, bp, Xt, tiled_s, prec="bf16x3"))
+    t_b = timed(lambda: lib.cpa_svt_batched_plan(h, bp, Xt, tiled_s, prec="bf16x3"))
     good_l = ok_l * len(tiled_m) / t_l
     good_b = ok_b * len(tiled_m) / t_b
     print("\nlearned: L_scale %.2f, mean L %.1f, fallbacks %d, %.1f%% within 1e-2, %.0f matrices/s, %.0f good/s" %

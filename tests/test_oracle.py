@@ -482,3 +482,22 @@ def test_block_vector_form_matches_the_c_oracle():
     # X T^T H(Phi_) T, row i = (T^T H T x_i)^T
     Yb = (T.T @ O.filter_block(Phib, s, 11, lam, T @ X.T)).T
     assert np.allclose(Yb, Y, rtol=0, atol=1e-11 * np.abs(Y).max())
+
+
+def test_lapack_routes_match_the_jacobi_oracle():
+    """singular_values and shrink_exact_lapack (LAPACK as the decomposition
+    step) against the oracle's own one-sided Jacobi SVD and its exact
+    shrinkage, and spectral_errors against the error of the dense FP64
+    Algorithm 1 measured directly."""
+    rng = np.random.default_rng(23)
+    for shape in [(30, 17), (17, 30), (12, 12)]:
+        X = rng.standard_normal(shape)
+        _, _, sj = O.svd_jacobi(X if shape[0] >= shape[1] else X.T)
+        assert np.allclose(O.singular_values(X), np.sort(sj)[::-1], rtol=1e-12, atol=1e-13)
+        for s in shrinks():
+            assert np.allclose(O.shrink_exact_lapack(X, s), O.shrink_exact(X, s), atol=1e-11)
+            lam = 1.03 * O.singular_values(X)[0] ** 2
+            want = [np.linalg.norm(O.cpa(X, s, a, lam) - O.shrink_exact(X, s)) /
+                    np.linalg.norm(O.shrink_exact(X, s)) for a in (1, 2, 5, 17)]
+            got = O.spectral_errors(O.singular_values(X), s, lam, [1, 2, 5, 17])
+            assert np.allclose(got, want, rtol=1e-8, atol=1e-13), (s, got, want)
