@@ -244,14 +244,16 @@ __global__ void __launch_bounds__(kThreads) learn_bound_kernel(
     for (int sidx = 0; sidx <= 4; ++sidx) {
         const float *u = (sidx & 1) ? u1 : u0;
         float *un = (sidx & 1) ? u0 : u1;
+        // the previous step's vector and norm are complete in every block
+        lgrid_barrier(bar, target, err, wait);
         const double nin = __ldcg(&acc[kUn + sidx]);
         const float sc = sidx == 0 ? 1.f : (nin > 0.0 ? __frcp_rn(__fsqrt_rn((float)nin)) : 0.f);
         if (stage) {
             const float4 *src = reinterpret_cast<const float4 *>(u);
             float4 *dst = reinterpret_cast<float4 *>(vs);
             for (int i = threadIdx.x; i < (p4 >> 2); i += kThreads) dst[i] = __ldcg(src + i);
+            __syncthreads();
         }
-        lgrid_barrier(bar, target, err, wait);   // staging complete; previous step's norm summed
         const float *usrc = stage ? vs : u;
         float pa = 0.f, pb = 0.f;
         for (int row = gwarp; row < p; row += nwarps) {
