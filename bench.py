@@ -42,6 +42,9 @@ L2_BYTES = 129 * 1024 * 1024
 # drop an entry when its kernel changes
 NCU_TRAFFIC = {("rpca_frame", "bf16"): 8.63616e6 + 0.814336e6,
                ("video_background", "bf16"): 8.04469e9 + 4.811779e9}
+# tensor-pipe utilisation (%) of the dominant kernel, from the committed ncu
+# summaries under profiles/; drop an entry when its kernel changes
+NCU_TENSOR_PIPE = {}
 SEED = 0x1705071120000000
 
 
@@ -234,6 +237,8 @@ def run_reference(args, world, rank):
         return 0
     if args.workload == "patch_groups":
         return run_reference_batched(args, world)
+    if args.workload == "served_mix":
+        return run_reference_served(args, world)
     w = make_workload(args.workload)
     m, n = w.X.shape
     rows = args.ref_rows
@@ -259,6 +264,49 @@ def run_reference(args, world, rank):
     if args.workload == "block_completion":
         line["cpu_baseline"]["sample"] += ("; the shrinkage step of one completion ADMM iteration (the 2-D DCT "
                                            "products and elementwise updates not counted)")
+    print(json.dumps(line))
+    return 0
+
+
+def _served_exact_only(a):
+    seed_index, i = a
+    import oracle as O
+    from paper_1705_07112_gb300 import inputs
+    sm = inputs.served_one(seed_index, i)
+    sp = sm.shrink
+    O.shrink_exact_lapack(sm.X.astype(np.float64), O.Shrink(sp.kind, sp.tau, sp.c, sp.eps, sp.noise))
+    return 0
+
+
+def run_reference_served(args, world):
+    """The oracle's exact shrinkage (LAPACK SVD as the decomposition step:
+    no approximation, so every result is within the 1e-3 target) on the
+    host cores, one spawn worker per core, single-threaded BLAS; each step
+    a fresh seeded sample of the served mix."""
+    import multiprocessing as mp
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    ncpu = os.cpu_count() or 1
+    per_step = args.ref_served
+    times = []
+    with mp.get_context("spawn").Pool(ncpu) as pool:
+        for it in range(args.warmup + args.steps):
+            sample = served_sample(args.served, per_step, seed=1000 + it)
+            t0 = time.perf_counter()
+            pool.map(_served_exact_only, [(0, int(i)) for i in sample], chunksize=1)
+            if it >= args.warmup:
+                times.append(time.perf_counter() - t0)
+    value = args.steps * per_step / sum(times)
+    unit = "matrices/s within 1e-3"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "served_mix_%d_sides64-2048_half_patch_groups" % args.served},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": ncpu, "kind": "oracle",
+                             "sample": "%d matrices of the served mix per step (uniform sample), the oracle's "
+                                       "exact shrinkage through LAPACK's SVD, %d single-thread workers"
+                                       % (per_step, ncpu)},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
@@ -301,6 +349,55 @@ def workload_config(w, args, reference=False):
         cfg["cuda_graph"] = not args.no_graph
         cfg["series"] = args.series
     return cfg
+
+
+# --------------------------------------------------------------------------- served mix (CPU leg)
+#
+# The headline workload's CPU leg: the oracle's exact shrinkage (LAPACK SVD
+# as its decomposition step) of a sample of the served matrices, timed on
+# the host cores; the same exact results judge both GPU arms' outputs, and
+# the oracle's spectra give each fixed order's FP64 error for choosing the
+# plain arm's order.
+
+SERVED_TOL = 1e-3
+LADDER = [32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024]
+
+
+def _served_exact_job(a):
+    """(exact shrinkage, singular values, 20-step power bound) of matrix i
+    of the serving mix of seed `seed_index` (oracle; runs in a worker)."""
+    seed_index, i = a
+    import oracle as O
+    from paper_1705_07112_gb300 import inputs
+    sm = inputs.served_one(seed_index, i)
+    X = sm.X.astype(np.float64)
+    sp = sm.shrink
+    s = O.Shrink(sp.kind, sp.tau, sp.c, sp.eps, sp.noise)
+    t0 = time.perf_counter()
+    Y = O.shrink_exact_lapack(X, s)
+    dt = time.perf_counter() - t0
+    sv = O.singular_values(X)
+    lam = O.lambda_bound(X, 20, 0.01, O.start_vector(SEED, min(X.shape)))["lam"]
+    errs = O.spectral_errors(sv, s, lam, LADDER)
+    return Y.astype(np.float32), errs, dt
+
+
+def served_oracle(seed_index, sample, procs):
+    """Exact results for the sample in a spawn pool of `procs` single-threaded
+    workers; returns (results, wall seconds)."""
+    import multiprocessing as mp
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(_served_exact_job, [(seed_index, int(i)) for i in sample], chunksize=1)
+    return res, time.perf_counter() - t0
+
+
+def served_sample(count, k, seed=11):
+    """A seeded uniform sample of k member indices (without replacement)."""
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(count, size=min(k, count), replace=False))
 
 
 # --------------------------------------------------------------------------- GPU arm
@@ -639,7 +736,207 @@ def run_gpu_completion(args, world, rank, local):
     return 0
 
 
+def run_gpu_served(args, world, rank, local):
+    """The learned predictor's serving mix (5,000 matrices, half patch-group
+    shapes, half sides log-uniform in [64, 2048], hard / soft / weighted
+    soft): learned (Lambda_max, L) with BF16 split-precision tensor-core
+    products against plain FP32 CPA at a fixed order, on the same matrices.
+    One step = the whole batch through one arm.  Each arm's outputs on a
+    sample are judged against the oracle's exact shrinkage; `value` is the
+    learned arm's matrices per second within 1e-3 relative Frobenius error
+    (throughput times the judged fraction within it)."""
+    import torch
+
+    import paper_1705_07112_gb300 as cpa
+    from paper_1705_07112_gb300 import inputs, train_predictor
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    count = args.served
+    t_gen = time.perf_counter()
+    mix = inputs.served_mix(count, seed_index=rank)
+    t_gen = time.perf_counter() - t_gen
+    Xs = [torch.from_numpy(sm.X).to(dev) for sm in mix]
+    Yl = [torch.empty_like(X) for X in Xs]
+    Yp = [torch.empty_like(X) for X in Xs]
+    specs = [dict(kind=sm.shrink.kind, tau=sm.shrink.tau, c=sm.shrink.c, eps=sm.shrink.eps,
+                  noise=sm.shrink.noise) for sm in mix]
+    h = cpa.Handle(local)
+    net, pred = train_predictor.load_predictor()
+    rule = cpa.learn_rule(L_scale=pred["L_scale"], margin=pred["margin"], L_min=4, L_max=args.served_L_max,
+                          L_fallback=50, use_lambda=True)
+    ml = cpa.MemberList(Xs, Yl, specs)
+    mp_ = cpa.MemberList(Xs, Yp, specs)
+    stream = torch.cuda.current_stream(dev)
+    nbytes = int(sum(sm.X.nbytes for sm in mix))
+
+    def learned():
+        cpa.cpa_serve_learned(h, net, ml, rule, prec="bf16x3", stream=stream)
+
+    def timed(fn, steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        learned()
+    # per-stage device time of the single-matrix members' shrinkage (one step)
+    cpa.cpa_profile_read(h, reset=True)
+    cpa.cpa_profile_enable(h, True)
+    learned()
+    prof = cpa.cpa_profile_read(h, reset=True)
+    cpa.cpa_profile_enable(h, False)
+    Ls, lams, nfb = cpa.cpa_serve_read(h, count)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    ms_l = timed(learned, args.steps)
+    barrier(world)
+    clk = clocks.stop()
+    ms_l = max_over_ranks(world, ms_l, dev)
+    rate_l = world * args.steps * count / (ms_l / 1e3)
+    return _served_finish(args, world, rank, local, cpa, h, net, rule, mix, Xs, Yl, Yp, mp_, specs, Ls, lams, nfb,
+                          prof, ms_l, rate_l, clk, nbytes, t_gen, timed, stream, dev, pred)
+
+
+def _served_finish(args, world, rank, local, cpa, h, net, rule, mix, Xs, Yl, Yp, mp_, specs, Ls, lams, nfb, prof,
+                   ms_l, rate_l, clk, nbytes, t_gen, timed, stream, dev, pred):
+    import torch
+    peaks = load_peaks()
+    count = len(mix)
+    sample = served_sample(count, args.judge)
+    ncpu = os.cpu_count() or 1
+    res, wall = served_oracle(rank, sample, ncpu)
+    exact = [r[0] for r in res]
+    errs_fp64 = np.array([r[1] for r in res])          # FP64 CPA error per ladder order (power bound)
+    dt_exact = float(sum(r[2] for r in res))
+
+    def judged(Ys):
+        out = []
+        for i, ex in zip(sample, exact):
+            y = Ys[int(i)].cpu().numpy().astype(np.float64)
+            e64 = ex.astype(np.float64)
+            den = np.linalg.norm(e64)
+            out.append(np.linalg.norm(y - e64) / (den if den > 0 else np.linalg.norm(mix[int(i)].X)))
+        return np.array(out)
+
+    err_l = judged(Yl)
+    frac_l = float(np.mean(err_l <= SERVED_TOL))
+    # the plain arm's order: the smallest ladder order whose FP64 error (the
+    # oracle's spectra, the same power bound) puts at least the learned
+    # arm's fraction of the sample within the target, else the best one
+    fr = (errs_fp64 <= SERVED_TOL).mean(axis=0)
+    ok = [k for k in range(len(LADDER)) if fr[k] >= frac_l]
+    kp = ok[0] if ok else int(np.argmax(fr))
+    L_plain = LADDER[kp]
+
+    def plain(L):
+        return lambda: cpa.cpa_svt_batched(h, mp_, L0=L, prec="fp32", stream=stream)
+
+    plain(L_plain)()
+    ms_p = max_over_ranks(world, timed(plain(L_plain), args.plain_steps), dev)
+    rate_p = world * args.plain_steps * count / (ms_p / 1e3)
+    err_p = judged(Yp)
+    frac_p = float(np.mean(err_p <= SERVED_TOL))
+    plain(50)()
+    ms_50 = max_over_ranks(world, timed(plain(50), 1), dev)
+    err_50 = judged(Yp)
+    frac_50 = float(np.mean(err_50 <= SERVED_TOL))
+    rate_50 = world * count / (ms_50 / 1e3)
+
+    # end to end through the C ABI with host buffers: every step copies the
+    # batch in from pinned memory and the results out
+    hX = [torch.from_numpy(sm.X).pin_memory() for sm in mix]
+    hY = [torch.empty_like(x).pin_memory() for x in hX]
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for x, X in zip(hX, Xs):
+            X.copy_(x, non_blocking=True)
+        cpa.cpa_serve_learned(h, net, _ml_cache(cpa, Xs, Yl, specs), rule, prec="bf16x3", stream=stream)
+        for y, Y in zip(hY, Yl):
+            y.copy_(Y, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0, dev)
+    e2e = {"value": world * args.steps * count * frac_l / e2e_s, "unit": "matrices/s within 1e-3",
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+           "throughput_all_matrices": world * args.steps * count / e2e_s}
+
+    # roofline of the single-matrix members' recurrence (the tensor-core
+    # launch that dominates the step): symmetric-minimal flops p^2 (p + 1)
+    # per product, L - 2 products per member
+    big = [i for i, sm in enumerate(mix) if not (min(sm.X.shape) <= 64 and max(sm.X.shape) <= 128)]
+    flops = sum((max(int(Ls[i]), 2) - 2) * float(min(mix[i].X.shape)) ** 2 * (min(mix[i].X.shape) + 1)
+                for i in big)
+    rec = prof["recur"]
+    rec_ms = rec["ms"]
+    achieved = flops / (rec_ms / 1e3) / 1e12 if rec_ms > 0 else None
+    stage_ms = {k: v["ms"] for k, v in prof.items()}
+    roof = {"kernel": "recurrence (cooperative tcgen05 launch per single-matrix member, BF16 split)",
+            "bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+            "frac": (achieved / peaks["bf16_tflops"]) if achieved else None, "traffic": None,
+            "flops_per_step": flops, "recurrence_ms_per_step": rec_ms, "launches_per_step": rec["launches"],
+            "peak_source": "%s bf16 burst" % peaks["source"], "stage_ms_per_step": stage_ms,
+            "batched_and_other_ms_per_step": ms_l / args.steps - sum(stage_ms.values()),
+            "tensor_pipe_pct_ncu": NCU_TENSOR_PIPE.get("served_mix")}
+    Ls_np = np.asarray(Ls)
+    value = rate_l * frac_l
+    cfg = {"workload": "served_mix_%d_sides64-2048_half_patch_groups" % count, "count": count,
+           "families": "half 64 x U{40..80}, half sides log-uniform [64, 2048]; rank 1-50; sigma 0.01-0.2",
+           "kinds": "hard / soft / weighted soft, a third each, tau = U[1.2, 3] x noise edge",
+           "tolerance": SERVED_TOL, "learned": {"prec": "bf16x3", "L_max": rule.L_max, "L_scale": rule.L_scale,
+                                                "margin": rule.margin, "fallback_L": rule.L_fallback,
+                                                "lambda": "predicted, floored at (theta_4 + r_4)(1 + margin)"},
+           "predictor": pred["meta"], "judged_sample": len(sample),
+           "inputs": "%d distinct matrices, %.0f MB > L2 (129 MB)" % (count, nbytes / 1e6),
+           "parallelism": "replicas x%d" % world}
+    line = {"metric": METRIC, "value": value, "unit": "matrices/s within 1e-3",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_l / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3",
+            "data": "synthetic", "config": cfg, "roofline": roof, "e2e": e2e, "clocks": clk,
+            "gpu_launches": int(round(args.steps * (sum(v["launches"] for v in prof.values()) + 1))),
+            "learned": {"matrices_per_s": rate_l, "frac_within_tol": frac_l, "good_per_s": value,
+                        "mean_L": float(Ls_np.mean()), "median_L": float(np.median(Ls_np)),
+                        "fallbacks": int(nfb), "median_err": float(np.median(err_l))},
+            "plain_fp32": {"L": L_plain, "matrices_per_s": rate_p, "frac_within_tol": frac_p,
+                           "good_per_s": rate_p * frac_p, "median_err": float(np.median(err_p)),
+                           "order_rule": "smallest ladder L whose oracle FP64 error reaches the learned fraction"},
+            "plain_fp32_L50": {"matrices_per_s": rate_50, "frac_within_tol": frac_50, "good_per_s": rate_50 * frac_50},
+            "vs_plain_fp32_good_per_s": value / max(rate_p * frac_p, 1e-300) if frac_p > 0 else None,
+            "cpu_baseline": {"value": len(sample) / dt_exact, "unit": "matrices/s (exact shrinkage)", "cores": 1,
+                             "kind": "oracle", "sample": "%d matrices of the batch, the oracle's exact shrinkage "
+                             "(LAPACK SVD), summed single-thread time %.1f s" % (len(sample), dt_exact),
+                             "all_cores": {"value": len(sample) / wall, "cores": ncpu,
+                                           "note": "wall time of %d single-thread workers, each also computing the "
+                                                   "matrix's spectrum and power bound" % ncpu}},
+            "generation_s": t_gen}
+    if rank == 0:
+        print(json.dumps(line))
+    net.close()
+    h.close()
+    return 0
+
+
+_ML = {}
+
+
+def _ml_cache(cpa, Xs, Ys, specs):
+    key = (id(Xs), id(Ys))
+    if key not in _ML:
+        _ML[key] = cpa.MemberList(Xs, Ys, specs)
+    return _ML[key]
+
+
 def run_gpu(args, world, rank, local):
+    if args.workload == "served_mix":
+        return run_gpu_served(args, world, rank, local)
     if args.workload == "patch_groups":
         return run_gpu_batched(args, world, rank, local)
     if args.workload == "rpca_admm":
@@ -800,6 +1097,11 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=32)
     ap.add_argument("--batch", type=int, default=20000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--served", type=int, default=5000, help="matrices of the served mix")
+    ap.add_argument("--served-L-max", type=int, default=1024)
+    ap.add_argument("--judge", type=int, default=160, help="matrices judged against the exact shrinkage")
+    ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--ref-served", type=int, default=64, help="served-mix matrices per reference step")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -112,6 +112,16 @@ typedef struct {
     int transform;       /* cpa_transform                                        */
     int mode;            /* cpa_sparse_mode                                      */
     double eps_or_frac;  /* absolute threshold or fraction of entries kept       */
+    int interval;        /* 0: the series on [0, Lambda_max] as Section III-B
+                            writes it; 1: the guarded interval [a, b], a =
+                            -|Phi - Phi_|_F, b = Lambda_max, which holds the
+                            spectrum of the thresholded Phi_ (Weyl: its
+                            eigenvalues are >= -|E|_2 >= -|E|_F), with
+                            B_hat = (2 Phi_ - (a + b) Id) / (b - a) and the
+                            coefficients of h on [a, b] (h = 0 for x <= 0);
+                            the call then synchronises once to read a and b
+                            and forms the coefficients on the host (FP64).
+                            Ignored without an entry threshold.              */
 } cpa_sparsify;
 
 typedef struct cpa_ctx *cpa_handle;
@@ -223,7 +233,13 @@ CPA_API cpa_status cpa_get_coeffs(cpa_handle h, double *c_out, int L, void *stre
  *   for one arrival more than the grid makes, so that it can end only by the
  *   limit above; for tests of the timeout path.  0 (the default) is normal
  *   operation. */
-enum { CPA_OPT_SERIES = 1, CPA_OPT_WAIT_KCYCLES = 2, CPA_OPT_STALL_TEST = 3 };
+/* CPA_OPT_SPARSE_SKIP: 1 (the default) lets the tensor-core recurrence skip
+ *   the tiles of the thresholded operand 2 Phi_ / Lambda_max that are zero
+ *   (128 rows by 64 or 128 columns; the sparsity-based reduction with an
+ *   entry threshold): their loads and products are not issued.  The skipped
+ *   products are exact zeros, so the result is the same bit for bit; 0
+ *   runs every tile (for comparisons). */
+enum { CPA_OPT_SERIES = 1, CPA_OPT_WAIT_KCYCLES = 2, CPA_OPT_STALL_TEST = 3, CPA_OPT_SPARSE_SKIP = 4 };
 enum { CPA_SERIES_FORWARD = 0, CPA_SERIES_CLENSHAW = 1 };
 CPA_API cpa_status cpa_set_option(cpa_handle h, int option, int value);
 

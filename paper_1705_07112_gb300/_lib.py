@@ -31,7 +31,7 @@ EXPORTS = ["cpa_create", "cpa_destroy", "cpa_status_string", "cpa_last_error", "
            "cpa_completion_create", "cpa_completion_destroy", "cpa_completion_run", "cpa_sync_status",
            "cpa_svt_learned", "cpa_get_order", "cpa_learn_features", "cpa_serve_learned", "cpa_serve_read"]
 OPT_SERIES, SERIES_FORWARD, SERIES_CLENSHAW = 1, 0, 1
-OPT_WAIT_KCYCLES, OPT_STALL_TEST = 2, 3
+OPT_WAIT_KCYCLES, OPT_STALL_TEST, OPT_SPARSE_SKIP = 2, 3, 4
 STAGES = ["prep", "gram", "bound", "coeff", "shift", "recur", "apply", "sparse"]
 T_IDENTITY, T_HAAR1_LOWPASS, T_BLOCK_DCT8, T_DCT = 0, 1, 2, 3
 SPARSE_OFF, SPARSE_ABS, SPARSE_TOPK = 0, 1, 2
@@ -43,7 +43,8 @@ class CpaShrink(ctypes.Structure):
 
 
 class CpaSparsify(ctypes.Structure):
-    _fields_ = [("transform", ctypes.c_int), ("mode", ctypes.c_int), ("eps_or_frac", ctypes.c_double)]
+    _fields_ = [("transform", ctypes.c_int), ("mode", ctypes.c_int), ("eps_or_frac", ctypes.c_double),
+                ("interval", ctypes.c_int)]
 
 
 class CpaLearnRule(ctypes.Structure):
@@ -265,7 +266,8 @@ def cpa_svt(h: Handle, X, shrink, L: int, lambda_max: float = 0.0, prec="fp32", 
     s = _as_shrink(shrink)
     sp = None
     if sparsify is not None:
-        sp = ctypes.byref(CpaSparsify(int(sparsify[0]), int(sparsify[1]), float(sparsify[2])))
+        sp = ctypes.byref(CpaSparsify(int(sparsify[0]), int(sparsify[1]), float(sparsify[2]),
+                                              int(sparsify[3]) if len(sparsify) > 3 else 0))
     p = PREC[prec] if isinstance(prec, str) else int(prec)
     _check(load().cpa_svt(h.ptr, ctypes.c_void_p(ptr), m, n, ld, ctypes.byref(s), int(L), float(lambda_max), p,
                           sp, ctypes.c_void_p(yptr), ldy, _stream_ptr(stream)), "cpa_svt")
@@ -297,7 +299,8 @@ def cpa_svt_host(h: Handle, Xs, shrink, L: int, lambda_max: float = 0.0, prec="f
     s = _as_shrink(shrink)
     sp = None
     if sparsify is not None:
-        sp = ctypes.byref(CpaSparsify(int(sparsify[0]), int(sparsify[1]), float(sparsify[2])))
+        sp = ctypes.byref(CpaSparsify(int(sparsify[0]), int(sparsify[1]), float(sparsify[2]),
+                                              int(sparsify[3]) if len(sparsify) > 3 else 0))
     p = PREC[prec] if isinstance(prec, str) else int(prec)
     _check(load().cpa_svt_host(h.ptr, len(Xs), xp, m, n, Xs[0].stride(0), ctypes.byref(s), int(L),
                                float(lambda_max), p, sp, yp, Ys[0].stride(0), _stream_ptr(stream)), "cpa_svt_host")

@@ -32,6 +32,7 @@ struct cpa_ctx {
     int series = CPA_SERIES_FORWARD;   // how the filter's series is summed
     WaitPolicy wait;                   // grid-barrier wait limit, test stall
     int *d_err = nullptr;              // error word of the last cpa_svt's tensor-core kernels
+    int sparse_skip = 1;               // skip zero tiles of the thresholded operand
     bool have_learn = false;           // the last call chose its order on the device
     int *d_L = nullptr;                // {L, fallback} of that call
     // pointer-form batches (cpa_svt_batched, cpa_serve_learned): the
@@ -185,6 +186,7 @@ struct SvtWs {
     int64_t ldp = 0;
     float *T = nullptr;                 // sparsify transform (when requested)
     float *eps = nullptr;
+    double *removed2 = nullptr;         // |Phi - Phi_|_F^2 (guarded interval)
     unsigned long long *counts = nullptr;
     float *G = nullptr, *A = nullptr, *Z[2] = {nullptr, nullptr}, *H = nullptr, *v0 = nullptr, *v1 = nullptr;
     double *out = nullptr, *norm2 = nullptr, *coef = nullptr;
@@ -202,6 +204,8 @@ struct SvtWs {
     float *u0 = nullptr, *u1 = nullptr;
     double *lacc = nullptr, *ltab = nullptr;
     int *Lsel = nullptr;
+    // tile occupancy of the thresholded operand (sparsity-based reduction)
+    uint8_t *amask = nullptr;
     size_t bytes = 0;
 };
 
@@ -245,6 +249,7 @@ SvtWs carve(char *base, int64_t m, int64_t n, int L, int iters, int prec, bool s
     if (sparse) {
         w.T = c.take<float>(pp);
         w.eps = c.take<float>(4);
+        w.removed2 = c.take<double>(2);
         w.counts = c.take<unsigned long long>(32);
     }
     if (prec != CPA_FP32) {
@@ -270,6 +275,7 @@ SvtWs carve(char *base, int64_t m, int64_t n, int L, int iters, int prec, bool s
             w.Zlo[0] = c.take<__nv_bfloat16>(pk);
             w.Zlo[1] = c.take<__nv_bfloat16>(pk);
         }
+        if (sparse) w.amask = c.take<uint8_t>((size_t)((p + 127) / 128) * (size_t)((w.ldk + 63) / 64));
     }
     w.bytes = c.off;
     return w;
@@ -540,7 +546,9 @@ cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
         if (sp->mode == CPA_SPARSE_ABS && !(sp->eps_or_frac >= 0.0)) return CPA_ERR_INVALID_ARG;
         if (sp->mode == CPA_SPARSE_TOPK && !(sp->eps_or_frac > 0.0 && sp->eps_or_frac <= 1.0))
             return CPA_ERR_INVALID_ARG;
+        if (sp->interval != 0 && sp->interval != 1) return CPA_ERR_INVALID_ARG;
     }
+    const bool guarded = sparse && sp->interval == 1 && sp->mode != CPA_SPARSE_OFF;
     if (ranges_overlap(dX, (size_t)((m - 1) * ldx + n) * sizeof(float), dY,
                        (size_t)((m - 1) * ldy + n) * sizeof(float)))
         return CPA_ERR_INVALID_ARG;
@@ -595,8 +603,10 @@ cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
         e2.symmetric_upper = 1;
         CK(gemm_f32((int)p, (int)p, (int)p, w.A, w.ldp, true, w.T, w.ldp, true, e2, st));
         h->launches[CPA_STAGE_SPARSE] += 3;
+        if (guarded) CK(cudaMemsetAsync(w.removed2, 0, sizeof(double), st));
         if (sp->mode == CPA_SPARSE_ABS) {
-            CK(threshold_entries(w.G, (int)p, w.ldp, nullptr, (float)sp->eps_or_frac, st, h->num_sms));
+            CK(threshold_entries(w.G, (int)p, w.ldp, nullptr, (float)sp->eps_or_frac, st, h->num_sms,
+                                 guarded ? w.removed2 : nullptr));
             h->launches[CPA_STAGE_SPARSE] += 1;
         } else if (sp->mode == CPA_SPARSE_TOPK) {
             const double pp2 = (double)p * (double)p;
@@ -604,7 +614,7 @@ cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
             k = std::max(1LL, std::min(k, (long long)pp2));
             CK(topk_eps(w.G, (int)p, w.ldp, k, w.counts, (unsigned int *)(w.flag + 3), w.flag + 4, w.eps, st,
                         h->num_sms));
-            CK(threshold_entries(w.G, (int)p, w.ldp, w.eps, 0.f, st, h->num_sms));
+            CK(threshold_entries(w.G, (int)p, w.ldp, w.eps, 0.f, st, h->num_sms, guarded ? w.removed2 : nullptr));
             h->launches[CPA_STAGE_SPARSE] += 2;
         }
     }
@@ -628,8 +638,23 @@ cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
         CK(power_bound_persistent(w.G, w.ldp, (int)p, iters, w.v0, w.v1, w.norm2, (unsigned int *)w.flag,
                                   w.flag + 1, w.out, st, h->num_sms, L, &sp_, w.coef, h->wait));
     }
+    // guarded interval [-|Phi - Phi_|_F, Lambda_max]: its ends are read
+    // once (one synchronisation) and its coefficients formed on the host
+    double span = 0.0, sigma = 1.0;
+    if (guarded) {
+        CK(cudaMemcpyAsync(h->h_pin, w.out, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(h->h_pin + 6, w.removed2, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const double b = h->h_pin[3], a = -sqrt(std::max(h->h_pin[6], 0.0));
+        if (!(b > 0.0) || !std::isfinite(b) || !std::isfinite(a)) return CPA_ERR_BOUND;
+        span = b - a;
+        sigma = (a + b) / (b - a);
+        std::vector<double> cc((size_t)L);
+        coeffs_interval(sp_, L, a, b, cc.data());
+        CK(cudaMemcpy(w.coef, cc.data(), sizeof(double) * (size_t)L, cudaMemcpyHostToDevice));
+    }
     // coefficients (FP64, on the device so the call stays asynchronous)
-    if (lambda_max > 0.0 && !learn) {
+    if (lambda_max > 0.0 && !learn && !guarded) {
         StageScope sc(h, CPA_STAGE_COEFF, st, 1);
         CK(device_coeffs(w.out + 3, 0.0, L, sp_, w.coef, st));
     }
@@ -639,7 +664,7 @@ cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
         CK(shift_init(w.G, w.ldp, (int)p, w.out + 3, w.coef, L, tc ? nullptr : w.A, w.Z[1], w.H, w.ldp,
                       tc ? w.Ahi : nullptr, tc ? w.Alo : nullptr, tc ? w.Zhi[1] : nullptr,
                       tc ? w.Zlo[1] : nullptr, tc ? w.ldk : w.ldp, st, h->num_sms, clenshaw,
-                      tc ? w.Zhi[0] : nullptr, tc ? w.Zlo[0] : nullptr));
+                      tc ? w.Zhi[0] : nullptr, tc ? w.Zlo[0] : nullptr, span, sigma));
     }
     // recurrence with fused accumulation: Psi_k = 2 B_hat Psi_{k-1} - Psi_{k-2}, H += c_k Psi_k.
     // Ring: Psi_k overwrites Psi_{k-2} in slot k&1; Psi_0 = Id is implicit.
@@ -656,7 +681,7 @@ cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
         e.ldc2 = w.ldp;
         e.s_acc = 2.f;
         e.s_c = -1.f;
-        e.s_c2 = -2.f;
+        e.s_c2 = (float)(-2.0 * sigma);
         e.H = w.H;
         e.ldh = w.ldp;
         e.coef = w.coef;
@@ -666,7 +691,8 @@ cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
         TcOperand a;
         a.hi = w.Ahi; a.lo = w.Alo; a.ld = w.ldk; a.rows = (int)p;
         CK(gemm_tc_recurrence((int)p, a, nsplit_rec, e, 2, L, w.Z, w.Zhi, w.Zlo, (unsigned int *)(w.flag + 2), st,
-                              h->num_sms, clenshaw, L, &closed, (int)w.ldk, h->wait, learn ? w.Lsel : nullptr));
+                              h->num_sms, clenshaw, L, &closed, (int)w.ldk, h->wait, learn ? w.Lsel : nullptr,
+                              (sparse && sp->mode != CPA_SPARSE_OFF && h->sparse_skip) ? w.amask : nullptr));
     }
     if (learn && !tc) {
         // the CUDA-core recurrence is driven from the host: read the order
@@ -708,12 +734,12 @@ cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
             // -1 would move the eigenvalues near the interval's ends)
             e.C2 = w.Z[prev];
             e.ldc2 = w.ldp;
-            e.s_c2 = -2.f;
+            e.s_c2 = (float)(-2.0 * sigma);
             CK(gemm_f32((int)p, (int)p, (int)p, w.A, w.ldp, true, w.Z[prev], w.ldp, true, e, st));
         } else {
             e.C2 = w.Z[prev];                  // Psi_{k-1}
             e.ldc2 = w.ldp;
-            e.s_c2 = -2.f;
+            e.s_c2 = (float)(-2.0 * sigma);
             e.Dhi = w.Zhi[cur];
             e.Dlo = w.Zlo[cur];
             e.ldb = w.ldk;
@@ -848,6 +874,11 @@ cpa_status cpa_set_option(cpa_handle h, int option, int value) {
     if (option == CPA_OPT_WAIT_KCYCLES) {
         if (value < 0) return CPA_ERR_INVALID_ARG;
         h->wait.wait_cycles = (long long)value * 1000LL;
+        return CPA_OK;
+    }
+    if (option == CPA_OPT_SPARSE_SKIP) {
+        if (value != 0 && value != 1) return CPA_ERR_INVALID_ARG;
+        h->sparse_skip = value;
         return CPA_OK;
     }
     if (option == CPA_OPT_STALL_TEST) {

@@ -237,7 +237,32 @@ struct MultiStep {
     // number of terms chosen on the device (learned order): the launch runs
     // the steps k_first <= k < min(k_end, *L_dev); null: k_end as given
     const int *L_dev = nullptr;
+    // occupancy of the A operand (the thresholded At of the sparsity-based
+    // reduction): amask[tm * mask_groups + zg] = 0 when rows tm*128.. of A
+    // are zero over the zg-th group of K slices loaded per stage; such
+    // groups are neither loaded nor multiplied (their products are exact
+    // zeros), except group 0, which starts each accumulator
+    const uint8_t *amask = nullptr;
+    int mask_groups = 0;
 };
+
+// Occupancy of A in tiles of 128 rows x (width) columns: one block per tile,
+// any nonzero hi or lo part marks it.
+__global__ void amask_kernel(const __nv_bfloat16 *__restrict__ hi, const __nv_bfloat16 *__restrict__ lo, int64_t ld,
+                             int rows, int K, int width, uint8_t *mask, int groups) {
+    const int tm = blockIdx.y, zg = blockIdx.x;
+    int any = 0;
+    for (int e = threadIdx.x; e < 128 * width; e += blockDim.x) {
+        const int r = tm * 128 + e / width, c = zg * width + e % width;
+        if (r < rows && c < K) {
+            const int64_t o = (int64_t)r * ld + c;
+            if (__bfloat16_as_ushort(hi[o]) & 0x7FFF) any = 1;
+            if (lo && (__bfloat16_as_ushort(lo[o]) & 0x7FFF)) any = 1;
+        }
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) mask[tm * groups + zg] = any ? 1 : 0;
+}
 
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -760,8 +785,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tile_of(t, tiles_m, tiles_n, sym, BN, tm, tn);
                     const int m0 = tm * BM, n0 = tn * BN;
                     for (int kb = 0; kb < nkb; kb += gs) {
-                        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) break;
                         const int seg = kb / kb_per, z = kb % kb_per;
+                        if (ms.amask && z > 0 && !ms.amask[tm * ms.mask_groups + z / gs]) continue;
+                        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) break;
                         const CUtensorMap *ma = (seg < 2) ? &maps.a_hi : &maps.a_lo;
                         const CUtensorMap *mb = (seg == 1) ? &sm.b_lo : &sm.b_hi;
                         mbar_expect_tx(&full[stage], stage_bytes);
@@ -812,7 +838,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tphase[buf] ^= 1;
                     fence_after();
                     const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
+                    int tmm = 0, tnn = 0;
+                    if (ms.amask) tile_of(t, tiles_m, tiles_n, sym, BN, tmm, tnn);
                     for (int kb = 0; kb < nkb; kb += gs) {
+                        if (ms.amask && (kb % kb_per) > 0 && !ms.amask[tmm * ms.mask_groups + (kb % kb_per) / gs])
+                            continue;
                         if (!mbar_wait(&full[stage], phase, abort_flag)) {
                             ok = false;
                             break;
@@ -1171,7 +1201,7 @@ cudaError_t dispatch_bn(int bn, F f) {
 cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epilogue &e, int k_first, int k_end,
                                float *const z[2], __nv_bfloat16 *const zhi[2], __nv_bfloat16 *const zlo[2],
                                unsigned int *bar, cudaStream_t st, int num_sms, int clenshaw, int L, int *closed,
-                               int kpad, const WaitPolicy &wp, const int *L_dev) {
+                               int kpad, const WaitPolicy &wp, const int *L_dev, uint8_t *mask_buf) {
     if (closed) *closed = 0;
     if (p <= 0 || k_end <= k_first) return cudaSuccess;
     if (!load_encode()) return cudaErrorNotSupported;
@@ -1187,6 +1217,7 @@ cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epil
     ms.stall = wp.stall;
     ms.L_dev = L_dev;
     if (L_dev && clenshaw) return cudaErrorInvalidValue;   // Clenshaw's sum runs from the last term down
+    ms.amask = mask_buf;
     ms.k_first = k_first;
     ms.k_end = k_end;
     for (int i = 0; i < 2; ++i) {
@@ -1211,6 +1242,17 @@ cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epil
     // length (a multiple of 128: grouped loads, no K tail)
     const int K = kpad > p ? kpad : p;
     if (K > A.ld) return cudaErrorInvalidValue;
+    if (mask_buf) {
+        // the K slices per stage of this launch: 2 when the grouped 3-D
+        // loads apply (K a multiple of 128 below BN = 256), else 1
+        const int gs = (bn < 256 && K % 128 == 0) ? 2 : 1;
+        const int width = 64 * gs;
+        ms.mask_groups = (K + width - 1) / width;
+        amask_kernel<<<dim3(ms.mask_groups, (p + 127) / 128), 256, 0, st>>>(A.hi, A.lo, A.ld, p, K, width, mask_buf,
+                                                                          ms.mask_groups);
+        cudaError_t rm = cudaGetLastError();
+        if (rm != cudaSuccess) return rm;
+    }
     cudaError_t r2 = dispatch_bn(bn, [&](auto b) {
         return launch<decltype(b)::value>(p, p, K, A, B, nsplit, e, ms, st, num_sms);
     });

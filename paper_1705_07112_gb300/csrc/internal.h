@@ -143,12 +143,15 @@ cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epil
                                float *const z[2], __nv_bfloat16 *const zhi[2], __nv_bfloat16 *const zlo[2],
                                unsigned int *bar, cudaStream_t st, int num_sms, int clenshaw = 0, int L = 0,
                                int *closed = nullptr, int kpad = 0, const WaitPolicy &wp = WaitPolicy(),
-                               const int *L_dev = nullptr);
+                               const int *L_dev = nullptr, uint8_t *mask_buf = nullptr);
+// mask_buf (optional, ceil(p/128) * ceil(kpad/64) bytes): the launch first
+// records which 128-row x K-slice-group tiles of A are zero and skips their
+// loads and products (the sparsity-based reduction's thresholded operand).
 
 // Sparsity-based reduction helpers (sparsify.cu).
 cudaError_t make_transform(int type, int p, float *T, int64_t ld, cudaStream_t st, int num_sms);
 cudaError_t threshold_entries(float *Phi, int p, int64_t ld, const float *eps_dev, float eps_host, cudaStream_t st,
-                              int num_sms);
+                              int num_sms, double *removed2 = nullptr);
 cudaError_t symmetrize_lower(float *S, int p, int64_t ld, cudaStream_t st, int num_sms);
 cudaError_t topk_eps(const float *Phi, int p, int64_t ld, long long k, unsigned long long *counts, unsigned int *bar,
                      int *err, float *eps_out, cudaStream_t st, int num_sms);
@@ -182,10 +185,17 @@ cudaError_t device_coeffs(const double *lam_dev, double lam_host, int L, const S
 // CUDA-core path, as BF16 hi/lo in Athi/Atlo for the tensor-core path, with
 // Z1 as BF16 hi/lo; their columns p .. ldb-1, and those of the ring's other
 // BF16 slot Z0hi/Z0lo when given, are set to zero.
+// span > 0: the series' interval is [a, b] with b - a = span and
+// sigma = (a + b) / (b - a): At = (2/span) G, B_hat = At - sigma Id (the
+// guarded interval); span = 0: [0, lambda], sigma = 1.
 cudaError_t shift_init(const float *G, int64_t ldg, int p, const double *lam, const double *c, int L, float *A,
                        float *Z1, float *H, int64_t ld, __nv_bfloat16 *Athi, __nv_bfloat16 *Atlo,
                        __nv_bfloat16 *Z1hi, __nv_bfloat16 *Z1lo, int64_t ldb, cudaStream_t st, int num_sms,
-                       int clenshaw = 0, __nv_bfloat16 *Z0hi = nullptr, __nv_bfloat16 *Z0lo = nullptr);
+                       int clenshaw = 0, __nv_bfloat16 *Z0hi = nullptr, __nv_bfloat16 *Z0lo = nullptr,
+                       double span = 0.0, double sigma = 1.0);
+// Host FP64 coefficients of Eq. chebychev_coeff_shifted on [a, b] (the
+// response is 0 for x <= 0).
+void coeffs_interval(const ShrinkParams &s, int L, double a, double b, double *c);
 // Clenshaw's closing step H = (b_0 - b_2) / 2 with b_0 in H and b_2 in B2
 // (B2 null: b_2 = c[2] Id); lower triangle only when lower_only.
 cudaError_t clenshaw_finish(float *H, const float *B2, int p, int64_t ld, const double *c, int lower_only,

@@ -211,13 +211,14 @@ __device__ __forceinline__ void put_split(__nv_bfloat16 *hi, __nv_bfloat16 *lo, 
 __global__ void shift_kernel(const float *__restrict__ G, int64_t ldg, int p, const double *lam,
                              const double *c, int L, float *A, float *Z1, float *H, int64_t ld,
                              __nv_bfloat16 *Athi, __nv_bfloat16 *Atlo, __nv_bfloat16 *Z1hi, __nv_bfloat16 *Z1lo,
-                             int64_t ldb, int clenshaw, __nv_bfloat16 *Z0hi, __nv_bfloat16 *Z0lo) {
+                             int64_t ldb, int clenshaw, __nv_bfloat16 *Z0hi, __nv_bfloat16 *Z0lo, double span,
+                             float sigma) {
     // the scalars once per block: an FP64 division in every thread would
     // queue hundreds of thousands of them on this part's scarce FP64 pipe
     __shared__ float sc[5];
     const bool cl = clenshaw && L >= 3;
     if (threadIdx.x == 0) {
-        sc[0] = (float)(2.0 / lam[0]);
+        sc[0] = (float)(2.0 / (span > 0.0 ? span : lam[0]));
         sc[1] = (float)(0.5 * c[0]);
         sc[2] = L > 1 ? (float)c[1] : 0.f;
         sc[3] = cl ? (float)c[L - 2] : 0.f;
@@ -230,7 +231,7 @@ __global__ void shift_kernel(const float *__restrict__ G, int64_t ldg, int p, co
     for (int i = blockIdx.x; i < p; i += gridDim.x)
     for (int j = threadIdx.x; j < p; j += blockDim.x) {
         float at = s * G[(int64_t)i * ldg + j];
-        float a = at - (i == j ? 1.f : 0.f);
+        float a = at - (i == j ? sigma : 0.f);
         const float z1 = za * a + (i == j ? zc : 0.f);
         if (A) A[(int64_t)i * ld + j] = at;
         if (Z1) Z1[(int64_t)i * ld + j] = z1;
@@ -627,12 +628,24 @@ __global__ void clenshaw_finish_kernel(float *H, const float *B2, int p, int64_t
 cudaError_t shift_init(const float *G, int64_t ldg, int p, const double *lam, const double *c, int L, float *A,
                        float *Z1, float *H, int64_t ld, __nv_bfloat16 *Athi, __nv_bfloat16 *Atlo,
                        __nv_bfloat16 *Z1hi, __nv_bfloat16 *Z1lo, int64_t ldb, cudaStream_t st, int num_sms,
-                       int clenshaw, __nv_bfloat16 *Z0hi, __nv_bfloat16 *Z0lo) {
+                       int clenshaw, __nv_bfloat16 *Z0hi, __nv_bfloat16 *Z0lo, double span, double sigma) {
     int blocks = std::min(p, num_sms * 8);   // a block per row, grid-stride
     if (blocks < 1) blocks = 1;
     shift_kernel<<<blocks, 256, 0, st>>>(G, ldg, p, lam, c, L, A, Z1, H, ld, Athi, Atlo, Z1hi, Z1lo, ldb,
-                                         clenshaw, Z0hi, Z0lo);
+                                         clenshaw, Z0hi, Z0lo, span, (float)sigma);
     return cudaGetLastError();
+}
+
+void coeffs_interval(const ShrinkParams &s, int L, double a, double b, double *c) {
+    for (int k = 0; k < L; ++k) {
+        double acc = 0.0;
+        for (int l = 1; l <= L; ++l) {
+            const double th = kPi * ((double)l - 0.5) / (double)L;
+            const double x = a + 0.5 * (b - a) * (cos(th) + 1.0);
+            acc += cos((double)k * th) * (x > 0.0 ? response(s, x) : 0.0);
+        }
+        c[k] = 2.0 / (double)L * acc;
+    }
 }
 
 cudaError_t split_bf16(const float *X, int rows, int cols, int64_t ldx, bool transpose, __nv_bfloat16 *hi,

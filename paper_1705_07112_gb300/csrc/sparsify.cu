@@ -51,12 +51,24 @@ __global__ void make_transform_kernel(int type, int p, float *T, int64_t ld) {
     }
 }
 
-__global__ void threshold_kernel(float *Phi, int p, int64_t ld, const float *eps_dev, float eps_host) {
+// Entries below eps set to zero; removed2 (optional) accumulates the sum of
+// their squares, |Phi - Phi_|_F^2 (per-warp FP32 partials, FP64 atomics).
+__global__ void threshold_kernel(float *Phi, int p, int64_t ld, const float *eps_dev, float eps_host,
+                                 double *removed2) {
     const float eps = eps_dev ? *eps_dev : eps_host;
     const int64_t total = (int64_t)p * p;
+    float r2 = 0.f;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         float *q = Phi + (e / p) * ld + e % p;
-        if (!(fabsf(*q) >= eps)) *q = 0.f;
+        const float v = *q;
+        if (!(fabsf(v) >= eps)) {
+            r2 = fmaf(v, v, r2);
+            *q = 0.f;
+        }
+    }
+    if (removed2) {
+        for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+        if ((threadIdx.x & 31) == 0 && r2 != 0.f) atomicAdd(removed2, (double)r2);
     }
 }
 
@@ -123,10 +135,10 @@ cudaError_t make_transform(int type, int p, float *T, int64_t ld, cudaStream_t s
 }
 
 cudaError_t threshold_entries(float *Phi, int p, int64_t ld, const float *eps_dev, float eps_host, cudaStream_t st,
-                              int num_sms) {
+                              int num_sms, double *removed2) {
     const int64_t total = (int64_t)p * p;
     int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 8);
-    threshold_kernel<<<std::max(blocks, 1), 256, 0, st>>>(Phi, p, ld, eps_dev, eps_host);
+    threshold_kernel<<<std::max(blocks, 1), 256, 0, st>>>(Phi, p, ld, eps_dev, eps_host, removed2);
     return cudaGetLastError();
 }
 

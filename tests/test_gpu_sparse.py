@@ -196,3 +196,64 @@ def test_sparsify_full_size_sampled(cpa, handle, tkind, mode, prec):
     for j, i in enumerate(rows):
         err = np.linalg.norm(got[i] - want[j]) / max(np.linalg.norm(want[j]), scale)
         assert err <= TOL[prec], (tkind, mode, prec, i, err, k)
+
+
+@pytest.mark.parametrize("tkind", [0, 1, 2, 3])
+@pytest.mark.parametrize("mode", [1, 2])
+def test_zero_tile_skip_is_bit_identical(cpa, handle, tkind, mode):
+    """The recurrence skips the all-zero tiles of the thresholded operand:
+    the same result, bit for bit, as running every tile (the skipped
+    products are exact zeros)."""
+    import torch
+    from paper_1705_07112_gb300 import _lib
+    X, T, Phi = _big_case(tkind)
+    p = 1024
+    eps, k, _ = wide_gap(Phi)
+    arg = eps if mode == 1 else (k - 0.5) / (p * p)
+    Xd = torch.from_numpy(X.astype(np.float32)).cuda()
+    lam = 1.05 * np.max(np.abs(np.linalg.eigvalsh(np.where(np.abs(Phi) >= eps, Phi, 0.0))))
+    spec = {"kind": O.SOFT, "tau": 0.1 * math.sqrt(lam)}
+    out = []
+    for skip in (1, 0):
+        _lib.cpa_set_option(handle, _lib.OPT_SPARSE_SKIP, skip)
+        Y = cpa.cpa_svt(handle, Xd, spec, 15, lam, "bf16x3", sparsify=(tkind, mode, arg))
+        torch.cuda.synchronize()
+        out.append(Y.cpu().numpy())
+    _lib.cpa_set_option(handle, _lib.OPT_SPARSE_SKIP, 1)
+    assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("shape", [(120, 64), (64, 120), (90, 37)])
+@pytest.mark.parametrize("tkind", [2, 3])
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_guarded_interval_matches_oracle(cpa, handle, shape, tkind, mode, prec):
+    """The guarded interval [-|Phi - Phi_|_F, Lambda_max] for the
+    thresholded Phi_ (cpa_sparsify.interval = 1) against the oracle's
+    guarded form (oracle/interval.py) with the same T, eps and Lambda_max."""
+    import torch
+    from oracle import interval as I
+    rng = np.random.default_rng(shape[0] * 7 + shape[1] + 3 * tkind)
+    X = smooth_matrix(rng, *shape)
+    p = min(shape)
+    T = transform(tkind, p)
+    Phi = O.phi(X, T)
+    eps, k, ratio = gap_threshold(Phi)
+    assert ratio > 1.02
+    arg = eps if mode == 1 else (k - 0.5) / (p * p)
+    lam = 1.05 * np.max(np.abs(np.linalg.eigvalsh(np.where(np.abs(Phi) >= eps, Phi, 0.0))))
+    s = O.Shrink(O.SOFT, 0.1 * math.sqrt(lam))
+    L = 15
+    ref = I.guarded_cpa(X, s, L, lam, T, eps)
+    Xd = torch.from_numpy(X.astype(np.float32)).cuda()
+    Y = cpa.cpa_svt(handle, Xd, {"kind": O.SOFT, "tau": s.tau}, L, lam, prec, sparsify=(tkind, mode, arg, 1))
+    torch.cuda.synchronize()
+    got = Y.cpu().numpy().astype(np.float64)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err <= TOL[prec], (shape, tkind, mode, prec, err)
+    # the unguarded result differs where Phi_ has negative eigenvalues
+    if np.min(np.linalg.eigvalsh(np.where(np.abs(Phi) >= eps, Phi, 0.0))) < -1e-6 * lam:
+        plain = O.cpa(X, s, L, lam, T=T, eps_thr=eps)
+        assert np.linalg.norm(plain - ref) > 0.0
+    with pytest.raises(cpa.CpaError):
+        cpa.cpa_svt(handle, Xd, {"kind": O.SOFT, "tau": s.tau}, L, lam, prec, sparsify=(tkind, mode, arg, 2))

@@ -1,54 +1,97 @@
-"""The predictor's training labels and its FP64 feature restatement
-(tests/predictor_data.py), pinned on the CPU against the dense oracle and
-against spectral facts."""
+"""The learned predictor's training labels (tests/golden/make_predictor_labels.py)
+and its FP64 feature restatement (tests/predictor_data.py), pinned on the
+CPU against the dense oracle and spectral facts."""
+import importlib.util
 import math
+import os
 
 import numpy as np
+import pytest
 
 import oracle as O
 import predictor_data as D
+from paper_1705_07112_gb300 import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_spec = importlib.util.spec_from_file_location("make_predictor_labels",
+                                               os.path.join(HERE, "golden", "make_predictor_labels.py"))
+LAB = importlib.util.module_from_spec(_spec)
+_spec.loader.exec_module(LAB)
 
 
-def test_spectral_errors_match_the_oracle_series():
-    """The vectorised Chebyshev evaluation of the labels equals the oracle's
-    own series recurrence route (approx_error_spectral)."""
-    mats, specs = D.generate(6, seed=31)
-    for X, s in zip(mats, specs):
-        Xd = X.astype(np.float64)
-        m, n = X.shape
-        _, _, sv = O.svd_jacobi(Xd if m >= n else Xd.T)
-        lam = 1.02 * float(np.max(sv)) ** 2
-        hx = np.array([O.h(s, v * v) for v in sv])
-        denom = float(np.sqrt(np.sum((sv * hx) ** 2)))
-        got = D.spectral_errors(sv, s, lam, [5, 17, 40])
-        ref = [O.approx_error_spectral(sv, s, L, lam) / denom for L in (5, 17, 40)]
-        assert np.allclose(got, ref, rtol=1e-9, atol=1e-13)
+def patch_members(seed_index, want, start=0):
+    """Indices of the first `want` patch-shaped members (cheap for the dense
+    oracle) of the serving mix of seed_index."""
+    out, i = [], start
+    while len(out) < want:
+        if inputs.served_one(seed_index, i).family == 0:
+            out.append(i)
+        i += 1
+    return out
 
 
-def test_label_order_meets_the_tolerance_on_the_dense_oracle():
-    """Brute force: Algorithm 1 in FP64 with the labelled L* (and the bound
-    the label uses) is within TOL of the exact shrinkage, and L* - 1 is not
-    (L* starts the run of passing orders that ends at 96)."""
-    mats, specs = D.generate(40, seed=32)
+def test_label_order_meets_the_target_on_the_dense_oracle():
+    """Brute force: Algorithm 1 in FP64 at the labelled L* on the label's
+    interval is within TOL of the exact shrinkage (the oracle's Jacobi SVD),
+    and the next lower ladder order is not; unreachable labels miss TOL at
+    the top of the ladder."""
     checked = 0
-    for X, s in zip(mats, specs):
-        t0, t1, sv = D.label(X, s)
-        L = int(round(math.exp(t1)))
-        if L > D.L_HI:
-            continue
-        Xd = X.astype(np.float64)
-        p = min(X.shape)
-        lam = O.lambda_bound(Xd, D.POWER_ITERS, D.MARGIN, O.start_vector(D.START_SEED, p))["lam"]
-        ex = O.shrink_exact(Xd, s)
+    for i in patch_members(301, 12):
+        row = LAB.label_one((301, i))
+        sm = inputs.served_one(301, i)
+        X = sm.X.astype(np.float64)
+        sp = sm.shrink
+        s = O.Shrink(sp.kind, sp.tau, sp.c, sp.eps, sp.noise)
+        lam = max(row[10], row[8] + row[9]) * (1.0 + LAB.MARGIN)
+        ex = O.shrink_exact(X, s)
         den = np.linalg.norm(ex)
-        assert np.linalg.norm(O.cpa(Xd, s, L, lam) - ex) / den <= D.TOL
-        if L > D.L_LO:
-            assert np.linalg.norm(O.cpa(Xd, s, L - 1, lam) - ex) / den > D.TOL
-        assert t0 >= -1e-12   # theta_4 <= sigma_max^2
+        L = int(row[13])
+        assert row[11] >= -1e-12   # theta_4 <= sigma_max^2
+        if L == LAB.L_NONE:
+            top = LAB.LADDER[-1]
+            assert np.linalg.norm(O.cpa(X, s, top, lam) - ex) / den > LAB.TOL
+            continue
+        assert abs(math.exp(row[12]) - L) <= 1e-9 * L
+        assert np.linalg.norm(O.cpa(X, s, L, lam) - ex) / den <= LAB.TOL
+        k = LAB.LADDER.index(L)
+        if k > 0:
+            assert np.linalg.norm(O.cpa(X, s, LAB.LADDER[k - 1], lam) - ex) / den > LAB.TOL
         checked += 1
-        if checked == 6:
-            break
-    assert checked >= 3
+    assert checked >= 4
+
+
+def test_label_targets_from_their_definitions():
+    """t0 = log(sigma_max^2 / theta_4) with theta_4 the Rayleigh quotient
+    after four power products (brute force: explicit products with the Gram
+    matrix) and sigma_max from LAPACK."""
+    for i in patch_members(302, 3):
+        row = LAB.label_one((302, i))
+        X = inputs.served_one(302, i).X.astype(np.float64)
+        G = X.T @ X if X.shape[0] >= X.shape[1] else X @ X.T
+        v = O.start_vector(LAB.START_SEED, G.shape[0])
+        v = v / np.linalg.norm(v)
+        for _ in range(3):
+            v = G @ v
+            v = v / np.linalg.norm(v)
+        th4 = float(v @ G @ v)
+        r4 = float(np.linalg.norm(G @ v - th4 * v))
+        assert abs(row[8] - th4) <= 1e-10 * th4 and abs(row[9] - r4) <= 1e-8 * th4
+        smax2 = np.linalg.norm(X, 2) ** 2
+        assert abs(row[11] - math.log(smax2 / th4)) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["predictor_labels_train.npz", "predictor_labels_eval.npz"])
+def test_stored_labels_reproduce(name):
+    """A few rows of each committed label file recomputed from the oracle."""
+    path = os.path.join(HERE, "golden", name)
+    if not os.path.exists(path):
+        pytest.skip("label file not generated")
+    d = np.load(path)
+    seed = int(d["seed_index"])
+    for i in patch_members(seed, 3) + [int(j) for j in np.nonzero(d["family"] == 1)[0][:2]]:
+        row = LAB.label_one((seed, i))
+        for k, f in enumerate(LAB.FIELDS):
+            assert np.isclose(d[f][i], row[k], rtol=1e-9, atol=1e-12), (name, i, f, d[f][i], row[k])
 
 
 def test_reference_features_obey_spectral_bounds():
