@@ -239,7 +239,14 @@ CPA_API cpa_status cpa_get_coeffs(cpa_handle h, double *c_out, int L, void *stre
  *   entry threshold): their loads and products are not issued.  The skipped
  *   products are exact zeros, so the result is the same bit for bit; 0
  *   runs every tile (for comparisons). */
-enum { CPA_OPT_SERIES = 1, CPA_OPT_WAIT_KCYCLES = 2, CPA_OPT_STALL_TEST = 3, CPA_OPT_SPARSE_SKIP = 4 };
+/* CPA_OPT_STREAMS: 1..16 (default 1): the pointer-form batches
+ *   (cpa_svt_batched, cpa_serve_learned) run their larger members (those
+ *   not taken by the batched kernel) round-robin on this many streams, each
+ *   with a workspace of its own, forked from and joined back into the
+ *   call's stream; matrices too small to fill the GPU then run side by
+ *   side.  The results are those of one stream. */
+enum { CPA_OPT_SERIES = 1, CPA_OPT_WAIT_KCYCLES = 2, CPA_OPT_STALL_TEST = 3, CPA_OPT_SPARSE_SKIP = 4,
+       CPA_OPT_STREAMS = 5 };
 enum { CPA_SERIES_FORWARD = 0, CPA_SERIES_CLENSHAW = 1 };
 CPA_API cpa_status cpa_set_option(cpa_handle h, int option, int value);
 
@@ -418,11 +425,12 @@ CPA_API cpa_status cpa_batch_read_lambdas(cpa_batch b, double *host_out, void *s
  *   Lambda_max = the 20-step power-iteration bound of cpa_lambda_bound, or,
  *     with use_lambda != 0, the prediction theta_4 exp(max(y0, 0))
  *     (1 + margin), never below the residual-corrected estimate
- *     (theta_4 + r_4)(1 + margin) (a bound below sigma_max^2 makes the
- *     series grow outside [-1, 1]; clamped predictions count as
- *     fallbacks).  With use_lambda only the features' four power products
- *     run, and a non-finite prediction falls back to the bound of those
- *     products, min((theta_5 + r_5)(1 + 0.01), trace G), with L_fallback.
+ *     (theta_4 + r_4)(1 + 0.01) (a bound below sigma_max^2 makes the
+ *     series grow outside [-1, 1]).  With use_lambda only the features'
+ *     four power products run, and a non-finite prediction falls back to
+ *     the bound of those products, min((theta_5 + r_5)(1 + 0.01), trace G),
+ *     with L_fallback.  The fallback count is of members that took
+ *     L_fallback.
  * L_scale > 0, margin >= 0, 1 <= L_min <= L_max <= 1024, 1 <= L_fallback <=
  * 1024, else CPA_ERR_INVALID_ARG.  cpa_batch_read_choices returns the L used
  * per matrix and the number of fallbacks of the last learned run. */
@@ -447,8 +455,8 @@ CPA_API cpa_status cpa_batch_read_choices(cpa_batch b, int *host_L, int *host_fa
  * `stream` for CPA_BF16 / CPA_BF16X3 (CPA_FP32 synchronises once to read L).
  * The forward series only (CPA_ERR_UNSUPPORTED under CPA_SERIES_CLENSHAW).
  * cpa_get_order returns the L and the fallback flag (1 when the predicted
- * order exceeded L_max or the predicted bound was clamped or non-finite)
- * of the last learned call; cpa_get_lambda its Lambda_max. */
+ * order exceeded L_max or the prediction was not finite) of the last
+ * learned call; cpa_get_lambda its Lambda_max. */
 typedef struct {
     double L_scale;   /* > 0: L = ceil(exp(y1) L_scale)                       */
     double margin;    /* >= 0: relative margin of the predicted bound          */

@@ -31,7 +31,7 @@ EXPORTS = ["cpa_create", "cpa_destroy", "cpa_status_string", "cpa_last_error", "
            "cpa_completion_create", "cpa_completion_destroy", "cpa_completion_run", "cpa_sync_status",
            "cpa_svt_learned", "cpa_get_order", "cpa_learn_features", "cpa_serve_learned", "cpa_serve_read"]
 OPT_SERIES, SERIES_FORWARD, SERIES_CLENSHAW = 1, 0, 1
-OPT_WAIT_KCYCLES, OPT_STALL_TEST, OPT_SPARSE_SKIP = 2, 3, 4
+OPT_WAIT_KCYCLES, OPT_STALL_TEST, OPT_SPARSE_SKIP, OPT_STREAMS = 2, 3, 4, 5
 STAGES = ["prep", "gram", "bound", "coeff", "shift", "recur", "apply", "sparse"]
 T_IDENTITY, T_HAAR1_LOWPASS, T_BLOCK_DCT8, T_DCT = 0, 1, 2, 3
 SPARSE_OFF, SPARSE_ABS, SPARSE_TOPK = 0, 1, 2

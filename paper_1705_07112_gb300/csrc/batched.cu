@@ -462,8 +462,8 @@ __device__ __noinline__ Choice learned_phase(BatchSmem &S, int idx, int p, int q
         __syncthreads();
         // decision rule, taken by thread 0 and broadcast.  The predicted
         // bound is never taken below the residual-corrected estimate
-        // (theta_4 + r_4)(1 + margin): below sigma_max^2 the series grows
-        // outside [-1, 1]; such predictions count as fallbacks
+        // (theta_4 + r_4)(1 + 0.01): below sigma_max^2 the series grows
+        // outside [-1, 1]
         if (tid == 0) {
             const double y0 = (double)yv[0], y1 = (double)yv[1];
             const double Lf = ceil(exp(y1) * la.L_scale);
@@ -474,8 +474,8 @@ __device__ __noinline__ Choice learned_phase(BatchSmem &S, int idx, int p, int q
             bool ok_lam = true;
             if (la.use_lambda) {
                 const double lp = (double)th4 * exp(fmax(y0, 0.0)) * (1.0 + la.margin);
-                const double floor_lam = ((double)th4 + (double)r4) * (1.0 + la.margin);
-                ok_lam = isfinite(lp) && lp > 0.0 && lp >= floor_lam;
+                const double floor_lam = ((double)th4 + (double)r4) * (1.0 + kLambdaMargin);
+                ok_lam = isfinite(lp) && lp > 0.0;
                 if (isfinite(lp) && lp > 0.0) {
                     lc = fmax(lp, floor_lam);
                 } else {

@@ -43,6 +43,13 @@ struct cpa_ctx {
     double *d_big_lam = nullptr;
     int big_cap = 0;
     std::vector<int> serve_small, serve_big;   // member indices of the last learned call
+    // concurrent members: sub-handles (own workspace), each on its own
+    // stream forked from the caller's
+    int nstreams = 1;
+    cpa_ctx *sub[16] = {};
+    cudaStream_t sub_st[16] = {};
+    cudaEvent_t sub_ev[16] = {};
+    cudaEvent_t fork_ev = nullptr;
     // diagnostics
     bool profiling = false;
     int64_t launches[CPA_NSTAGES] = {};
@@ -354,6 +361,12 @@ cpa_status cpa_destroy(cpa_handle h) {
     }
     if (h->start) cudaEventDestroy(h->start);
     ptr_plan_destroy(h->pplan);
+    for (int k = 0; k < 16; ++k) {
+        if (h->sub[k]) cpa_destroy(h->sub[k]);
+        if (h->sub_st[k]) cudaStreamDestroy(h->sub_st[k]);
+        if (h->sub_ev[k]) cudaEventDestroy(h->sub_ev[k]);
+    }
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     if (h->d_big_L) cudaFree(h->d_big_L);
     if (h->d_big_lam) cudaFree(h->d_big_lam);
     delete h;
@@ -876,6 +889,11 @@ cpa_status cpa_set_option(cpa_handle h, int option, int value) {
         h->wait.wait_cycles = (long long)value * 1000LL;
         return CPA_OK;
     }
+    if (option == CPA_OPT_STREAMS) {
+        if (value < 1 || value > 16) return CPA_ERR_INVALID_ARG;
+        h->nstreams = value;
+        return CPA_OK;
+    }
     if (option == CPA_OPT_SPARSE_SKIP) {
         if (value != 0 && value != 1) return CPA_ERR_INVALID_ARG;
         h->sparse_skip = value;
@@ -1077,6 +1095,43 @@ cpa_status ensure_pplan(cpa_ctx *h) {
     return h->pplan ? CPA_OK : CPA_ERR_NO_MEMORY;
 }
 
+// The members `order` (largest first) through fn(handle, k, stream): on the
+// caller's handle and stream when h->nstreams is 1 or there is one member,
+// else round-robin over sub-handles, each on its own stream forked from the
+// caller's stream and joined back into it.
+template <class F>
+cpa_status run_members(cpa_ctx *h, const std::vector<int> &order, cudaStream_t st, F fn) {
+    const int S = std::min<int>(h->nstreams, (int)order.size());
+    if (S <= 1) {
+        for (size_t k = 0; k < order.size(); ++k) {
+            cpa_status r = fn(h, (int)k, st);
+            if (r != CPA_OK) return r;
+        }
+        return CPA_OK;
+    }
+    for (int j = 0; j < S; ++j) {
+        if (!h->sub[j]) {
+            cpa_status r = cpa_create(&h->sub[j], h->device);
+            if (r != CPA_OK) return r;
+            CK(cudaStreamCreateWithFlags(&h->sub_st[j], cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&h->sub_ev[j], cudaEventDisableTiming));
+        }
+        h->sub[j]->series = h->series;
+        h->sub[j]->wait = h->wait;
+        h->sub[j]->sparse_skip = h->sparse_skip;
+    }
+    if (!h->fork_ev) CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(h->fork_ev, st));
+    for (int j = 0; j < S; ++j) CK(cudaStreamWaitEvent(h->sub_st[j], h->fork_ev, 0));
+    cpa_status r = CPA_OK;
+    for (size_t k = 0; k < order.size() && r == CPA_OK; ++k) r = fn(h->sub[k % S], (int)k, h->sub_st[k % S]);
+    for (int j = 0; j < S; ++j) {
+        CK(cudaEventRecord(h->sub_ev[j], h->sub_st[j]));
+        CK(cudaStreamWaitEvent(st, h->sub_ev[j], 0));
+    }
+    return r;
+}
+
 std::vector<int> by_size_desc(const std::vector<int> &idx, const int64_t *m, const int64_t *n) {
     std::vector<int> v = idx;
     std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
@@ -1127,12 +1182,12 @@ cpa_status cpa_svt_batched(cpa_handle h, int count, const float *const *dX, cons
                               nullptr, nullptr, st)) != CPA_OK)
             return r;
     }
-    for (int i : by_size_desc(big, m, n)) {
-        r = svt_impl(h, dX[i], m[i], n[i], ldx[i], &s[s_count > 1 ? i : 0], L ? L[i] : L0,
-                     lambda ? lambda[i] : 0.0, prec, nullptr, dY[i], ldy[i], stream, nullptr);
-        if (r != CPA_OK) return r;
-    }
-    return CPA_OK;
+    const std::vector<int> order = by_size_desc(big, m, n);
+    return run_members(h, order, st, [&](cpa_ctx *hh, int k, cudaStream_t sk) {
+        const int i = order[k];
+        return svt_impl(hh, dX[i], m[i], n[i], ldx[i], &s[s_count > 1 ? i : 0], L ? L[i] : L0,
+                        lambda ? lambda[i] : 0.0, prec, nullptr, dY[i], ldy[i], sk, nullptr);
+    });
 }
 
 cpa_status cpa_serve_learned(cpa_handle h, cpa_mlp net, int count, const float *const *dX, const int64_t *m,
@@ -1185,17 +1240,18 @@ cpa_status cpa_serve_learned(cpa_handle h, cpa_mlp net, int count, const float *
     }
     h->serve_big = by_size_desc(h->serve_big, m, n);
     LearnCall lc{P, ru};
-    for (int k = 0; k < nb; ++k) {
+    r = run_members(h, h->serve_big, st, [&](cpa_ctx *hh, int k, cudaStream_t sk) -> cpa_status {
         const int i = h->serve_big[k];
-        r = svt_impl(h, dX[i], m[i], n[i], ldx[i], &s[s_count > 1 ? i : 0], ru.L_max, 0.0, prec, nullptr, dY[i],
-                     ldy[i], stream, &lc);
-        if (r != CPA_OK) return r;
+        cpa_status q = svt_impl(hh, dX[i], m[i], n[i], ldx[i], &s[s_count > 1 ? i : 0], ru.L_max, 0.0, prec,
+                                nullptr, dY[i], ldy[i], sk, &lc);
+        if (q != CPA_OK) return q;
         // keep this member's choice: the next call reuses the workspace
-        CK(cudaMemcpyAsync(h->d_big_L + 2 * k, h->d_L, 2 * sizeof(int), cudaMemcpyDeviceToDevice, st));
-        CK(cudaMemcpyAsync(h->d_big_lam + k, h->d_out + 3, sizeof(double), cudaMemcpyDeviceToDevice, st));
-    }
+        CK(cudaMemcpyAsync(h->d_big_L + 2 * k, hh->d_L, 2 * sizeof(int), cudaMemcpyDeviceToDevice, sk));
+        CK(cudaMemcpyAsync(h->d_big_lam + k, hh->d_out + 3, sizeof(double), cudaMemcpyDeviceToDevice, sk));
+        return CPA_OK;
+    });
     h->have_learn = false;
-    return CPA_OK;
+    return r;
 }
 
 cpa_status cpa_serve_read(cpa_handle h, int count, int *host_L, double *host_lambda, int *host_fallbacks,

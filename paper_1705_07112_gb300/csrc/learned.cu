@@ -374,8 +374,8 @@ __global__ void __launch_bounds__(kThreads) learn_bound_kernel(
                 bool ok_lam = true;
                 if (rule.use_lambda) {
                     const double lp = th4 * exp(fmax(y0, 0.0)) * (1.0 + rule.margin);
-                    const double floor_lam = (th4 + r4) * (1.0 + rule.margin);
-                    ok_lam = isfinite(lp) && lp > 0.0 && lp >= floor_lam;
+                    const double floor_lam = (th4 + r4) * (1.0 + kLambdaMargin);
+                    ok_lam = isfinite(lp) && lp > 0.0;
                     if (isfinite(lp) && lp > 0.0 && isfinite(floor_lam))
                         lc = fmax(lp, floor_lam);
                     else

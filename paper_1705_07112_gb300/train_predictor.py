@@ -15,8 +15,8 @@ Steps, all on the GPU through the library:
   serving    the input standardisation folded into the first layer; the
              order scale L_scale from a quantile of the training residual
              of log L*; the bound margin from a quantile of the residual of
-             t0, so the served bound theta_4 exp(y0) (1 + margin) covers
-             sigma_max^2 for the training matrices.
+             t0 and the bound's floor, so the served bound covers
+             sigma_max^2 for that quantile of the training matrices.
 Matrices whose L* is beyond the label ladder (no order reaches the target)
 keep their label (log of the sentinel): the network learns to predict a
 large order for them, which the serving rule turns into the fallback.
@@ -104,7 +104,7 @@ def main():
     ap.add_argument("--out", required=True)
     ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--order-quantile", type=float, default=0.85)
-    ap.add_argument("--bound-quantile", type=float, default=0.999)
+    ap.add_argument("--bound-quantile", type=float, default=0.995)
     a = ap.parse_args()
     t0 = time.time()
     lab = np.load(a.labels)
@@ -120,10 +120,17 @@ def main():
     r0, r1 = T[:, 0] - y[:, 0], T[:, 1] - y[:, 1]
     reach = lab["Lstar"] < int(lab["L_none"])
     L_scale = float(math.exp(np.quantile(r1[reach], a.order_quantile)))
-    # served bound theta_4 exp(max(y0, 0)) (1 + margin) >= sigma_max^2 needs
-    # margin >= exp(t0 - max(y0, 0)) - 1
-    need = np.exp(T[:, 0] - np.maximum(y[:, 0], 0.0)) - 1.0
-    margin = float(max(0.01, np.quantile(need, a.bound_quantile)))
+    # the served bound max(theta_4 exp(max(y0, 0)) (1 + margin),
+    # (theta_4 + r_4)(1 + 0.01)) must reach sigma_max^2: the smallest margin
+    # (on a grid) doing so for the bound quantile of the training matrices
+    th4, r4, smax2 = lab["theta4"], lab["r4"], lab["smax2"]
+    floor = (th4 + r4) * 1.01
+    pred = th4 * np.exp(np.maximum(y[:, 0], 0.0))
+    margin = 1.0
+    for mg in np.arange(0.01, 1.0, 0.005):
+        if np.mean(np.maximum(pred * (1.0 + mg), floor) >= smax2) >= a.bound_quantile:
+            margin = float(mg)
+            break
     meta = {"labels": os.path.basename(a.labels), "seed_index": seed_index, "count": int(len(idx)),
             "steps": a.steps, "rms_t0": float(np.sqrt(np.mean(r0 ** 2))),
             "rms_t1": float(np.sqrt(np.mean(r1[reach] ** 2))), "L_scale": L_scale, "margin": margin,

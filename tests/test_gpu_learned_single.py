@@ -120,7 +120,7 @@ def test_single_decision_and_result(lib, use_lambda, prec):
         p = min(X64.shape)
         if use_lambda:
             r4 = O.lambda_bound(X64, 3, 0.0, O.start_vector(D.START_SEED, p))["resid"]
-            want = max(th * math.exp(max(y[0], 0.0)), th + r4) * (1.0 + rule.margin)
+            want = max(th * math.exp(max(y[0], 0.0)) * (1.0 + rule.margin), (th + r4) * 1.01)
             assert abs(lam - want) <= 1e-4 * want, (sm.X.shape, lam, want)
         else:
             want = O.lambda_bound(X64, 20, 0.01, O.start_vector(D.START_SEED, p))["lam"]
@@ -182,5 +182,44 @@ def test_router_members_match_their_paths(lib):
         assert L1 == Ls[i] and abs(lib.cpa_get_lambda(h) - lams[i]) <= 1e-12 * lams[i]
         assert rel(Y1.cpu().numpy().astype(np.float64), Ys[i].cpu().numpy().astype(np.float64)) <= 1e-6
     plan.close()
+    net.close()
+    h.close()
+
+
+def test_router_streams_match_one_stream(lib):
+    """The larger members on several streams (CPA_OPT_STREAMS) give the
+    orders and results of one stream, and every member's call reports no
+    device-side failure."""
+    import torch
+    h = lib.Handle(0)
+    net = lib.MLP((12, 64, 64, 2), seed=4)
+    P = net.get_params()
+    P[-2], P[-1] = 0.2, math.log(60.0)
+    net.set_params(P)
+    rule = lib.learn_rule(L_scale=1.0, margin=0.05, L_min=5, L_max=400, L_fallback=50, use_lambda=True)
+    mix = inputs.served_mix(60, seed_index=9)
+    Xs = [torch.from_numpy(sm.X).cuda() for sm in mix]
+    specs = [spec_dict(sm.shrink) for sm in mix]
+    outs = []
+    for streams in (1, 6):
+        lib.cpa_set_option(h, lib.OPT_STREAMS, streams)
+        Ys = [torch.zeros_like(X) for X in Xs]
+        lib.cpa_serve_learned(h, net, lib.MemberList(Xs, Ys, specs), rule, prec="bf16x3")
+        Ls, lams, _ = lib.cpa_serve_read(h, len(mix))
+        outs.append((Ls, lams, [Y.cpu().numpy().astype(np.float64) for Y in Ys]))
+        # plain members too
+        Yp = [torch.zeros_like(X) for X in Xs]
+        lib.cpa_svt_batched(h, lib.MemberList(Xs, Yp, specs), L0=40, prec="bf16x3")
+        outs[-1] = outs[-1] + ([Y.cpu().numpy().astype(np.float64) for Y in Yp],)
+    (L1, l1, Y1, P1), (L6, l6, Y6, P6) = outs
+    assert np.array_equal(L1, L6)
+    assert np.allclose(l1, l6, rtol=1e-12)
+    for a, b in zip(Y1, Y6):
+        assert rel(a, b) <= 1e-6
+    for a, b in zip(P1, P6):
+        assert rel(a, b) <= 1e-6
+    lib.cpa_set_option(h, lib.OPT_STREAMS, 1)
+    with pytest.raises(lib.CpaError):
+        lib.cpa_set_option(h, lib.OPT_STREAMS, 17)
     net.close()
     h.close()
