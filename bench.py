@@ -773,7 +773,7 @@ def run_gpu_served(args, world, rank, local):
     cpa._lib.cpa_set_option(h, cpa._lib.OPT_STREAMS, args.streams)
     net, pred = train_predictor.load_predictor()
     rule = cpa.learn_rule(L_scale=pred["L_scale"], margin=pred["margin"], L_min=4, L_max=args.served_L_max,
-                          L_fallback=50, use_lambda=True)
+                          L_fallback=50, use_lambda=args.predicted_bound)
     ml = cpa.MemberList(Xs, Yl, specs)
     mp_ = cpa.MemberList(Xs, Yp, specs)
     stream = torch.cuda.current_stream(dev)
@@ -840,10 +840,10 @@ def _served_finish(args, world, rank, local, cpa, h, net, rule, mix, Xs, Yl, Yp,
 
     err_l = judged(Yl)
     frac_l = float(np.mean(err_l <= SERVED_TOL))
-    # the learned order with the 20-step power bound instead of the
-    # predicted one (same network and order rule), for comparison
+    # the learned order with the other bound (the predicted one when the
+    # 20-step power bound is served, and the reverse), for comparison
     rule_pb = cpa.learn_rule(L_scale=rule.L_scale, margin=rule.margin, L_min=rule.L_min, L_max=rule.L_max,
-                             L_fallback=rule.L_fallback, use_lambda=False)
+                             L_fallback=rule.L_fallback, use_lambda=not args.predicted_bound)
     ms_pb = max_over_ranks(world, timed(lambda: cpa.cpa_serve_learned(h, net, _ml_cache(cpa, Xs, Yl, specs), rule_pb,
                                                                       prec="bf16x3", stream=stream), 1), dev)
     frac_pb = float(np.mean(judged(Yl) <= SERVED_TOL))
@@ -914,7 +914,9 @@ def _served_finish(args, world, rank, local, cpa, h, net, rule, mix, Xs, Yl, Yp,
            "kinds": "hard / soft / weighted soft, a third each, tau = U[1.2, 3] x noise edge",
            "tolerance": SERVED_TOL, "learned": {"prec": "bf16x3", "L_max": rule.L_max, "L_scale": rule.L_scale,
                                                 "margin": rule.margin, "fallback_L": rule.L_fallback,
-                                                "lambda": "predicted, floored at (theta_4 + r_4)(1 + margin)"},
+                                                "lambda": ("predicted, floored at (theta_4 + r_4)(1 + 0.01)"
+                                                           if args.predicted_bound else
+                                                           "20-step power bound (+1 %)")},
            "predictor": pred["meta"], "judged_sample": len(sample), "streams": args.streams,
            "inputs": "%d distinct matrices, %.0f MB > L2 (129 MB)" % (count, nbytes / 1e6),
            "parallelism": "replicas x%d" % world}
@@ -925,8 +927,11 @@ def _served_finish(args, world, rank, local, cpa, h, net, rule, mix, Xs, Yl, Yp,
             "gpu_launches": int(round(args.steps * (sum(v["launches"] for v in prof.values()) + 1))),
             "learned": {"matrices_per_s": rate_l, "frac_within_tol": frac_l, "good_per_s": value,
                         "mean_L": float(Ls_np.mean()), "median_L": float(np.median(Ls_np)),
-                        "fallbacks": int(nfb), "median_err": float(np.median(err_l))},
-            "learned_power_bound": {"matrices_per_s": rate_pb, "frac_within_tol": frac_pb,
+                        "fallbacks": int(nfb), "median_err": float(np.nanmedian(err_l)),
+                        "nonfinite": int(np.sum(~np.isfinite(err_l))),
+                        "bound": "predicted" if args.predicted_bound else "20-step power bound"},
+            "learned_other_bound": {"bound": "20-step power bound" if args.predicted_bound else "predicted",
+                                    "matrices_per_s": rate_pb, "frac_within_tol": frac_pb,
                                     "good_per_s": rate_pb * frac_pb},
             "plain_fp32": {"L": L_plain, "matrices_per_s": rate_p, "frac_within_tol": frac_p,
                            "good_per_s": rate_p * frac_p, "order_rule": "the best measured good_per_s of the orders",
@@ -1202,6 +1207,8 @@ def main():
     ap.add_argument("--served", type=int, default=5000, help="matrices of the served mix")
     ap.add_argument("--served-L-max", type=int, default=512)
     ap.add_argument("--streams", type=int, default=8, help="concurrent streams for the served mix's larger members")
+    ap.add_argument("--predicted-bound", action="store_true",
+                    help="serve the predictor's Lambda_max instead of the 20-step power bound")
     ap.add_argument("--plain-orders", type=lambda v: [int(x) for x in v.split(",")], default=[64, 128, 256])
     ap.add_argument("--judge", type=int, default=160, help="matrices judged against the exact shrinkage")
     ap.add_argument("--plain-steps", type=int, default=1)
