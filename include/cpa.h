@@ -383,9 +383,11 @@ CPA_API cpa_status cpa_batch_destroy(cpa_batch b);
  *   lambda: NULL to compute each bound on the device (power iteration with
  *      `iters` steps, definition of cpa_lambda_bound), or a DEVICE array of
  *      count doubles.
- *   prec: CPA_FP32 (FP32 FMA) or CPA_BF16 / CPA_BF16X3 (tensor cores with the
- *      BF16 hi/lo split in every product: at these sizes the single-BF16
- *      recurrence would cost accuracy and save nothing).
+ *   prec: CPA_FP32 (FP32 FMA on the CUDA cores) or CPA_BF16 / CPA_BF16X3
+ *      (tcgen05 tensor cores, one 128-row tile per member with the
+ *      recurrence state in tensor memory, the BF16 hi/lo split in every
+ *      product: at these sizes the single-BF16 recurrence would cost
+ *      accuracy and save nothing).
  * Asynchronous on `stream`.  The shrink parameters are uploaded on the first
  * run of a plan and whenever they change: such a run synchronises `stream`
  * first and cannot be captured in a CUDA graph; runs with unchanged
@@ -471,9 +473,10 @@ CPA_API cpa_status cpa_get_order(cpa_handle h, int *L_out, int *fallback, void *
  * Batches given member by member: device pointers, shapes, leading
  * dimensions (elements, row-major) and orders per matrix, following the
  * problem statement of Algorithm 1 for each member.  Members with
- * min(m, n) <= 64, max(m, n) <= 128 and L <= 1024 (patch groups) run in one
- * persistent launch of the batched kernel; the others run through the
- * single-matrix path one after another on `stream`.  Asynchronous; the
+ * min(m, n) <= 128, max(m, n) <= 256 (CPA_BF16 / CPA_BF16X3; min <= 64, max
+ * <= 128 for CPA_FP32) and L <= 1024 run in one persistent launch of the
+ * batched kernel; the others run through the single-matrix path (on
+ * CPA_OPT_STREAMS streams).  Asynchronous; the
  * descriptor table is uploaded on `stream` from pinned staging owned by the
  * handle (a later call waits until the previous upload has been read).
  * Members' X and Y must not overlap.  Errors: INVALID_ARG (any member),

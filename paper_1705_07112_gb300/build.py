@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcpa.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["cpa_api.cu", "gemm_simt.cu", "gemm_tc.cu", "kernels_aux.cu", "batched.cu", "noalloc.cu", "sparsify.cu", "mlp.cu", "admm.cu", "completion.cu", "learned.cu"]
+SOURCES = ["cpa_api.cu", "gemm_simt.cu", "gemm_tc.cu", "kernels_aux.cu", "batched.cu", "noalloc.cu", "sparsify.cu", "mlp.cu", "admm.cu", "completion.cu", "learned.cu", "batched_tc.cu"]
 
 
 def nvcc() -> str:
@@ -29,7 +29,8 @@ def _flags():
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "internal.h"), os.path.join(HERE, "..", "include", "cpa.h")]
+    deps = [src, os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "tc_ptx.h"),
+            os.path.join(HERE, "..", "include", "cpa.h")]
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps if os.path.exists(d))
 
 

@@ -41,15 +41,6 @@ constexpr int kThreads = 128;
 constexpr int kMaxBatchTerms = 1024;
 constexpr uint64_t kEdgeSeedXor = 0x5EEDULL;   // start vector of the lower-edge feature
 
-struct BatchDesc {
-    int64_t off;   // element offset of X (and Y) in the packed buffers
-    int m, n, L, pad;
-    // per-matrix operands (pointer form): X and Y with their own row
-    // strides; null x: the packed buffers at `off` with row stride n
-    const float *x;
-    float *y;
-    int64_t ldx, ldy;
-};
 
 // ---------------------------------------------------------------- PTX helpers
 
@@ -299,16 +290,6 @@ __device__ __forceinline__ float *zbuf_f32(BatchSmem &S, int b) {
 constexpr int kFeatures = 12;
 constexpr int kHidden = 64;   // the predictor network: kFeatures -> 64 -> 64 -> 2
 
-// Learned selection inside the batched launch: the network's parameters
-// (layout W1[64][12], b1, W2[64][64], b2, W3[2][64], b3) and the rule that
-// maps its outputs (y0, y1) to (Lambda_max, L).
-struct LearnArgs {
-    const float *P;
-    double L_scale, margin;
-    int L_min, L_max, L_fallback, use_lambda;
-    int *L_out;       // L chosen per matrix
-    int *nfallback;   // matrices that took the fallback
-};
 
 // Features of one matrix (FEAT: written out, returns L = -1) or the learned
 // choice of (Lambda_max, L) for it (LEARN).  Kept out of line so that the
@@ -949,6 +930,12 @@ struct BatchRun {
 template <bool TC, bool FEAT, bool LEARN>
 cpa_status launch_run(const BatchRun &b, const float *dX, float *dY, int s_count, const double *lambda, int iters,
                       const int *L_override, float *feat, double *theta, const LearnArgs &la, cudaStream_t st) {
+    if (TC && !FEAT) {
+        // tensor-core products (tcgen05, state in tensor memory)
+        BCK(launch_batched_tc(b.desc, b.order, b.count, dX, dY, b.shrink, s_count > 1 ? 1 : 0, lambda, b.lambda_out,
+                              iters, b.status, L_override, la, LEARN, b.num_sms, st));
+        return CPA_OK;
+    }
     const size_t smem = sizeof(BatchSmem);
     auto kern = batched_kernel<TC, FEAT, LEARN>;
     BCK(ensure_smem_limit((const void *)kern, (int)smem));

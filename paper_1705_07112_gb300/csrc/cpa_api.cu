@@ -1073,8 +1073,11 @@ cpa_status cpa_svt_host(cpa_handle h, int count, const float *const *hX, int64_t
 
 namespace {
 
-bool patch_sized(int64_t m, int64_t n, int L) {
-    return std::min(m, n) <= 64 && std::max(m, n) <= 128 && L <= batched_max_terms();
+// Members the batched launch takes: the tensor-core kernel holds p <= 128,
+// q <= 256, the CUDA-core (FP32) kernel p <= 64, q <= 128.
+bool patch_sized(int64_t m, int64_t n, int L, int prec) {
+    const int64_t P = prec == CPA_FP32 ? 64 : kTcBatchP, Q = prec == CPA_FP32 ? 128 : kTcBatchQ;
+    return std::min(m, n) <= P && std::max(m, n) <= Q && L <= batched_max_terms();
 }
 
 cpa_status check_members(int count, const float *const *dX, const int64_t *m, const int64_t *n, const int64_t *ldx,
@@ -1162,7 +1165,7 @@ cpa_status cpa_svt_batched(cpa_handle h, int count, const float *const *dX, cons
     if ((r = set_device(h)) != CPA_OK) return r;
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<int> small, big;
-    for (int i = 0; i < count; ++i) (patch_sized(m[i], n[i], L ? L[i] : L0) ? small : big).push_back(i);
+    for (int i = 0; i < count; ++i) (patch_sized(m[i], n[i], L ? L[i] : L0, prec) ? small : big).push_back(i);
     if (!small.empty()) {
         if ((r = ensure_pplan(h)) != CPA_OK) return r;
         std::vector<PtrItem> items(small.size());
@@ -1211,7 +1214,7 @@ cpa_status cpa_serve_learned(cpa_handle h, cpa_mlp net, int count, const float *
     cudaStream_t st = (cudaStream_t)stream;
     h->serve_small.clear();
     h->serve_big.clear();
-    for (int i = 0; i < count; ++i) (patch_sized(m[i], n[i], 1) ? h->serve_small : h->serve_big).push_back(i);
+    for (int i = 0; i < count; ++i) (patch_sized(m[i], n[i], 1, prec) ? h->serve_small : h->serve_big).push_back(i);
     if (!h->serve_small.empty()) {
         if ((r = ensure_pplan(h)) != CPA_OK) return r;
         std::vector<PtrItem> items(h->serve_small.size());

@@ -222,6 +222,41 @@ cudaError_t learn_bound(const float *G, int64_t ldg, int p, int q, const ShrinkP
                         double *tabg, unsigned int *bar, int *err, double *out, int *L_out, float *feat,
                         double *theta_out, double *coef, cudaStream_t st, int num_sms, const WaitPolicy &wp);
 
+// One member of a batched launch: element offset of X (and Y) in packed
+// buffers, shape, order; or (pointer form, x != null) its own X and Y with
+// row strides.
+struct BatchDesc {
+    int64_t off;   // element offset of X (and Y) in the packed buffers
+    int m, n, L, pad;
+    // per-matrix operands (pointer form): X and Y with their own row
+    // strides; null x: the packed buffers at `off` with row stride n
+    const float *x;
+    float *y;
+    int64_t ldx, ldy;
+};
+
+// Learned selection inside the batched launch: the network's parameters
+// (layout W1[64][12], b1, W2[64][64], b2, W3[2][64], b3) and the rule that
+// maps its outputs (y0, y1) to (Lambda_max, L).
+struct LearnArgs {
+    const float *P;
+    double L_scale, margin;
+    int L_min, L_max, L_fallback, use_lambda;
+    int *L_out;       // L chosen per matrix
+    int *nfallback;   // matrices that took the fallback
+};
+
+
+// Tensor-core batched launch (batched_tc.cu): members with min(m, n) <= 128
+// and max(m, n) <= 256, every product with the BF16 hi/lo split on tcgen05
+// tiles, the recurrence state in tensor memory, one CTA per member at a
+// time.  Arguments as the batched kernel's (learn: the learned choice).
+constexpr int kTcBatchP = 128, kTcBatchQ = 256;
+cudaError_t launch_batched_tc(const BatchDesc *desc, const int *order, int count, const float *X, float *Y,
+                              const ShrinkParams *shr, int shr_stride, const double *lam_in, double *lam_out,
+                              int iters, int *status, const int *L_in, const LearnArgs &la, bool learn,
+                              int num_sms, cudaStream_t st);
+
 // Pointer form of the batched launch (batched.cu).  One member: device X
 // (m x n, row stride ldx) and Y (row stride ldy), order L, its shrinkage.
 // Members must satisfy min(m, n) <= 64, max(m, n) <= 128, L <=

@@ -157,8 +157,16 @@ def test_router_members_match_their_paths(lib):
     mem = lib.MemberList(Xs, Ys, specs)
     lib.cpa_serve_learned(h, net, mem, rule, prec="bf16x3")
     Ls, lams, nfb = lib.cpa_serve_read(h, len(mix))
-    small = [i for i, sm in enumerate(mix) if min(sm.X.shape) <= 64 and max(sm.X.shape) <= 128]
-    assert 0 < len(small) < len(mix)
+    # members the batched kernel takes (tensor cores: p <= 128, q <= 256);
+    # the plan form holds the patch-sized ones among them
+    batched = [i for i, sm in enumerate(mix) if min(sm.X.shape) <= 128 and max(sm.X.shape) <= 256]
+    small = [i for i in batched if min(mix[i].X.shape) <= 64 and max(mix[i].X.shape) <= 128]
+    assert 0 < len(small) and len(batched) < len(mix)
+    for i in batched:
+        sp = mix[i].shrink
+        ref = O.cpa(mix[i].X.astype(np.float64), O.Shrink(sp.kind, sp.tau, sp.c, sp.eps, sp.noise), int(Ls[i]),
+                    float(lams[i]))
+        assert rel(Ys[i].cpu().numpy().astype(np.float64), ref) <= TOL["bf16x3"], (mix[i].X.shape, Ls[i])
     plan = lib.BatchPlan(h, [mix[i].X.shape for i in small], L0=24)
     Xp = torch.from_numpy(np.concatenate([mix[i].X.ravel() for i in small])).cuda()
     Yp = lib.cpa_svt_batched_learned(h, plan, net, Xp, [specs[i] for i in small], L_scale=rule.L_scale,
@@ -173,7 +181,7 @@ def test_router_members_match_their_paths(lib):
         assert Ls[i] == Lp[k]
         o += m * n
     for i in range(len(mix)):
-        if i in small:
+        if i in batched:
             continue
         Y1 = lib.cpa_svt_learned(h, net, Xs[i], specs[i], rule, prec="bf16x3")
         L1, _ = lib.cpa_get_order(h)
