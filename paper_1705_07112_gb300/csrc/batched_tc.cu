@@ -17,7 +17,11 @@
 // reads the accumulator and the state from tensor memory, forms
 //   Psi_k = 2 At Psi_{k-1} - 2 Psi_{k-1} - Psi_{k-2},  H += c_k Psi_k
 // in FP32, writes Psi_k back in place of Psi_{k-2} and its BF16 parts into
-// the operand tile of the next product.  Lambda_max (power iteration, FP32
+// the operand tile of the next product.  The products read the operand's
+// rows, A B^T, so G and every Psi_k are kept exactly symmetric (each takes
+// its upper triangle's values, exchanged through shared memory), as the
+// single-matrix tensor-core path does by mirroring upper tiles.  Lambda_max
+// (power iteration, FP32
 // with the FP64 final step), the coefficients (FP64 sums) and the learned
 // choice follow the definitions of the CUDA-core batched kernel.
 #include <algorithm>
@@ -394,6 +398,13 @@ __global__ void __launch_bounds__(kT, 1)
                     if (c0 + e < p) g[tid * kLdG + c0 + e] = a[e];
         }
         __syncthreads();
+        // exactly symmetric G: the lower triangle takes the upper one (the
+        // products below multiply by the operand's rows, A B^T, which is
+        // A B only for an exactly symmetric B; rounding asymmetry would grow
+        // along the recurrence)
+        if (own)
+            for (int j = 0; j < tid; ++j) g[tid * kLdG + j] = g[j * kLdG + tid];
+        __syncthreads();
 
         // ---- Lambda_max: power iteration (definition of cpa_lambda_bound)
         double lam = lam_in ? lam_in[idx] : 0.0;
@@ -515,23 +526,36 @@ __global__ void __launch_bounds__(kT, 1)
             if (!alive) break;
             const float ck = S.coef[k];
             const uint32_t sPrev = ((k - 1) & 1) ? cPSI1 : cPSI0, sOld = (k & 1) ? cPSI1 : cPSI0;
+            // pass 1: row tid of 2 At Psi_{k-1} - 2 Psi_{k-1} - Psi_{k-2} into
+            // the FP32 scratch (the Gram matrix's space, free after the shift)
+            float *w = reinterpret_cast<float *>(R1);
             for (int c0 = 0; c0 < Np; c0 += 32) {
-                float a[32], z1[32], z0[32], hh[32];
+                float a[32], z1[32], z0[32];
                 tmem_ld32(trow + cACC + c0, a);
                 tmem_ld32(trow + sPrev + c0, z1);
                 tmem_ld32(trow + sOld + c0, z0);
+                if (own)
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        w[tid * kLdG + c0 + e] = fmaf(2.f, a[e], fmaf(-2.f, z1[e], -z0[e]));
+            }
+            __syncthreads();
+            // pass 2: Psi_k exactly symmetric (the upper triangle's values),
+            // into the ring, the running sum and the next product's operand
+            for (int c0 = 0; c0 < Np; c0 += 32) {
+                float v[32], hh[32];
                 tmem_ld32(trow + cH + c0, hh);
 #pragma unroll
                 for (int e = 0; e < 32; ++e) {
-                    const bool in = own && c0 + e < p;
-                    const float v = in ? fmaf(2.f, a[e], fmaf(-2.f, z1[e], -z0[e])) : 0.f;
-                    z0[e] = v;
-                    hh[e] = in ? fmaf(ck, v, hh[e]) : 0.f;
+                    const int j = c0 + e;
+                    const bool in = own && j < p;
+                    v[e] = in ? (j >= tid ? w[tid * kLdG + j] : w[j * kLdG + tid]) : 0.f;
+                    hh[e] = in ? fmaf(ck, v[e], hh[e]) : 0.f;
                 }
-                tmem_st32(trow + sOld + c0, z0);
+                tmem_st32(trow + sOld + c0, v);
                 tmem_st32(trow + cH + c0, hh);
 #pragma unroll
-                for (int u = 0; u < 32; u += 8) put8(R1 + kPsiHi, R1 + kPsiLo, kSlice128, tid, c0 + u, z0 + u);
+                for (int u = 0; u < 32; u += 8) put8(R1 + kPsiHi, R1 + kPsiLo, kSlice128, tid, c0 + u, v + u);
             }
         }
         if (!alive) break;
