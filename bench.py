@@ -428,6 +428,8 @@ def run_gpu_batched(args, world, rank, local):
     plan = cpa.BatchPlan(h, shapes, L0=L)
     shr = cpa.ShrinkArray(specs)   # marshalled once, not per call
     stream = torch.cuda.current_stream(dev)
+    # the plan's launch configuration: from the tuning cache, else timed
+    tuned, tune_ms = plan.tune(h, X, shr, prec=args.prec, reps=3, Y=Y, cache=args.tune_cache, stream=stream)
 
     def step():
         cpa.cpa_svt_batched_plan(h, plan, X, shr, prec=args.prec, Y=Y, stream=stream)
@@ -488,7 +490,8 @@ def run_gpu_batched(args, world, rank, local):
     launch_ms = ms_max / args.steps
     tflops = flops / (launch_ms / 1e3) / 1e12
     gbs = 2.0 * nbytes / (launch_ms / 1e3) / 1e9
-    roof = {"kernel": "batched_kernel (persistent, one launch per step)", "bound": "hbm",
+    roof = {"kernel": "batched launch (persistent, %s, one launch per step)" % ["mma.sync", "tcgen05"][tuned[0]],
+            "bound": "hbm",
             "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
             "traffic": None, "bytes_per_launch": 2.0 * nbytes, "ms_per_launch": launch_ms,
             "tensor_tflops_dense_equiv": tflops,
@@ -498,6 +501,8 @@ def run_gpu_batched(args, world, rank, local):
            "L": L, "shrink": "weighted_soft", "c": 0.3, "prec": args.prec, "cuda_graph": g is not None,
            "lambda_max": "device power iteration per matrix, 20 steps, +1% margin",
            "inputs": "one packed batch of %.0f MB > L2 (129 MB)" % (nbytes / 1e6),
+           "launch_config": {"variant": ["mma.sync", "tcgen05"][tuned[0]], "ctas_per_sm": tuned[1],
+                             "order": ["size", "given"][tuned[2]], "candidate_ms": tune_ms},
            "parallelism": "replicas x%d" % world}
     line = {"metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": launch_ms, "higher_is_better": True, "scaling": "weak",
@@ -1212,6 +1217,7 @@ def main():
     ap.add_argument("--plain-orders", type=lambda v: [int(x) for x in v.split(",")], default=[64, 128, 256])
     ap.add_argument("--judge", type=int, default=160, help="matrices judged against the exact shrinkage")
     ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--tune-cache", default=None, help="JSON cache of tuned batched launch configurations")
     ap.add_argument("--ref-served", type=int, default=64, help="served-mix matrices per reference step")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -396,6 +396,30 @@ CPA_API cpa_status cpa_svt_batched_plan(cpa_handle h, cpa_batch b, const float *
                            int s_count, const double *lambda, int iters, int prec, float *dY,
                            void *stream);
 
+/* Launch configuration of a plan (no counterpart in the paper).
+ *   variant: CPA_BATCH_MMA_SYNC (warp-level BF16 MMA, state in registers,
+ *     up to 2 CTAs per SM) or CPA_BATCH_TCGEN05 (one 128-row tcgen05 tile
+ *     per member, state in tensor memory, 1 CTA per SM); CPA_FP32 runs
+ *     always take the FP32 CUDA-core form of the first.
+ *   ctas_per_sm: CTAs per SM of the mma.sync kernel (1 or 2; 0: its
+ *     occupancy limit).
+ *   order: CPA_ORDER_SIZE (largest estimated work first, the default) or
+ *     CPA_ORDER_GIVEN (the plan's own order).
+ * Defaults: CPA_BATCH_MMA_SYNC, 0, CPA_ORDER_SIZE.
+ * cpa_batch_tune times every configuration on the given data (one warm-up
+ * and `reps` timed runs each, CUDA events on `stream`; synchronises),
+ * keeps the fastest in the plan and returns it in chosen[3]; ms (optional,
+ * 8 doubles) receives the mean time of each candidate, slot variant * 4 +
+ * (ctas_per_sm - 1) * 2 + order, negative for candidates not run (the
+ * tcgen05 variant runs at 1 CTA per SM, and not for CPA_FP32).  dY receives
+ * the last run's output. */
+enum { CPA_BATCH_MMA_SYNC = 0, CPA_BATCH_TCGEN05 = 1 };
+enum { CPA_ORDER_SIZE = 0, CPA_ORDER_GIVEN = 1 };
+CPA_API cpa_status cpa_batch_set_config(cpa_batch b, int variant, int ctas_per_sm, int order);
+CPA_API cpa_status cpa_batch_get_config(cpa_batch b, int *variant, int *ctas_per_sm, int *order);
+CPA_API cpa_status cpa_batch_tune(cpa_handle h, cpa_batch b, const float *dX, const cpa_shrink *s, int s_count,
+                                  int prec, float *dY, int reps, int *chosen, double *ms, void *stream);
+
 /* Per-matrix Lambda_max used by the last run of the plan (device array of
  * count doubles owned by the plan; valid until cpa_batch_destroy). */
 CPA_API const double *cpa_batch_lambdas(cpa_batch b);

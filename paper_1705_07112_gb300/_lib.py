@@ -29,7 +29,10 @@ EXPORTS = ["cpa_create", "cpa_destroy", "cpa_status_string", "cpa_last_error", "
            "cpa_mlp_train_step", "cpa_batch_features", "cpa_svt_batched_learned", "cpa_batch_read_choices",
            "cpa_admm_create", "cpa_admm_destroy", "cpa_admm_rpca", "cpa_set_option",
            "cpa_completion_create", "cpa_completion_destroy", "cpa_completion_run", "cpa_sync_status",
-           "cpa_svt_learned", "cpa_get_order", "cpa_learn_features", "cpa_serve_learned", "cpa_serve_read"]
+           "cpa_svt_learned", "cpa_get_order", "cpa_learn_features", "cpa_serve_learned", "cpa_serve_read",
+           "cpa_batch_set_config", "cpa_batch_get_config", "cpa_batch_tune"]
+BATCH_MMA_SYNC, BATCH_TCGEN05 = 0, 1
+ORDER_SIZE, ORDER_GIVEN = 0, 1
 OPT_SERIES, SERIES_FORWARD, SERIES_CLENSHAW = 1, 0, 1
 OPT_WAIT_KCYCLES, OPT_STALL_TEST, OPT_SPARSE_SKIP, OPT_STREAMS = 2, 3, 4, 5
 STAGES = ["prep", "gram", "bound", "coeff", "shift", "recur", "apply", "sparse"]
@@ -85,6 +88,10 @@ def load(path: str = LIB_PATH):
                                             ctypes.c_int, _d, ctypes.c_int, _P(CpaSparsify), _P(_vp), _i64, _vp]),
             "cpa_get_lambda": (ctypes.c_int, [_vp, _P(_d), _vp]),
             "cpa_sync_status": (ctypes.c_int, [_vp, _vp]),
+            "cpa_batch_set_config": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+            "cpa_batch_get_config": (ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_int), _P(ctypes.c_int)]),
+            "cpa_batch_tune": (ctypes.c_int, [_vp, _vp, _vp, _P(CpaShrink), ctypes.c_int, ctypes.c_int, _vp,
+                                              ctypes.c_int, _P(ctypes.c_int), _P(_d), _vp]),
             "cpa_svt_learned": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _P(CpaShrink), _P(CpaLearnRule),
                                                ctypes.c_int, _vp, _i64, _vp]),
             "cpa_get_order": (ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_int), _vp]),
@@ -373,6 +380,7 @@ class BatchPlan:
                 offsets.append(o)
                 o += a * b
         self.shapes, self.offsets = shapes, list(offsets)
+        self.L, self.L0 = (list(L) if L is not None else None), int(L0)
         self.total = max(o + a * b for (a, b), o in zip(shapes, self.offsets))
         off = (ctypes.c_int64 * self.count)(*self.offsets)
         ms = (ctypes.c_int32 * self.count)(*[a for a, _ in shapes])
@@ -393,6 +401,58 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+    def set_config(self, variant=BATCH_MMA_SYNC, ctas_per_sm=0, order=ORDER_SIZE):
+        _check(self._lib.cpa_batch_set_config(self.ptr, int(variant), int(ctas_per_sm), int(order)),
+               "cpa_batch_set_config")
+
+    def config(self):
+        v, c, o = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.cpa_batch_get_config(self.ptr, ctypes.byref(v), ctypes.byref(c), ctypes.byref(o)),
+               "cpa_batch_get_config")
+        return v.value, c.value, o.value
+
+    def tune_key(self, prec) -> str:
+        """Key of the tuning cache: precision and the histogram of (p, q, L)."""
+        import hashlib
+        hist = {}
+        for (m, n), L in zip(self.shapes, self.L if self.L is not None else [self.L0] * self.count):
+            k = (min(m, n), max(m, n), int(L))
+            hist[k] = hist.get(k, 0) + 1
+        txt = "%s|%s" % (prec, sorted(hist.items()))
+        return hashlib.sha1(txt.encode()).hexdigest()[:16]
+
+    def tune(self, h, X, shrink, prec="bf16x3", reps=3, Y=None, cache=None, stream=None):
+        """Picks the launch configuration of this plan: from the JSON file
+        `cache` when it holds this plan's key, else by timing every
+        candidate (cpa_batch_tune) and recording the choice there.  Returns
+        (config, candidate times in ms or None)."""
+        import json
+        import torch
+        key = self.tune_key(prec)
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+        if key in table:
+            self.set_config(*table[key]["config"])
+            return tuple(table[key]["config"]), None
+        if Y is None:
+            Y = torch.empty_like(X)
+        arr, k = _shrink_array(shrink)
+        chosen = (ctypes.c_int * 3)()
+        ms = (ctypes.c_double * 8)()
+        p = PREC[prec] if isinstance(prec, str) else int(prec)
+        _check(self._lib.cpa_batch_tune(h.ptr, self.ptr, ctypes.c_void_p(X.data_ptr()), arr, k, p,
+                                        ctypes.c_void_p(Y.data_ptr()), int(reps), chosen, ms, _stream_ptr(stream)),
+               "cpa_batch_tune")
+        cfg = (chosen[0], chosen[1], chosen[2])
+        times = [ms[i] for i in range(8)]
+        if cache:
+            table[key] = {"config": list(cfg), "ms": times}
+            with open(cache, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+        return cfg, times
 
     def lambdas(self, stream=None) -> np.ndarray:
         out = np.zeros(self.count, dtype=np.float64)

@@ -788,6 +788,11 @@ struct cpa_batch_ctx {
     std::vector<ShrinkParams> uploaded;   // shrink parameters currently on the device
     // learned serving (allocated on first use): L chosen per matrix, fallbacks
     int *d_L = nullptr, *d_nfb = nullptr;
+    // launch configuration (cpa_batch_set_config / cpa_batch_tune): kernel
+    // variant (CPA_BATCH_MMA_SYNC or CPA_BATCH_TCGEN05), CTAs per SM (0: the
+    // occupancy limit), work order (CPA_ORDER_SIZE or CPA_ORDER_GIVEN)
+    int variant = CPA_BATCH_MMA_SYNC, per_sm = 0, order_kind = CPA_ORDER_SIZE;
+    int *d_order_given = nullptr;
 };
 
 namespace {
@@ -844,6 +849,12 @@ cpa_status cpa_batch_create(cpa_handle h, int count, const int64_t *off, const i
     if (e == cudaSuccess) e = cudaMalloc(&b->d_status, 2 * sizeof(int));   // status, work counter
     if (e == cudaSuccess) e = cudaMemcpy(b->d_desc, desc.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_order_given, sizeof(int) * count);
+    if (e == cudaSuccess) {
+        std::vector<int> ident(count);
+        std::iota(ident.begin(), ident.end(), 0);
+        e = cudaMemcpy(b->d_order_given, ident.data(), sizeof(int) * count, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         cpa_batch_destroy(b);
         return bfail(e, "cpa_batch_create");
@@ -861,6 +872,7 @@ cpa_status cpa_batch_destroy(cpa_batch b) {
     cudaFree(b->d_status);
     cudaFree(b->d_L);
     cudaFree(b->d_nfb);
+    cudaFree(b->d_order_given);
     delete b;
     return CPA_OK;
 }
@@ -925,12 +937,14 @@ struct BatchRun {
     double *lambda_out;
     int *status;
     int num_sms;
+    int variant;    // CPA_BATCH_MMA_SYNC or CPA_BATCH_TCGEN05 (tensor-core precisions)
+    int per_sm;     // CTAs per SM of the mma.sync kernel, 0: its occupancy limit
 };
 
 template <bool TC, bool FEAT, bool LEARN>
 cpa_status launch_run(const BatchRun &b, const float *dX, float *dY, int s_count, const double *lambda, int iters,
                       const int *L_override, float *feat, double *theta, const LearnArgs &la, cudaStream_t st) {
-    if (TC && !FEAT) {
+    if (TC && !FEAT && b.variant == CPA_BATCH_TCGEN05) {
         // tensor-core products (tcgen05, state in tensor memory)
         BCK(launch_batched_tc(b.desc, b.order, b.count, dX, dY, b.shrink, s_count > 1 ? 1 : 0, lambda, b.lambda_out,
                               iters, b.status, L_override, la, LEARN, b.num_sms, st));
@@ -942,6 +956,7 @@ cpa_status launch_run(const BatchRun &b, const float *dX, float *dY, int s_count
     int per_sm = 0;
     BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
     if (per_sm < 1) per_sm = 1;
+    if (b.per_sm > 0 && b.per_sm < per_sm) per_sm = b.per_sm;
     const int grid = std::min(b.count, b.num_sms * per_sm);
     kern<<<grid, kThreads, smem, st>>>(b.desc, b.order, b.count, dX, dY, b.shrink, s_count > 1 ? 1 : 0, lambda,
                                        b.lambda_out, iters, b.status, L_override, feat, theta, la);
@@ -952,7 +967,8 @@ cpa_status launch_run(const BatchRun &b, const float *dX, float *dY, int s_count
 template <bool TC, bool FEAT, bool LEARN>
 cpa_status launch_batched(cpa_batch b, const float *dX, float *dY, int s_count, const double *lambda, int iters,
                           const int *L_override, float *feat, double *theta, const LearnArgs &la, cudaStream_t st) {
-    const BatchRun r{b->d_desc, b->d_order, b->count, b->d_shrink, b->d_lambda, b->d_status, b->num_sms};
+    const BatchRun r{b->d_desc, b->order_kind == CPA_ORDER_GIVEN ? b->d_order_given : b->d_order, b->count,
+                     b->d_shrink, b->d_lambda, b->d_status, b->num_sms, b->variant, b->per_sm};
     return launch_run<TC, FEAT, LEARN>(r, dX, dY, s_count, lambda, iters, L_override, feat, theta, la, st);
 }
 
@@ -1037,6 +1053,78 @@ cpa_status cpa_svt_batched_learned(cpa_handle h, cpa_batch b, cpa_mlp net, const
                                                  nullptr, la, st);
     return launch_batched<false, false, true>(b, dX, dY, s_count, nullptr, kDefaultPowerIters, nullptr, nullptr,
                                               nullptr, la, st);
+}
+
+cpa_status cpa_batch_set_config(cpa_batch b, int variant, int ctas_per_sm, int order) {
+    if (!b || (variant != CPA_BATCH_MMA_SYNC && variant != CPA_BATCH_TCGEN05) || ctas_per_sm < 0 ||
+        ctas_per_sm > 2 || (order != CPA_ORDER_SIZE && order != CPA_ORDER_GIVEN))
+        return CPA_ERR_INVALID_ARG;
+    b->variant = variant;
+    b->per_sm = ctas_per_sm;
+    b->order_kind = order;
+    return CPA_OK;
+}
+
+cpa_status cpa_batch_get_config(cpa_batch b, int *variant, int *ctas_per_sm, int *order) {
+    if (!b) return CPA_ERR_INVALID_ARG;
+    if (variant) *variant = b->variant;
+    if (ctas_per_sm) *ctas_per_sm = b->per_sm;
+    if (order) *order = b->order_kind;
+    return CPA_OK;
+}
+
+cpa_status cpa_batch_tune(cpa_handle h, cpa_batch b, const float *dX, const cpa_shrink *s, int s_count, int prec,
+                          float *dY, int reps, int *chosen, double *ms, void *stream) {
+    if (!h || !b || !chosen || reps < 1 || reps > 1000) return CPA_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    BCK(cudaSetDevice(b->device));
+    const int saved[3] = {b->variant, b->per_sm, b->order_kind};
+    double best = -1.0;
+    int bc[3] = {saved[0], saved[1], saved[2]};
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    cpa_status r = CPA_OK;
+    int slot = 0;
+    for (int variant = 0; variant < 2 && r == CPA_OK; ++variant)
+        for (int per_sm = 1; per_sm <= 2 && r == CPA_OK; ++per_sm)
+            for (int order = 0; order < 2 && r == CPA_OK; ++order, ++slot) {
+                const bool run = !(variant == CPA_BATCH_TCGEN05 && (prec == CPA_FP32 || per_sm != 1));
+                if (ms) ms[slot] = -1.0;
+                if (!run) continue;
+                b->variant = variant;
+                b->per_sm = per_sm;
+                b->order_kind = order;
+                if ((r = cpa_svt_batched_plan(h, b, dX, s, s_count, nullptr, kDefaultPowerIters, prec, dY, stream)) !=
+                    CPA_OK)
+                    break;
+                if (cudaEventRecord(e0, st) != cudaSuccess) { r = CPA_ERR_CUDA; break; }
+                for (int k = 0; k < reps && r == CPA_OK; ++k)
+                    r = cpa_svt_batched_plan(h, b, dX, s, s_count, nullptr, kDefaultPowerIters, prec, dY, stream);
+                float t = 0.f;
+                if (r != CPA_OK || cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+                    if (r == CPA_OK) r = CPA_ERR_CUDA;
+                    break;
+                }
+                const double mean = (double)t / reps;
+                if (ms) ms[slot] = mean;
+                if (best < 0.0 || mean < best) {
+                    best = mean;
+                    bc[0] = variant;
+                    bc[1] = per_sm;
+                    bc[2] = order;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->variant = r == CPA_OK ? bc[0] : saved[0];
+    b->per_sm = r == CPA_OK ? bc[1] : saved[1];
+    b->order_kind = r == CPA_OK ? bc[2] : saved[2];
+    chosen[0] = b->variant;
+    chosen[1] = b->per_sm;
+    chosen[2] = b->order_kind;
+    return r;
 }
 
 cpa_status cpa_batch_read_choices(cpa_batch b, int *host_L, int *host_fallbacks, void *stream) {
@@ -1138,7 +1226,7 @@ void ptr_plan_destroy(PtrPlan *pp) {
 }
 
 cpa_status ptr_plan_run(PtrPlan *pp, int count, const PtrItem *items, const double *lambda_host, int prec,
-                        const float *net, const cpa_learn_rule *rule, cudaStream_t st) {
+                        const float *net, const cpa_learn_rule *rule, cudaStream_t st, int variant) {
     if (count <= 0) return CPA_OK;
     cpa_status r = ptr_plan_reserve(pp, count, st);
     if (r != CPA_OK) return r;
@@ -1162,7 +1250,8 @@ cpa_status ptr_plan_run(PtrPlan *pp, int count, const PtrItem *items, const doub
         BCK(cudaMemcpyAsync(pp->d_lam_in, pp->h_lam, sizeof(double) * count, cudaMemcpyHostToDevice, st));
     BCK(cudaEventRecord(pp->staged, st));
     BCK(cudaMemsetAsync(pp->d_status, 0, 2 * sizeof(int), st));
-    const BatchRun run{pp->d_desc, pp->d_order, count, pp->d_shrink, pp->d_lam_out, pp->d_status, pp->num_sms};
+    const BatchRun run{pp->d_desc, pp->d_order, count, pp->d_shrink, pp->d_lam_out, pp->d_status, pp->num_sms,
+                       variant, 0};
     const bool tc = prec != CPA_FP32;
     if (net) {
         BCK(cudaMemsetAsync(pp->d_nfb, 0, sizeof(int), st));

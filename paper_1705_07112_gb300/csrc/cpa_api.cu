@@ -38,7 +38,9 @@ struct cpa_ctx {
     // pointer-form batches (cpa_svt_batched, cpa_serve_learned): the
     // patch-sized members' launch, and per-member choices of the larger
     // members of the last learned call ({L, fallback} pairs, bounds)
-    PtrPlan *pplan = nullptr;
+    PtrPlan *pplan = nullptr;          // members up to 64 x 128 (mma.sync kernel)
+    PtrPlan *pplan_tc = nullptr;       // members up to 128 x 256 beyond those (tcgen05 kernel)
+    std::vector<int> serve_mid;        // member indices of the last learned call in the second group
     int *d_big_L = nullptr;
     double *d_big_lam = nullptr;
     int big_cap = 0;
@@ -361,6 +363,7 @@ cpa_status cpa_destroy(cpa_handle h) {
     }
     if (h->start) cudaEventDestroy(h->start);
     ptr_plan_destroy(h->pplan);
+    ptr_plan_destroy(h->pplan_tc);
     for (int k = 0; k < 16; ++k) {
         if (h->sub[k]) cpa_destroy(h->sub[k]);
         if (h->sub_st[k]) cudaStreamDestroy(h->sub_st[k]);
@@ -1073,12 +1076,6 @@ cpa_status cpa_svt_host(cpa_handle h, int count, const float *const *hX, int64_t
 
 namespace {
 
-// Members the batched launch takes: the tensor-core kernel holds p <= 128,
-// q <= 256, the CUDA-core (FP32) kernel p <= 64, q <= 128.
-bool patch_sized(int64_t m, int64_t n, int L, int prec) {
-    const int64_t P = prec == CPA_FP32 ? 64 : kTcBatchP, Q = prec == CPA_FP32 ? 128 : kTcBatchQ;
-    return std::min(m, n) <= P && std::max(m, n) <= Q && L <= batched_max_terms();
-}
 
 cpa_status check_members(int count, const float *const *dX, const int64_t *m, const int64_t *n, const int64_t *ldx,
                          const cpa_shrink *s, int s_count, float *const *dY, const int64_t *ldy) {
@@ -1095,7 +1092,20 @@ cpa_status check_members(int count, const float *const *dX, const int64_t *m, co
 
 cpa_status ensure_pplan(cpa_ctx *h) {
     if (!h->pplan) h->pplan = ptr_plan_create(h->device, h->num_sms);
-    return h->pplan ? CPA_OK : CPA_ERR_NO_MEMORY;
+    if (!h->pplan_tc) h->pplan_tc = ptr_plan_create(h->device, h->num_sms);
+    return h->pplan && h->pplan_tc ? CPA_OK : CPA_ERR_NO_MEMORY;
+}
+
+// The member class of the batched launch: 1 for the mma.sync kernel (p <=
+// 64, q <= 128; measured faster there, two CTAs per SM), 2 for the tcgen05
+// kernel (p <= 128, q <= 256, tensor-core precisions), 0 for the
+// single-matrix path.
+int member_class(int64_t m, int64_t n, int L, int prec) {
+    const int64_t p = std::min(m, n), q = std::max(m, n);
+    if (L > batched_max_terms()) return 0;
+    if (p <= 64 && q <= 128) return 1;
+    if (prec != CPA_FP32 && p <= kTcBatchP && q <= kTcBatchQ) return 2;
+    return 0;
 }
 
 // The members `order` (largest first) through fn(handle, k, stream): on the
@@ -1164,9 +1174,11 @@ cpa_status cpa_svt_batched(cpa_handle h, int count, const float *const *dX, cons
     if (count == 0) return CPA_OK;
     if ((r = set_device(h)) != CPA_OK) return r;
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<int> small, big;
-    for (int i = 0; i < count; ++i) (patch_sized(m[i], n[i], L ? L[i] : L0, prec) ? small : big).push_back(i);
-    if (!small.empty()) {
+    std::vector<int> cls[3];
+    for (int i = 0; i < count; ++i) cls[member_class(m[i], n[i], L ? L[i] : L0, prec)].push_back(i);
+    for (int c = 1; c <= 2; ++c) {
+        const std::vector<int> &small = cls[c];
+        if (small.empty()) continue;
         if ((r = ensure_pplan(h)) != CPA_OK) return r;
         std::vector<PtrItem> items(small.size());
         std::vector<double> lam(small.size());
@@ -1181,10 +1193,12 @@ cpa_status cpa_svt_batched(cpa_handle h, int count, const float *const *dX, cons
             }
         }
         // the batched kernel takes bounds for all members or none
-        if ((r = ptr_plan_run(h->pplan, (int)small.size(), items.data(), all_given ? lam.data() : nullptr, prec,
-                              nullptr, nullptr, st)) != CPA_OK)
+        if ((r = ptr_plan_run(c == 1 ? h->pplan : h->pplan_tc, (int)small.size(), items.data(),
+                              all_given ? lam.data() : nullptr, prec, nullptr, nullptr, st,
+                              c == 1 ? CPA_BATCH_MMA_SYNC : CPA_BATCH_TCGEN05)) != CPA_OK)
             return r;
     }
+    const std::vector<int> &big = cls[0];
     const std::vector<int> order = by_size_desc(big, m, n);
     return run_members(h, order, st, [&](cpa_ctx *hh, int k, cudaStream_t sk) {
         const int i = order[k];
@@ -1213,17 +1227,24 @@ cpa_status cpa_serve_learned(cpa_handle h, cpa_mlp net, int count, const float *
     if ((r = set_device(h)) != CPA_OK) return r;
     cudaStream_t st = (cudaStream_t)stream;
     h->serve_small.clear();
+    h->serve_mid.clear();
     h->serve_big.clear();
-    for (int i = 0; i < count; ++i) (patch_sized(m[i], n[i], 1, prec) ? h->serve_small : h->serve_big).push_back(i);
-    if (!h->serve_small.empty()) {
+    for (int i = 0; i < count; ++i) {
+        const int c = member_class(m[i], n[i], 1, prec);
+        (c == 1 ? h->serve_small : c == 2 ? h->serve_mid : h->serve_big).push_back(i);
+    }
+    for (int c = 1; c <= 2; ++c) {
+        const std::vector<int> &grp = c == 1 ? h->serve_small : h->serve_mid;
+        if (grp.empty()) continue;
         if ((r = ensure_pplan(h)) != CPA_OK) return r;
-        std::vector<PtrItem> items(h->serve_small.size());
+        std::vector<PtrItem> items(grp.size());
         for (size_t k = 0; k < items.size(); ++k) {
-            const int i = h->serve_small[k];
+            const int i = grp[k];
             items[k] = PtrItem{dX[i], dY[i], ldx[i], ldy[i], (int)m[i], (int)n[i], 1,
                                to_params(&s[s_count > 1 ? i : 0])};
         }
-        if ((r = ptr_plan_run(h->pplan, (int)items.size(), items.data(), nullptr, prec, P, rule, st)) != CPA_OK)
+        if ((r = ptr_plan_run(c == 1 ? h->pplan : h->pplan_tc, (int)items.size(), items.data(), nullptr, prec, P,
+                              rule, st, c == 1 ? CPA_BATCH_MMA_SYNC : CPA_BATCH_TCGEN05)) != CPA_OK)
             return r;
     }
     const int nb = (int)h->serve_big.size();
@@ -1259,28 +1280,39 @@ cpa_status cpa_serve_learned(cpa_handle h, cpa_mlp net, int count, const float *
 
 cpa_status cpa_serve_read(cpa_handle h, int count, int *host_L, double *host_lambda, int *host_fallbacks,
                           void *stream) {
-    if (!h || count != (int)(h->serve_small.size() + h->serve_big.size())) return CPA_ERR_INVALID_ARG;
+    if (!h || count != (int)(h->serve_small.size() + h->serve_mid.size() + h->serve_big.size()))
+        return CPA_ERR_INVALID_ARG;
     cpa_status r = set_device(h);
     if (r != CPA_OK) return r;
     cudaStream_t st = (cudaStream_t)stream;
-    const int ns = (int)h->serve_small.size(), nb = (int)h->serve_big.size();
-    std::vector<int> sL(ns), bL(2 * nb);
-    std::vector<double> sl(ns), bl(nb);
-    int nfb_small = 0;
+    const int ns = (int)h->serve_small.size(), nm = (int)h->serve_mid.size(), nb = (int)h->serve_big.size();
+    std::vector<int> sL(ns), mL(nm), bL(2 * nb);
+    std::vector<double> sl(ns), ml(nm), bl(nb);
+    int nfb_small = 0, nfb_mid = 0;
     if (ns) {
         CK(cudaMemcpyAsync(sL.data(), ptr_plan_orders(h->pplan), sizeof(int) * ns, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(sl.data(), ptr_plan_lambdas(h->pplan), sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(&nfb_small, ptr_plan_fallbacks(h->pplan), sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
+    if (nm) {
+        CK(cudaMemcpyAsync(mL.data(), ptr_plan_orders(h->pplan_tc), sizeof(int) * nm, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ml.data(), ptr_plan_lambdas(h->pplan_tc), sizeof(double) * nm, cudaMemcpyDeviceToHost,
+                           st));
+        CK(cudaMemcpyAsync(&nfb_mid, ptr_plan_fallbacks(h->pplan_tc), sizeof(int), cudaMemcpyDeviceToHost, st));
     }
     if (nb) {
         CK(cudaMemcpyAsync(bL.data(), h->d_big_L, sizeof(int) * 2 * nb, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(bl.data(), h->d_big_lam, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
     }
     CK(cudaStreamSynchronize(st));
-    int nfb = nfb_small;
+    int nfb = nfb_small + nfb_mid;
     for (int k = 0; k < ns; ++k) {
         if (host_L) host_L[h->serve_small[k]] = sL[k];
         if (host_lambda) host_lambda[h->serve_small[k]] = sl[k];
+    }
+    for (int k = 0; k < nm; ++k) {
+        if (host_L) host_L[h->serve_mid[k]] = mL[k];
+        if (host_lambda) host_lambda[h->serve_mid[k]] = ml[k];
     }
     for (int k = 0; k < nb; ++k) {
         if (host_L) host_L[h->serve_big[k]] = bL[2 * k];

@@ -274,7 +274,8 @@ struct PtrPlan;
 PtrPlan *ptr_plan_create(int device, int num_sms);
 void ptr_plan_destroy(PtrPlan *pp);
 cpa_status ptr_plan_run(PtrPlan *pp, int count, const PtrItem *items, const double *lambda_host, int prec,
-                        const float *net, const cpa_learn_rule *rule, cudaStream_t st);
+                        const float *net, const cpa_learn_rule *rule, cudaStream_t st,
+                        int variant = CPA_BATCH_MMA_SYNC);
 const double *ptr_plan_lambdas(const PtrPlan *pp);
 const int *ptr_plan_orders(const PtrPlan *pp);
 const int *ptr_plan_fallbacks(const PtrPlan *pp);

@@ -70,3 +70,20 @@ def test_null_handle_is_rejected(lib):
     assert lib.cpa_svt(None, None, 4, 4, 4, ctypes.byref(s), 5, 0.0, 0, None, None, 4, None) == L.CPA_ERR_INVALID_ARG
     assert lib.cpa_lambda_bound(None, None, 4, 4, 4, 5, ctypes.byref(out), None) == L.CPA_ERR_INVALID_ARG
     assert lib.cpa_get_lambda(None, ctypes.byref(out), None) == L.CPA_ERR_INVALID_ARG
+
+
+def test_tuning_cache_key_is_a_histogram():
+    """The tuning cache key depends on the multiset of (p, q, L) and the
+    precision only (not on the members' order or orientation)."""
+    from paper_1705_07112_gb300 import _lib
+
+    class P:   # the key's inputs without a device plan
+        tune_key = _lib.BatchPlan.tune_key
+
+    a, b, c = P(), P(), P()
+    a.shapes, a.L, a.L0, a.count = [(64, 40), (40, 64), (64, 80)], None, 24, 3
+    b.shapes, b.L, b.L0, b.count = [(64, 80), (64, 40), (64, 40)], None, 24, 3
+    c.shapes, c.L, c.L0, c.count = [(64, 80), (64, 40), (64, 40)], [24, 24, 25], 24, 3
+    assert a.tune_key("bf16x3") == b.tune_key("bf16x3")
+    assert a.tune_key("bf16x3") != a.tune_key("fp32")
+    assert c.tune_key("bf16x3") != b.tune_key("bf16x3")

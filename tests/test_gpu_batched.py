@@ -209,3 +209,42 @@ def test_pointer_form_matches_plan_and_oracle(cpa, handle):
             ref = O.cpa(A, O.Shrink(O.SOFT, specs[i]["tau"]), Ls[i], lams[i])
             assert rel(Ys[i].cpu().numpy().astype(np.float64), ref) <= tol, (prec, shapes[i], rel(Ys[i].cpu().numpy(), ref))
         plan.close()
+
+
+def test_launch_configurations_and_tuner(cpa, handle, tmp_path):
+    """Every launch configuration of a plan (mma.sync kernel at 1 or 2 CTAs
+    per SM, tcgen05 kernel; size-sorted or given work order) gives an
+    oracle-accurate result; the tuner times them, keeps the fastest and
+    records it in its JSON cache, which a second plan of the same shapes
+    takes without timing."""
+    import torch
+    from paper_1705_07112_gb300 import _lib
+    mats = [m.astype(np.float32).astype(np.float64) for m in edge_batch(seed=17)]
+    shapes = [m.shape for m in mats]
+    lams = np.array([oracle_lambda(m) for m in mats])
+    specs = [dict(kind=O.SOFT, tau=0.2 * np.sqrt(l / 1.01)) for l in lams]
+    X = pack(mats)
+    plan = cpa.BatchPlan(handle, shapes, L0=30)
+    refs = [O.cpa(m, O.Shrink(O.SOFT, s["tau"]), 30, l) for m, s, l in zip(mats, specs, lams)]
+    lam_t = torch.from_numpy(lams).cuda()
+    for cfg in [(0, 1, 0), (0, 2, 1), (1, 0, 0), (1, 0, 1)]:
+        plan.set_config(*cfg)
+        assert plan.config() == cfg
+        Y = cpa.cpa_svt_batched_plan(handle, plan, X, specs, lambdas=lam_t, prec="bf16x3")
+        torch.cuda.synchronize()
+        for y, ref, sh in zip(unpack(Y, shapes), refs, shapes):
+            assert rel(y, ref) <= TOL["bf16x3"], (cfg, sh)
+    with pytest.raises(cpa.CpaError):
+        plan.set_config(2, 0, 0)
+    cache = str(tmp_path / "tune.json")
+    cfg, ms = plan.tune(handle, X, specs, prec="bf16x3", reps=2, cache=cache)
+    ran = [t for t in ms if t >= 0]
+    assert len(ran) == 6 and plan.config() == cfg
+    best = int(np.argmin([t if t >= 0 else np.inf for t in ms]))
+    # candidate slots: variant x ctas_per_sm (1, 2) x order; the chosen one is the fastest
+    assert cfg == (best // 4, 1 + (best // 2) % 2, best % 2)
+    plan2 = cpa.BatchPlan(handle, shapes, L0=30)
+    cfg2, ms2 = plan2.tune(handle, X, specs, prec="bf16x3", cache=cache)
+    assert cfg2 == cfg and ms2 is None and plan2.config() == cfg
+    plan.close()
+    plan2.close()
