@@ -239,14 +239,19 @@ CPA_API cpa_status cpa_get_coeffs(cpa_handle h, double *c_out, int L, void *stre
  *   entry threshold): their loads and products are not issued.  The skipped
  *   products are exact zeros, so the result is the same bit for bit; 0
  *   runs every tile (for comparisons). */
-/* CPA_OPT_STREAMS: 1..16 (default 1): the pointer-form batches
+/* CPA_OPT_STREAMS: 1..64 (default 1): the pointer-form batches
  *   (cpa_svt_batched, cpa_serve_learned) run their larger members (those
  *   not taken by the batched kernel) round-robin on this many streams, each
  *   with a workspace of its own, forked from and joined back into the
  *   call's stream; matrices too small to fill the GPU then run side by
  *   side.  The results are those of one stream. */
+/* CPA_OPT_MEMBER_SMS: >= 0 (default 0, all): the SMs each of those members'
+ *   launches is sized for (tile widths and grids of its products, bound and
+ *   recurrence), so that several large members run side by side instead of
+ *   one after another; values above the device's SM count mean all.  The
+ *   results do not depend on it beyond FP32 summation order. */
 enum { CPA_OPT_SERIES = 1, CPA_OPT_WAIT_KCYCLES = 2, CPA_OPT_STALL_TEST = 3, CPA_OPT_SPARSE_SKIP = 4,
-       CPA_OPT_STREAMS = 5 };
+       CPA_OPT_STREAMS = 5, CPA_OPT_MEMBER_SMS = 6 };
 enum { CPA_SERIES_FORWARD = 0, CPA_SERIES_CLENSHAW = 1 };
 CPA_API cpa_status cpa_set_option(cpa_handle h, int option, int value);
 
@@ -497,10 +502,11 @@ CPA_API cpa_status cpa_get_order(cpa_handle h, int *L_out, int *fallback, void *
  * Batches given member by member: device pointers, shapes, leading
  * dimensions (elements, row-major) and orders per matrix, following the
  * problem statement of Algorithm 1 for each member.  Members with
- * min(m, n) <= 128, max(m, n) <= 256 (CPA_BF16 / CPA_BF16X3; min <= 64, max
- * <= 128 for CPA_FP32) and L <= 1024 run in one persistent launch of the
- * batched kernel; the others run through the single-matrix path (on
- * CPA_OPT_STREAMS streams).  Asynchronous; the
+ * min(m, n) <= 64, max(m, n) <= 128 and L <= 1024 run in one persistent
+ * launch of the CUDA-core batched kernel (warp-level MMA); with CPA_BF16 /
+ * CPA_BF16X3 the others with min(m, n) <= 128, max(m, n) <= 4096 and
+ * L <= 1024 run in one persistent launch of the tcgen05 batched kernel; the
+ * rest run through the single-matrix path (on CPA_OPT_STREAMS streams).  Asynchronous; the
  * descriptor table is uploaded on `stream` from pinned staging owned by the
  * handle (a later call waits until the previous upload has been read).
  * Members' X and Y must not overlap.  Errors: INVALID_ARG (any member),
@@ -535,7 +541,7 @@ CPA_API cpa_status cpa_learn_features(cpa_handle h, const float *dX, int64_t m, 
                                       const cpa_shrink *s, float *dF, double *dTheta, void *stream);
 
 /* ---------------------------------------------------------------------------
- * Background-modelling ADMM around the shrinkage (Appendix B, Eq.
+ * Background-modelling ADMM around the shrinkage (the appendix ADMM Applicable Forms, Background Modeling, Eq.
  * admm_algorithm_mod): min |l|_* + eta |s|_1 subject to l + s = d, with
  * rho the ADMM step.  Each iteration runs cpa_svt (soft threshold
  * tau_nuclear = 1/rho on the singular values, L terms, Lambda_max computed
@@ -543,13 +549,13 @@ CPA_API cpa_status cpa_learn_features(cpa_handle h, const float *dX, int64_t m, 
  * tau_l1 = eta/rho on s + u2, the projection z3 = d, the dual update, and
  * the least-squares step l = (2a1 - a2 + a3)/3, s = (-a1 + 2a2 + a3)/3 with
  * a = z - u, all but the shrinkage in one fused elementwise kernel.  Start:
- * l = s = u = 1 (Section V-C).
+ * l = s = u = 1 (Section V, Background Modeling of Video).
  *
  * cpa_admm_create: solver for m x n problems on the handle's device; owns
  *   6 m n floats of state (m n <= 2^31).
  * cpa_admm_rpca: sp (optional) applies the sparsity-based reduction in every
  *   shrinkage; with schedule != 0 (sp->mode must be CPA_SPARSE_TOPK) the
- *   kept fraction follows Section V-D's rule (Eq. recommendation_epsilon)
+ *   kept fraction follows the rule of Section V, Effects of Thresholding Value (Eq. recommendation_epsilon)
  *   on the current E_t: 0.5e-4 of p^2 while E_t > 0.03, 1.5e-4 while
  *   E_t > 6e-4, 0.5e-3 below (one host synchronisation per iteration).
  *   dD device m x n (row stride ldd >= n); dL, dS device m x n
@@ -570,10 +576,10 @@ CPA_API cpa_status cpa_admm_rpca(cpa_admm a, const float *dD, int64_t ldd, doubl
                                  float *dL, float *dS, int *iters_done, double *errors, void *stream);
 
 /* ---------------------------------------------------------------------------
- * Matrix completion ADMM of Section V-E: the inpainting problem of Section
- * V-B (Eq. texture_repaire4) without its average term, min |L|_* +
+ * Matrix completion ADMM of Section V, Comparison with Existing Methods: the inpainting problem of
+ * Section V, Texture Image Inpainting (Eq. texture_repaire4) without its average term, min |L|_* +
  * eta |Psi l|_1 subject to the observed entries and 0 <= L <= 1, in the
- * ADMM form of Appendix A (Eq. admm_algorithm_inp without the z^(5) block):
+ * ADMM form of the appendix ADMM Applicable Forms, Texture Image Inpainting (Eq. admm_algorithm_inp without the z^(5) block):
  * z = K l, K = [Id; Psi; Omega; Id], Psi the orthonormal 2-D DCT (Psi l =
  * C_m L C_n^T, C_p[k][j] = s_k cos(pi (2j+1) k / (2p)), s_0 = sqrt(1/p),
  * s_k = sqrt(2/p)), Omega the observation mask.  Each iteration: the
@@ -584,7 +590,7 @@ CPA_API cpa_status cpa_admm_rpca(cpa_admm a, const float *dD, int64_t ldd, doubl
  * values, z4 = l + u4 clipped to [0, 1], u += K l - z.  The four products
  * with C_m, C_n run in FP32 (prec = CPA_FP32) or on the tensor cores with
  * BF16 hi/lo operands, three products each (other precisions).  Start
- * (Section V-B): l = u = 1, z = K l.
+ * (Section V, Texture Image Inpainting): l = u = 1, z = K l.
  *
  * cpa_completion_create: solver for m x n problems (m, n <= 65536, m n <=
  *   2^31) on the handle's device; owns 10 m n + m^2 + n^2 floats and about
@@ -595,7 +601,7 @@ CPA_API cpa_status cpa_admm_rpca(cpa_admm a, const float *dD, int64_t ldd, doubl
  *   iterate l; dZ1 (optional, contiguous m x n) the last shrinkage output.
  *   Outputs must not overlap the inputs or each other.  Runs max_iters
  *   iterations, or stops after the iteration whose E = |l_new - l|_F /
- *   |l_new|_F (the stopping quantity of Section IV's footnote, computed
+ *   |l_new|_F (the stopping quantity of the stopping-criterion footnote of Section V, Optimization Tools, computed
  *   after each least-squares step) is below tol > 0 (one host
  *   synchronisation per iteration).  *iters_done and errors (host, max_iters
  *   doubles) as for cpa_admm_rpca.  Errors: CPA_ERR_INVALID_ARG on bad

@@ -1,6 +1,6 @@
 """FP64 reference of the background-modelling ADMM (test infrastructure only).
 
-Appendix B, Eq. admm_algorithm_mod: min |l|_* + eta |s|_1 subject to
+the appendix ADMM Applicable Forms, Background Modeling, Eq. admm_algorithm_mod: min |l|_* + eta |s|_1 subject to
 l + s = d, rewritten with z = K l', K = [[I, 0], [0, I], [I, I]] and solved
 by ADMM with step rho.  One iteration, from (z_t, u_t):
 
@@ -12,13 +12,13 @@ by ADMM with step rho.  One iteration, from (z_t, u_t):
 
 (K^T K)^{-1} = (1/3) [[2, -1], [-1, 2]] and K^T a = (a1 + a3, a2 + a3), so
 with a_i = z_i - u_i:  l = (2 a1 - a2 + a3) / 3,  s = (-a1 + 2 a2 + a3) / 3.
-Start (Section V-C, background modelling): l_0 = s_0 = u_0 = all ones and
+Start (Section V, Background Modeling of Video): l_0 = s_0 = u_0 = all ones and
 z_0 = K l'_0.  E_t = |l_t - l_{t-1}|_F / |l_t|_F (the stopping quantity of
-Section IV's footnote and Section V-D).
+the stopping-criterion footnote of Section V, Optimization Tools, and Section V, Effects of Thresholding Value).
 
 The shrinkage step is a callable: the exact shrinkage (Jacobi SVD) for the
 oracle-SVT run, or Algorithm 1 in FP64 for the method's own run, also with
-the sparsity-based reduction and its threshold schedule of Section V-D
+the sparsity-based reduction and its threshold schedule of Section V, Effects of Thresholding Value
 (Eq. recommendation_epsilon): eps = the k-th largest |Phi_ij| with k a
 fraction of p^2 chosen from the current E_t.
 """
@@ -56,7 +56,7 @@ def svt_cpa(tau, L, iters=20, margin=0.01, seed=0x1705071120000000):
     return f
 
 
-E_L, E_M = 0.3e-1, 6e-4   # the schedule's E_l and E_m (Section V-D)
+E_L, E_M = 0.3e-1, 6e-4   # the schedule's E_l and E_m (Section V, Effects of Thresholding Value)
 
 
 def eps_fraction(E):

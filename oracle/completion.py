@@ -1,8 +1,8 @@
 """FP64 reference of the synthetic completion test (test infrastructure only).
 
-Section V-E restores a corrupted matrix with the inpainting problem of
-Section V-B (Eq. texture_repaire4) without its average term.  Its ADMM form
-(Appendix A, Eq. admm_algorithm_inp, the z^(5) block dropped with the
+Section V, Comparison with Existing Methods restores a corrupted matrix with the inpainting problem of
+Section V, Texture Image Inpainting (Eq. texture_repaire4) without its average term.  Its ADMM form
+(the appendix ADMM Applicable Forms, Texture Image Inpainting, Eq. admm_algorithm_inp, the z^(5) block dropped with the
 average term) works on z = K l with
 
   K = [Id; Psi; Omega; Id],   Psi the orthonormal 2-D DCT, Omega the
@@ -19,7 +19,7 @@ and one iteration from (z_t, u_t) reads
 
 Psi^T Psi = Id and Omega^T Omega = Omega, so K^T K = 3 Id + Omega is
 diagonal and the least-squares step is l = (a1 + Psi^T a2 + Omega a3 + a4)
-/ (3 + omega) with a_i = z_i - u_i.  Start (Section V-B): l_0 = u_0 = all
+/ (3 + omega) with a_i = z_i - u_i.  Start (Section V, Texture Image Inpainting): l_0 = u_0 = all
 ones, z_0 = K l_0.  E_t = |l_t - l_{t-1}|_F / |l_t|_F, the quantity Section
 IV's footnote names for this very algorithm.
 

@@ -640,7 +640,7 @@ int orc_eig_jacobi(const double *S, int p, double *w, double *V, double tol, int
 /* ------------------------------------------------------------------------- */
 /* Exact singular value shrinkage, Eq. sing_shrink_exact:                    */
 /*   G(X) = U diag(g(sigma_i)) V^T = sum_i h(sigma_i^2) (X v_i) v_i^T,       */
-/* from the Jacobi SVD (the SVD-based method of Section V-A).                */
+/* from the Jacobi SVD (the SVD-based method of Section V, Experimental Conditions).                */
 /* sv (optional, p entries) receives the singular values.                    */
 /* ------------------------------------------------------------------------- */
 int orc_shrink_exact(const double *X, int m, int n, int kind, double tau, double c,

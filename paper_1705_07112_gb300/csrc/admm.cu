@@ -1,4 +1,4 @@
-// Background-modelling ADMM (Appendix B, Eq. admm_algorithm_mod) around the
+// Background-modelling ADMM (the appendix ADMM Applicable Forms, Background Modeling, Eq. admm_algorithm_mod) around the
 // CPA shrinkage: min |l|_* + eta |s|_1 subject to l + s = d, written with
 // z = K l', K = [[I, 0], [0, I], [I, I]] and solved by ADMM.  Iteration t:
 //   l', s' = (K^T K)^{-1} K^T (z - u)           (closed form below)
@@ -7,14 +7,14 @@
 //   z3 = d                                      projection onto {x = d}
 //   u += K l' - z
 // With a_i = z_i - u_i:  l = (2 a1 - a2 + a3) / 3,  s = (-a1 + 2 a2 + a3) / 3.
-// Start (Section V-C): l = s = u = 1, z = K l'.
+// Start (Section V, Background Modeling of Video): l = s = u = 1, z = K l'.
 //
 // Device state: l, s, u1, u2, u3 and the next shrinkage input w = l + u1
 // (FP32, m x n, owned by the solver object); z1 lives in the caller's L
 // output and z2 in its S output.  One fused kernel per iteration finishes
 // iteration t (z2, u) and starts t + 1 (l, s, w, and the sums of
 // E_{t+1} = |l_{t+1} - l_t|_F / |l_{t+1}|_F, the stopping quantity of
-// Section IV's footnote).
+// the stopping-criterion footnote of Section V, Optimization Tools).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>

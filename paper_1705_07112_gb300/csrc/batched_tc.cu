@@ -1,9 +1,15 @@
-// Batched CPA shrinkage on the tensor cores: one CTA of 128 threads per
+// Batched CPA shrinkage on the tensor cores: one CTA of 512 threads per
 // member matrix at a time (persistent over a size-sorted work list), for
-// members with p = min(m, n) <= 128 and q = max(m, n) <= 256.
+// members with p = min(m, n) <= 128 and q = max(m, n) <= 4096 (X staged
+// through shared memory in chunks of 256 columns for the Gram matrix and
+// 256 output columns for the final product).
 //
-// Thread t owns row t of every p x p matrix of the member, and tensor-memory
-// lane t holds that row:
+// Tensor-memory lane r holds row r of every p x p matrix of the member.
+// Thread t = 128 cq + r (cq = 0..3) works on row r, columns [32 cq, 32 cq
+// + 32) of the element-wise passes (a warp may only touch its own quarter
+// of the lanes: warp w's lanes are 32 (w mod 4) .. + 31, which is row r's
+// quarter); the scalar phases (power iteration, features, network) run on
+// the threads of cq = 0, one per row.  Tensor-memory columns:
 //   TMEM columns [0, 128)    product accumulator (the Gram matrix, A Psi_{k-1};
 //                            the final product uses [0, 256))
 //   [128, 256), [256, 384)   the ring Psi_{k-1}, Psi_{k-2} (FP32)
@@ -17,7 +23,8 @@
 // reads the accumulator and the state from tensor memory, forms
 //   Psi_k = 2 At Psi_{k-1} - 2 Psi_{k-1} - Psi_{k-2},  H += c_k Psi_k
 // in FP32, writes Psi_k back in place of Psi_{k-2} and its BF16 parts into
-// the operand tile of the next product.  The products read the operand's
+// the operand tile of the next product (padding rows and columns beyond p
+// are zero in every operand and state, so they stay zero).  The products read the operand's
 // rows, A B^T, so G and every Psi_k are kept exactly symmetric (each takes
 // its upper triangle's values, exchanged through shared memory), as the
 // single-matrix tensor-core path does by mirroring upper tiles.  Lambda_max
@@ -34,10 +41,11 @@ namespace {
 
 using namespace tc;
 
-constexpr int kT = 128;                 // threads (4 warps), one per row
+constexpr int kT = 512;                 // threads (16 warps): 4 column quarters x 128 rows
+constexpr int kRows = 128;              // rows of a tile = tensor-memory lanes
 constexpr int kP = kTcBatchP;           // rows of a member's p x p matrices
-constexpr int kQ = kTcBatchQ;
 constexpr int kLdG = kP + 1;            // FP32 Gram matrix row stride (conflict-free rows)
+constexpr int kChunkQ = 256;            // columns of X_p staged per Gram chunk / rows of X_p^T per output chunk
 constexpr int kTcMaxTerms = 1024;
 constexpr int kFeat = 12, kHid = 64;
 constexpr uint64_t kEdgeXor = 0x5EEDULL;
@@ -62,7 +70,7 @@ constexpr int kXLo = 4 * kSlice128;
 struct Small {
     float coef[kTcMaxTerms];      // c_k in FP32 (before: the predictor's scratch)
     float v[2][kP];             // power-iteration vectors
-    float red[8];               // block-sum partials, two sets of four
+    float red[8];               // block-sum partials (warps 0-3), two sets of four
     double scal[4];             // lambda, chosen L (as double), spare
     double lam;
     float s2;
@@ -110,12 +118,13 @@ __device__ __forceinline__ void zero_smem(uint8_t *p, int bytes) {
     for (int i = threadIdx.x; i < bytes / 16; i += kT) q[i] = make_uint4(0, 0, 0, 0);
 }
 
-// D[tmem d] = sum over kslices K slices of A B^T with the BF16 split
-// (hi*hi + hi*lo + lo*hi), then a commit to `bar`.  Issued by one thread.
+// D[tmem d] (+)= sum over kslices K slices of A B^T with the BF16 split
+// (hi*hi + hi*lo + lo*hi; accumulating onto D when acc0 = 1), then a commit
+// to `bar`.  Issued by one thread.
 __device__ __forceinline__ void issue_split_product(uint32_t d, const uint8_t *a_hi, const uint8_t *a_lo,
                                                     int a_slice, const uint8_t *b_hi, const uint8_t *b_lo, int b_slice,
-                                                    int kslices, uint32_t idesc, uint64_t *bar) {
-    uint32_t acc = 0;
+                                                    int kslices, uint32_t idesc, uint64_t *bar, uint32_t acc0) {
+    uint32_t acc = acc0;
 #pragma unroll 1
     for (int seg = 0; seg < 3; ++seg) {
         const uint8_t *a = seg == 2 ? a_lo : a_hi;
@@ -133,19 +142,52 @@ __device__ __forceinline__ void issue_split_product(uint32_t d, const uint8_t *a
     mma_commit(bar);
 }
 
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float *v) {
+// Sixteen columns of this thread's lane at each of three addresses, one wait.
+__device__ __forceinline__ void tmem_ld16x3(uint32_t ta, uint32_t tb, uint32_t tc, float *a, float *b, float *c) {
+    uint32_t r[48];
+#define CPA_LD16(base, addr)                                                                                         \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "                                                           \
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"                                  \
+                 : "=r"(r[base + 0]), "=r"(r[base + 1]), "=r"(r[base + 2]), "=r"(r[base + 3]), "=r"(r[base + 4]),   \
+                   "=r"(r[base + 5]), "=r"(r[base + 6]), "=r"(r[base + 7]), "=r"(r[base + 8]), "=r"(r[base + 9]),   \
+                   "=r"(r[base + 10]), "=r"(r[base + 11]), "=r"(r[base + 12]), "=r"(r[base + 13]),                 \
+                   "=r"(r[base + 14]), "=r"(r[base + 15])                                                            \
+                 : "r"(addr))
+    CPA_LD16(0, ta);
+    CPA_LD16(16, tb);
+    CPA_LD16(32, tc);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int g = 0; g < 32; g += 8) tmem_st8(taddr + g, v + g);
+    for (int j = 0; j < 16; ++j) {
+        a[j] = __uint_as_float(r[j]);
+        b[j] = __uint_as_float(r[16 + j]);
+        c[j] = __uint_as_float(r[32 + j]);
+    }
 }
 
-// Block sum (4 warps) of one float per thread; the partials alternate
-// between two slot sets so one barrier per call suffices.
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, float *a) {
+    uint32_t r[16];
+    CPA_LD16(0, ta);
+#undef CPA_LD16
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) a[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float *v) {
+    tmem_st8(taddr, v);
+    tmem_st8(taddr + 8, v + 8);
+}
+
+// Block sum of one float per thread of the first 128 (the scalar phases'
+// threads; the others pass 0 and only take part in the barrier); the
+// partials alternate between two slot sets so one barrier per call suffices.
 __device__ __forceinline__ float bsum(float x, float *red8, int &slot) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     float *r = red8 + 4 * (slot & 1);
     ++slot;
-    if ((threadIdx.x & 31) == 0) r[threadIdx.x >> 5] = x;
+    if ((threadIdx.x & 31) == 0 && threadIdx.x < kRows) r[threadIdx.x >> 5] = x;
     __syncthreads();
     return (r[0] + r[1]) + (r[2] + r[3]);
 }
@@ -321,6 +363,7 @@ __global__ void __launch_bounds__(kT, 1)
     uint8_t *R1 = base, *R2 = base + kR1;
     Small &S = *reinterpret_cast<Small *>(base + kR1 + kR2);
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid & (kRows - 1), c0q = 32 * (tid / kRows);   // this thread's row and 32-column chunk
     constexpr uint32_t cACC = 0, cPSI0 = 128, cPSI1 = 256, cH = 384;
 
     if (warp == 0) {
@@ -337,21 +380,22 @@ __global__ void __launch_bounds__(kT, 1)
     __syncthreads();
     fence_after();
     const uint32_t tmem = S.tmem_slot;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's 32 lanes = its 32 rows
+    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);   // this warp's 32 lanes (rows)
     volatile int *abort_flag = &S.abort_flag;
     uint32_t phase = 0;
 
     // One split product into TMEM columns [0, N): operands written by every
     // thread are made visible to the tensor core, one thread issues, all wait.
     auto run_product = [&](const uint8_t *ahi, const uint8_t *alo, int aslice, const uint8_t *bhi,
-                           const uint8_t *blo, int bslice, int kslices, int N) -> bool {
+                           const uint8_t *blo, int bslice, int kslices, int N, uint32_t acc0 = 0) -> bool {
         tmem_st_wait();
         fence_proxy_async();
         fence_before();
         __syncthreads();
         if (tid == 0) {
             fence_after();
-            issue_split_product(tmem + cACC, ahi, alo, aslice, bhi, blo, bslice, kslices, idesc_bf16(128, N), &S.bar);
+            issue_split_product(tmem + cACC, ahi, alo, aslice, bhi, blo, bslice, kslices, idesc_bf16(128, N), &S.bar,
+                                acc0);
         }
         mbar_wait(&S.bar, phase, abort_flag);
         phase ^= 1;
@@ -371,39 +415,53 @@ __global__ void __launch_bounds__(kT, 1)
         int L = L_in ? L_in[idx] : d.L;
         const bool tall = m >= n;
         const int p = tall ? n : m, q = tall ? m : n;
-        const int Np = (p + 15) & ~15, Kp = (p + 63) & ~63, Kq = (q + 63) & ~63, Nq = (q + 15) & ~15;
+        const int Np = (p + 15) & ~15, Kp = (p + 63) & ~63;
         const float *Xg = d.x ? d.x : X + d.off;
         float *Yg = d.x ? d.y : Y + d.off;
         const int64_t ldxm = d.x ? d.ldx : n, ldym = d.x ? d.ldy : n;
         const ShrinkParams sp = shr[shr_stride ? idx : 0];
-        const bool own = tid < p;
+        const bool own = tid < p;        // scalar phases: thread tid < 128 is row tid
+        const bool rowin = row < p;      // element-wise passes
 
-        // ---- X_p (= X^T when m >= n, else X; p x q) into R1, zero padded
-        zero_smem(R1, 2 * kXLo);
-        __syncthreads();
-        for (int e = tid; e < m * n; e += kT) {
-            const int i = e / n, j = e - i * n;
-            const float v = __ldg(Xg + (int64_t)i * ldxm + j);
-            put1(R1, R1 + kXLo, kSlice128, tall ? j : i, tall ? i : j, v);
+        // ---- Gram G = X_p X_p^T, X_p = X^T when m >= n, else X (p x q):
+        // K chunks of 256 columns of X_p staged in R1 (zero padded) and
+        // accumulated in tensor memory
+        bool ok = true;
+        for (int k0 = 0; k0 < q && ok; k0 += kChunkQ) {
+            const int kc = min(kChunkQ, q - k0);
+            zero_smem(R1, 2 * kXLo);
+            __syncthreads();
+            if (tall) {   // X_p[r][k0 + c] = X[k0 + c][r]: rows of X are contiguous in r
+                for (int e = tid; e < kc * p; e += kT) {
+                    const int c = e / p, r = e - c * p;
+                    put1(R1, R1 + kXLo, kSlice128, r, c, __ldg(Xg + (int64_t)(k0 + c) * ldxm + r));
+                }
+            } else {      // X_p[r][k0 + c] = X[r][k0 + c]
+                for (int e = tid; e < p * kc; e += kT) {
+                    const int r = e / kc, c = e - r * kc;
+                    put1(R1, R1 + kXLo, kSlice128, r, c, __ldg(Xg + (int64_t)r * ldxm + k0 + c));
+                }
+            }
+            ok = run_product(R1, R1 + kXLo, kSlice128, R1, R1 + kXLo, kSlice128, ((kc + 63) & ~63) / 64, Np,
+                             k0 > 0 ? 1u : 0u);
         }
-        // ---- Gram G = X_p X_p^T
-        if (!run_product(R1, R1 + kXLo, kSlice128, R1, R1 + kXLo, kSlice128, Kq / 64, Np)) break;
+        if (!ok) break;
         float *g = reinterpret_cast<float *>(R1);
-        for (int c0 = 0; c0 < Np; c0 += 32) {
+        if (c0q < Np) {
             float a[32];
-            tmem_ld32(trow + cACC + c0, a);
-            if (own)
+            tmem_ld32(trow + cACC + c0q, a);
+            if (rowin)
 #pragma unroll
                 for (int e = 0; e < 32; ++e)
-                    if (c0 + e < p) g[tid * kLdG + c0 + e] = a[e];
+                    if (c0q + e < p) g[row * kLdG + c0q + e] = a[e];
         }
         __syncthreads();
         // exactly symmetric G: the lower triangle takes the upper one (the
         // products below multiply by the operand's rows, A B^T, which is
         // A B only for an exactly symmetric B; rounding asymmetry would grow
         // along the recurrence)
-        if (own)
-            for (int j = 0; j < tid; ++j) g[tid * kLdG + j] = g[j * kLdG + tid];
+        if (rowin)
+            for (int j = c0q; j < min(c0q + 32, row); ++j) g[row * kLdG + j] = g[j * kLdG + row];
         __syncthreads();
 
         // ---- Lambda_max: power iteration (definition of cpa_lambda_bound)
@@ -496,26 +554,30 @@ __global__ void __launch_bounds__(kT, 1)
         // parts (operand in R1)
         {
             const float s2 = S.s2, c0h = 0.5f * S.coef[0], c1 = L > 1 ? S.coef[1] : 0.f;
-            for (int c0 = 0; c0 < Kp; c0 += 32) {
-                float at[32], z1[32], z0[32], hh[32];
+            if (c0q < Kp) {
 #pragma unroll
-                for (int e = 0; e < 32; ++e) {
-                    const int j = c0 + e;
-                    const bool in = own && j < p;
-                    const float eye = (in && j == tid) ? 1.f : 0.f;
-                    at[e] = in ? s2 * g[tid * kLdG + j] : 0.f;
-                    z1[e] = at[e] - eye;
-                    z0[e] = eye;
-                    hh[e] = fmaf(c1, z1[e], c0h * eye);
-                }
+                for (int hf = 0; hf < 32; hf += 16) {
+                    const int c0 = c0q + hf;
+                    float at[16], z1[16], z0[16], hh[16];
 #pragma unroll
-                for (int u = 0; u < 32; u += 8) {
-                    put8(R2, R2 + 2 * kSlice128, kSlice128, tid, c0 + u, at + u);
-                    put8(R1 + kPsiHi, R1 + kPsiLo, kSlice128, tid, c0 + u, z1 + u);
+                    for (int e = 0; e < 16; ++e) {
+                        const int j = c0 + e;
+                        const bool in = rowin && j < p;
+                        const float eye = (in && j == row) ? 1.f : 0.f;
+                        at[e] = in ? s2 * g[row * kLdG + j] : 0.f;
+                        z1[e] = at[e] - eye;
+                        z0[e] = eye;
+                        hh[e] = fmaf(c1, z1[e], c0h * eye);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 16; u += 8) {
+                        put8(R2, R2 + 2 * kSlice128, kSlice128, row, c0 + u, at + u);
+                        put8(R1 + kPsiHi, R1 + kPsiLo, kSlice128, row, c0 + u, z1 + u);
+                    }
+                    tmem_st16(trow + cPSI1 + c0, z1);
+                    tmem_st16(trow + cPSI0 + c0, z0);
+                    tmem_st16(trow + cH + c0, hh);
                 }
-                tmem_st32(trow + cPSI1 + c0, z1);
-                tmem_st32(trow + cPSI0 + c0, z0);
-                tmem_st32(trow + cH + c0, hh);
             }
         }
 
@@ -528,34 +590,43 @@ __global__ void __launch_bounds__(kT, 1)
             const uint32_t sPrev = ((k - 1) & 1) ? cPSI1 : cPSI0, sOld = (k & 1) ? cPSI1 : cPSI0;
             // pass 1: row tid of 2 At Psi_{k-1} - 2 Psi_{k-1} - Psi_{k-2} into
             // the FP32 scratch (the Gram matrix's space, free after the shift)
+            // (every row, including the zero padding rows, so that pass 2
+            // reads written values only)
             float *w = reinterpret_cast<float *>(R1);
-            for (int c0 = 0; c0 < Np; c0 += 32) {
-                float a[32], z1[32], z0[32];
-                tmem_ld32(trow + cACC + c0, a);
-                tmem_ld32(trow + sPrev + c0, z1);
-                tmem_ld32(trow + sOld + c0, z0);
-                if (own)
+            if (c0q < Np) {
 #pragma unroll
-                    for (int e = 0; e < 32; ++e)
-                        w[tid * kLdG + c0 + e] = fmaf(2.f, a[e], fmaf(-2.f, z1[e], -z0[e]));
+                for (int hf = 0; hf < 32; hf += 16) {
+                    const int c0 = c0q + hf;
+                    float a[16], z1[16], z0[16];
+                    tmem_ld16x3(trow + cACC + c0, trow + sPrev + c0, trow + sOld + c0, a, z1, z0);
+                    float *wr = w + row * kLdG + c0;
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) wr[e] = fmaf(2.f, a[e], fmaf(-2.f, z1[e], -z0[e]));
+                }
             }
             __syncthreads();
             // pass 2: Psi_k exactly symmetric (the upper triangle's values),
-            // into the ring, the running sum and the next product's operand
-            for (int c0 = 0; c0 < Np; c0 += 32) {
-                float v[32], hh[32];
-                tmem_ld32(trow + cH + c0, hh);
+            // into the ring, the running sum and the next product's operand;
+            // the entries of padding columns j >= p are the zeros pass 1
+            // formed from zero operands and state, padding rows stay zero
+            if (c0q < Np) {
 #pragma unroll
-                for (int e = 0; e < 32; ++e) {
-                    const int j = c0 + e;
-                    const bool in = own && j < p;
-                    v[e] = in ? (j >= tid ? w[tid * kLdG + j] : w[j * kLdG + tid]) : 0.f;
-                    hh[e] = in ? fmaf(ck, v[e], hh[e]) : 0.f;
+                for (int hf = 0; hf < 32; hf += 16) {
+                    const int c0 = c0q + hf;
+                    float v[16], hh[16];
+                    tmem_ld16(trow + cH + c0, hh);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int j = c0 + e;
+                        const float *src = j >= row ? w + row * kLdG + j : w + j * kLdG + row;
+                        v[e] = rowin ? *src : 0.f;
+                        hh[e] = fmaf(ck, v[e], hh[e]);
+                    }
+                    tmem_st16(trow + sOld + c0, v);
+                    tmem_st16(trow + cH + c0, hh);
+                    put8(R1 + kPsiHi, R1 + kPsiLo, kSlice128, row, c0, v);
+                    put8(R1 + kPsiHi, R1 + kPsiLo, kSlice128, row, c0 + 8, v + 8);
                 }
-                tmem_st32(trow + sOld + c0, v);
-                tmem_st32(trow + cH + c0, hh);
-#pragma unroll
-                for (int u = 0; u < 32; u += 8) put8(R1 + kPsiHi, R1 + kPsiLo, kSlice128, tid, c0 + u, v + u);
             }
         }
         if (!alive) break;
@@ -564,39 +635,51 @@ __global__ void __launch_bounds__(kT, 1)
         // R2), X_p^T (q rows of p, operand in R1)
         tmem_st_wait();
         __syncthreads();
-        for (int c0 = 0; c0 < Kp; c0 += 32) {
+        if (c0q < Kp) {
             float hh[32];
-            tmem_ld32(trow + cH + c0, hh);
+            tmem_ld32(trow + cH + c0q, hh);
 #pragma unroll
             for (int e = 0; e < 32; ++e)
-                if (!(own && c0 + e < p)) hh[e] = 0.f;
+                if (!(rowin && c0q + e < p)) hh[e] = 0.f;
 #pragma unroll
-            for (int u = 0; u < 32; u += 8) put8(R2, R2 + 2 * kSlice128, kSlice128, tid, c0 + u, hh + u);
+            for (int u = 0; u < 32; u += 8) put8(R2, R2 + 2 * kSlice128, kSlice128, row, c0q + u, hh + u);
         }
-        zero_smem(R1, 2 * kXtLo);
-        __syncthreads();
-        for (int e = tid; e < m * n; e += kT) {
-            const int i = e / n, j = e - i * n;
-            const float v = __ldg(Xg + (int64_t)i * ldxm + j);
-            // X_p^T row r, column k: X[i][j] with (r, k) = (i, j) (m >= n) or (j, i)
-            put1(R1, R1 + kXtLo, kSlice256, tall ? i : j, tall ? j : i, v);
-        }
-        if (!run_product(R2, R2 + 2 * kSlice128, kSlice128, R1, R1 + kXtLo, kSlice256, Kp / 64, Nq)) break;
-        for (int c0 = 0; c0 < Nq; c0 += 32) {
-            float dv[32];
-            tmem_ld32(trow + cACC + c0, dv);
-            if (own)
-#pragma unroll
-                for (int e = 0; e < 32; ++e) {
-                    const int jq = c0 + e;
-                    if (jq < q) {
-                        if (tall)
-                            Yg[(int64_t)jq * ldym + tid] = dv[e];
-                        else
-                            Yg[(int64_t)tid * ldym + jq] = dv[e];
-                    }
+        // X_p^T (q rows of p) in chunks of 256 rows staged in R1; each
+        // chunk's product D[:, n0 .. n0 + 256) goes straight to Y
+        for (int n0 = 0; n0 < q && ok; n0 += kChunkQ) {
+            const int nc = min(kChunkQ, q - n0), Nc = (nc + 15) & ~15;
+            zero_smem(R1, 2 * kXtLo);
+            __syncthreads();
+            if (tall) {   // X_p^T[rr][k] = X[n0 + rr][k]
+                for (int e = tid; e < nc * p; e += kT) {
+                    const int rr = e / p, k = e - rr * p;
+                    put1(R1, R1 + kXtLo, kSlice256, rr, k, __ldg(Xg + (int64_t)(n0 + rr) * ldxm + k));
                 }
+            } else {      // X_p^T[rr][k] = X[k][n0 + rr]
+                for (int e = tid; e < p * nc; e += kT) {
+                    const int k = e / nc, rr = e - k * nc;
+                    put1(R1, R1 + kXtLo, kSlice256, rr, k, __ldg(Xg + (int64_t)k * ldxm + n0 + rr));
+                }
+            }
+            ok = run_product(R2, R2 + 2 * kSlice128, kSlice128, R1, R1 + kXtLo, kSlice256, Kp / 64, Nc);
+            if (!ok) break;
+            for (int c0 = c0q; c0 < Nc; c0 += 4 * 32) {
+                float dv[32];
+                tmem_ld32(trow + cACC + c0, dv);
+                if (rowin)
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        const int jq = n0 + c0 + e;
+                        if (c0 + e < nc) {
+                            if (tall)
+                                Yg[(int64_t)jq * ldym + row] = dv[e];
+                            else
+                                Yg[(int64_t)row * ldym + jq] = dv[e];
+                        }
+                    }
+            }
         }
+        if (!ok) break;
         tmem_st_wait();
         __syncthreads();   // shared and tensor memory are reused by the next member
     }

@@ -1,6 +1,6 @@
-// Completion ADMM of Section V-E: the inpainting problem of Section V-B
+// Completion ADMM of Section V, Comparison with Existing Methods: the inpainting problem of Section V, Texture Image Inpainting
 // (Eq. texture_repaire4) without its average term, in the ADMM form of
-// Appendix A (Eq. admm_algorithm_inp, the z^(5) block dropped) around the CPA
+// the appendix ADMM Applicable Forms, Texture Image Inpainting (Eq. admm_algorithm_inp, the z^(5) block dropped) around the CPA
 // shrinkage.  z = K l with K = [Id; Psi; Omega; Id], Psi the orthonormal 2-D
 // DCT (Psi l = C_m L C_n^T), Omega the observation mask:
 //   l = (a1 + Psi^T a2 + omega a3 + a4) / (3 + omega),  a_i = z_i - u_i
@@ -9,7 +9,7 @@
 //   z3 = omega i                             the observed values
 //   z4 = min(max(l + u4, 0), 1)
 //   u += K l - z
-// Start (Section V-B): l = u = 1, z = K l.
+// Start (Section V, Texture Image Inpainting): l = u = 1, z = K l.
 //
 // Device state (FP32, m x n, row stride n, owned by the solver): u1..u4,
 // S = a1 + omega a3 + a4 (the spatial part of the next least-squares

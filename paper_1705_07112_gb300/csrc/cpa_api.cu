@@ -15,6 +15,7 @@ using namespace cpa;
 namespace {
 // below this p the BF16 mode also splits the recurrence operands
 constexpr int64_t kSplitRecBelow = 256;
+constexpr int kMaxStreams = 64;   // concurrent member streams of the pointer-form batches
 }  // namespace
 
 struct cpa_ctx {
@@ -39,7 +40,7 @@ struct cpa_ctx {
     // patch-sized members' launch, and per-member choices of the larger
     // members of the last learned call ({L, fallback} pairs, bounds)
     PtrPlan *pplan = nullptr;          // members up to 64 x 128 (mma.sync kernel)
-    PtrPlan *pplan_tc = nullptr;       // members up to 128 x 256 beyond those (tcgen05 kernel)
+    PtrPlan *pplan_tc = nullptr;       // members up to 128 x 4096 beyond those (tcgen05 kernel)
     std::vector<int> serve_mid;        // member indices of the last learned call in the second group
     int *d_big_L = nullptr;
     double *d_big_lam = nullptr;
@@ -48,9 +49,10 @@ struct cpa_ctx {
     // concurrent members: sub-handles (own workspace), each on its own
     // stream forked from the caller's
     int nstreams = 1;
-    cpa_ctx *sub[16] = {};
-    cudaStream_t sub_st[16] = {};
-    cudaEvent_t sub_ev[16] = {};
+    int member_sms = 0;                // SMs per member on those streams (0: all)
+    cpa_ctx *sub[kMaxStreams] = {};
+    cudaStream_t sub_st[kMaxStreams] = {};
+    cudaEvent_t sub_ev[kMaxStreams] = {};
     cudaEvent_t fork_ev = nullptr;
     // diagnostics
     bool profiling = false;
@@ -364,7 +366,7 @@ cpa_status cpa_destroy(cpa_handle h) {
     if (h->start) cudaEventDestroy(h->start);
     ptr_plan_destroy(h->pplan);
     ptr_plan_destroy(h->pplan_tc);
-    for (int k = 0; k < 16; ++k) {
+    for (int k = 0; k < kMaxStreams; ++k) {
         if (h->sub[k]) cpa_destroy(h->sub[k]);
         if (h->sub_st[k]) cudaStreamDestroy(h->sub_st[k]);
         if (h->sub_ev[k]) cudaEventDestroy(h->sub_ev[k]);
@@ -893,8 +895,13 @@ cpa_status cpa_set_option(cpa_handle h, int option, int value) {
         return CPA_OK;
     }
     if (option == CPA_OPT_STREAMS) {
-        if (value < 1 || value > 16) return CPA_ERR_INVALID_ARG;
+        if (value < 1 || value > kMaxStreams) return CPA_ERR_INVALID_ARG;
         h->nstreams = value;
+        return CPA_OK;
+    }
+    if (option == CPA_OPT_MEMBER_SMS) {
+        if (value < 0) return CPA_ERR_INVALID_ARG;
+        h->member_sms = value;
         return CPA_OK;
     }
     if (option == CPA_OPT_SPARSE_SKIP) {
@@ -1098,7 +1105,7 @@ cpa_status ensure_pplan(cpa_ctx *h) {
 
 // The member class of the batched launch: 1 for the mma.sync kernel (p <=
 // 64, q <= 128; measured faster there, two CTAs per SM), 2 for the tcgen05
-// kernel (p <= 128, q <= 256, tensor-core precisions), 0 for the
+// kernel (p <= 128, q <= 4096, tensor-core precisions), 0 for the
 // single-matrix path.
 int member_class(int64_t m, int64_t n, int L, int prec) {
     const int64_t p = std::min(m, n), q = std::max(m, n);
@@ -1115,7 +1122,8 @@ int member_class(int64_t m, int64_t n, int L, int prec) {
 template <class F>
 cpa_status run_members(cpa_ctx *h, const std::vector<int> &order, cudaStream_t st, F fn) {
     const int S = std::min<int>(h->nstreams, (int)order.size());
-    if (S <= 1) {
+    const int sms = h->member_sms > 0 ? std::min(h->member_sms, h->num_sms) : h->num_sms;
+    if (S <= 1 && sms == h->num_sms) {
         for (size_t k = 0; k < order.size(); ++k) {
             cpa_status r = fn(h, (int)k, st);
             if (r != CPA_OK) return r;
@@ -1130,6 +1138,7 @@ cpa_status run_members(cpa_ctx *h, const std::vector<int> &order, cudaStream_t s
             CK(cudaEventCreateWithFlags(&h->sub_ev[j], cudaEventDisableTiming));
         }
         h->sub[j]->series = h->series;
+        h->sub[j]->num_sms = sms;
         h->sub[j]->wait = h->wait;
         h->sub[j]->sparse_skip = h->sparse_skip;
     }

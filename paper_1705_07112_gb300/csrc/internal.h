@@ -248,10 +248,10 @@ struct LearnArgs {
 
 
 // Tensor-core batched launch (batched_tc.cu): members with min(m, n) <= 128
-// and max(m, n) <= 256, every product with the BF16 hi/lo split on tcgen05
+// and max(m, n) <= 4096, every product with the BF16 hi/lo split on tcgen05
 // tiles, the recurrence state in tensor memory, one CTA per member at a
 // time.  Arguments as the batched kernel's (learn: the learned choice).
-constexpr int kTcBatchP = 128, kTcBatchQ = 256;
+constexpr int kTcBatchP = 128, kTcBatchQ = 4096;
 cudaError_t launch_batched_tc(const BatchDesc *desc, const int *order, int count, const float *X, float *Y,
                               const ShrinkParams *shr, int shr_stride, const double *lam_in, double *lam_out,
                               int iters, int *status, const int *L_in, const LearnArgs &la, bool learn,

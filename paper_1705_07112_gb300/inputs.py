@@ -14,14 +14,14 @@ Laboratory video of Section V, are not available; these stand in for them):
                        soft threshold at half the noise-spectrum edge.
 * ``rpca_frame``       1024 x 1024 D = L0 + S0, L0 rank 30 with unit-norm
                        Gaussian factor columns, S0 5 % entries +-U[5,10]
-                       (the background-modelling problem of Section V-C);
+                       (the background-modelling problem of Section V, Background Modeling of Video);
                        soft threshold tau = 1/mu, mu = mn / (4 |D|_1).
 * ``patch_groups``     many 64 x c matrices, c uniform in [40, 80], rank-4
                        Gaussian signal + N(0, 0.05^2): patch groups of 8 x 8
                        patches with weighted soft thresholding.
 * ``video_background`` 4096 x 8192: rank-5 Gaussian background, 3 % sparse
                        foreground +-U[0.5, 1], N(0, 0.01^2) noise.
-* ``block_completion`` Section V-E's synthetic matrix J - blkdiag(0.5 1 1^T, n)
+* ``block_completion`` the synthetic matrix of Section V, Comparison with Existing Methods, J - blkdiag(0.5 1 1^T, n)
                        (rank n, entries 0.5 and 1) with a random x % of its
                        entries set to zero and marked unobserved.
 * ``served_mix``       the learned predictor's serving mix: half patch-group
@@ -180,7 +180,7 @@ def random_gaussian(rng, m, n, scale=1.0):
 
 
 def block_completion(seed_index=0, size=1000, rank=100, frac_zero=0.10):
-    """Section V-E's synthetic completion input: D = J - blkdiag(D_s, rank)
+    """The synthetic completion input of Section V, Comparison with Existing Methods: D = J - blkdiag(D_s, rank)
     with J the all-ones size x size matrix and D_s = 0.5 * ones(b, b),
     b = size / rank (size a multiple of rank); a uniformly random set of
     round(frac_zero * size^2) entries is set to zero.  Returns (D, I, mask):

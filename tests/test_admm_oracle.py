@@ -1,5 +1,5 @@
 """Pins of the FP64 background-modelling ADMM (oracle/admm.py) against the
-mathematics it follows (Appendix B, Eq. admm_algorithm_mod)."""
+mathematics it follows (the appendix ADMM Applicable Forms, Background Modeling, Eq. admm_algorithm_mod)."""
 import numpy as np
 
 import oracle as O

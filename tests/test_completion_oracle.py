@@ -1,7 +1,7 @@
 """Pins of the FP64 completion ADMM (oracle/completion.py) against what the
 paper and the mathematics fix: the DCT against scipy's, the least-squares
 step against LAPACK on the stacked K, the first iterate from the all-ones
-start, recovery of Section V-E's block matrix with the exact shrinkage, and
+start, recovery of the block matrix of Section V, Comparison with Existing Methods with the exact shrinkage, and
 the FP64 CPA run tracking the exact run."""
 import numpy as np
 import pytest
@@ -59,7 +59,7 @@ def test_first_iterate_from_the_all_ones_start():
 
 @pytest.mark.parametrize("size,rank", [(60, 6), (60, 30)])
 def test_exact_run_completes_the_block_matrix(size, rank):
-    """Section V-E's J - blkdiag(0.5 1 1^T, n) with 10 % of its entries
+    """The matrix of Section V, Comparison with Existing Methods, J - blkdiag(0.5 1 1^T, n) with 10 % of its entries
     zeroed is restored: the missing entries to 2e-3, the observed ones kept,
     the range constraint met, within the paper's stop rule E_t < 1e-4."""
     D, I, mask = inputs.block_completion(0, size, rank, 0.10)

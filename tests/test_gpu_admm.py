@@ -103,7 +103,7 @@ def test_admm_full_frame_precisions(lib):
 
 def test_admm_with_the_sparsity_schedule_matches_the_oracle(lib):
     """The ADMM with the sparsity-based reduction (DCT over the frame index)
-    and Section V-D's threshold schedule on smooth frames (96 frames, so the
+    and the threshold schedule of Section V, Effects of Thresholding Value on smooth frames (96 frames, so the
     three kept fractions keep 1, 2 and 5 entries of the 96 x 96 Phi) against
     the FP64 oracle ADMM with the same schedule, FP32 shrinkage."""
     import math

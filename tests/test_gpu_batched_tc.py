@@ -1,8 +1,10 @@
 """The tensor-core batched kernel (one 128-row tcgen05 tile per member,
 recurrence state in tensor memory) against the FP64 oracle, member by
-member, across its whole shape range (p = min(m, n) <= 128, q = max(m, n)
-<= 256), every shrink kind, orders from 1 to 300, with the bound given and
-computed on the device.  Tolerance as for every BF16 split-precision
+member, across its shape range (p = min(m, n) <= 128; q = max(m, n) up to
+2048, so the Gram matrix takes several 256-column chunks of X and the final
+product several 256-column output chunks, with ragged last chunks), every
+shrink kind, orders from 1 to 300, with the bound given and computed on the
+device.  Tolerance as for every BF16 split-precision
 result: 2e-3 relative Frobenius (measures ~1e-5)."""
 import numpy as np
 import pytest
@@ -14,7 +16,8 @@ SEED = 0x1705071120000000
 TOL = 2e-3
 
 SHAPES = [(1, 1), (1, 7), (7, 1), (3, 200), (200, 3), (17, 100), (100, 17), (40, 64), (64, 64), (65, 63),
-          (63, 65), (96, 250), (250, 96), (127, 255), (128, 128), (128, 256), (256, 128), (120, 121)]
+          (63, 65), (96, 250), (250, 96), (127, 255), (128, 128), (128, 256), (256, 128), (120, 121),
+          (57, 513), (513, 57), (128, 1030), (1030, 128), (90, 2048)]
 
 
 @pytest.fixture(scope="module")

@@ -1,6 +1,6 @@
-"""The device completion ADMM (cpa_completion_run, Section V-E) against the
+"""The device completion ADMM (cpa_completion_run, Section V, Comparison with Existing Methods) against the
 FP64 oracle ADMM (oracle/completion.py) with Algorithm 1 in FP64 as the
-shrinkage step, on Section V-E's block matrix J - blkdiag(0.5 1 1^T, n)
+shrinkage step, on the block matrix of Section V, Comparison with Existing Methods J - blkdiag(0.5 1 1^T, n)
 with 10 % of its entries zeroed; (1/rho, eta/rho) = (0.5, 0.1), L = 20."""
 import numpy as np
 import pytest
@@ -75,7 +75,7 @@ def test_completion_stop_rule_and_arguments(lib):
 
 
 def test_completion_full_size_restores_the_block_matrix(lib):
-    """Section V-E's size: 1000 x 1000, rank 100, 10 % zeroed, BF16X3.  The
+    """The size of Section V, Comparison with Existing Methods: 1000 x 1000, rank 100, 10 % zeroed, BF16X3.  The
     oracle cannot run this size in seconds, so the checks are the
     properties any converged run has: E_t falls below 1e-4 (the paper's
     stop rule), the observed entries are kept, the range constraint holds,

@@ -157,9 +157,9 @@ def test_router_members_match_their_paths(lib):
     mem = lib.MemberList(Xs, Ys, specs)
     lib.cpa_serve_learned(h, net, mem, rule, prec="bf16x3")
     Ls, lams, nfb = lib.cpa_serve_read(h, len(mix))
-    # members the batched kernel takes (tensor cores: p <= 128, q <= 256);
+    # members the batched kernels take (tensor cores: p <= 128, q <= 4096);
     # the plan form holds the patch-sized ones among them
-    batched = [i for i, sm in enumerate(mix) if min(sm.X.shape) <= 128 and max(sm.X.shape) <= 256]
+    batched = [i for i, sm in enumerate(mix) if min(sm.X.shape) <= 128 and max(sm.X.shape) <= 4096]
     small = [i for i in batched if min(mix[i].X.shape) <= 64 and max(mix[i].X.shape) <= 128]
     assert 0 < len(small) and len(batched) < len(mix)
     for i in batched:
@@ -228,6 +228,6 @@ def test_router_streams_match_one_stream(lib):
         assert rel(a, b) <= 1e-6
     lib.cpa_set_option(h, lib.OPT_STREAMS, 1)
     with pytest.raises(lib.CpaError):
-        lib.cpa_set_option(h, lib.OPT_STREAMS, 17)
+        lib.cpa_set_option(h, lib.OPT_STREAMS, 65)
     net.close()
     h.close()
