@@ -250,8 +250,19 @@ CPA_API cpa_status cpa_get_coeffs(cpa_handle h, double *c_out, int L, void *stre
  *   recurrence), so that several large members run side by side instead of
  *   one after another; values above the device's SM count mean all.  The
  *   results do not depend on it beyond FP32 summation order. */
+/* CPA_OPT_SPARSE_COMPACT: 1 (the default) lets a call with an entry
+ *   threshold run the bound, shift and recurrence on the block Phi_[S, S]
+ *   of the thresholded operand's nonzero rows S when |S| <= p / 2: every
+ *   polynomial of Phi_ is that of the block on S and a constant c_out (the
+ *   series at 0, or at the guarded interval's lower end mapped) elsewhere,
+ *   so the filter is T_S^T (H_hat(Phi_[S,S]) - c_out Id) T_S + c_out T^T T
+ *   with T_S the rows S of T, equal to the full recurrence's up to rounding;
+ *   the call then synchronises once to read |S|.  The power iteration on
+ *   the block starts from the entries S of the standard start vector, so
+ *   the bound is that of Phi_.  0 runs the recurrence on the full p x p
+ *   operand. */
 enum { CPA_OPT_SERIES = 1, CPA_OPT_WAIT_KCYCLES = 2, CPA_OPT_STALL_TEST = 3, CPA_OPT_SPARSE_SKIP = 4,
-       CPA_OPT_STREAMS = 5, CPA_OPT_MEMBER_SMS = 6 };
+       CPA_OPT_STREAMS = 5, CPA_OPT_MEMBER_SMS = 6, CPA_OPT_SPARSE_COMPACT = 7 };
 enum { CPA_SERIES_FORWARD = 0, CPA_SERIES_CLENSHAW = 1 };
 CPA_API cpa_status cpa_set_option(cpa_handle h, int option, int value);
 
@@ -278,7 +289,9 @@ typedef enum {
 CPA_API cpa_status cpa_profile_enable(cpa_handle h, int enable);
 
 /* Synchronises the device; ms and launches: host arrays of CPA_NSTAGES
- * (either may be NULL).  reset != 0 clears the accumulators afterwards. */
+ * (either may be NULL), summed over the handle and the member streams of
+ * its pointer-form batches (stage times of members that ran side by side
+ * add up).  reset != 0 clears the accumulators afterwards. */
 CPA_API cpa_status cpa_profile_read(cpa_handle h, double *ms, int64_t *launches, int reset);
 
 /* ---------------------------------------------------------------------------

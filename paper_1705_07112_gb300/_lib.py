@@ -34,7 +34,7 @@ EXPORTS = ["cpa_create", "cpa_destroy", "cpa_status_string", "cpa_last_error", "
 BATCH_MMA_SYNC, BATCH_TCGEN05 = 0, 1
 ORDER_SIZE, ORDER_GIVEN = 0, 1
 OPT_SERIES, SERIES_FORWARD, SERIES_CLENSHAW = 1, 0, 1
-OPT_WAIT_KCYCLES, OPT_STALL_TEST, OPT_SPARSE_SKIP, OPT_STREAMS, OPT_MEMBER_SMS = 2, 3, 4, 5, 6
+OPT_WAIT_KCYCLES, OPT_STALL_TEST, OPT_SPARSE_SKIP, OPT_STREAMS, OPT_MEMBER_SMS, OPT_SPARSE_COMPACT = 2, 3, 4, 5, 6, 7
 STAGES = ["prep", "gram", "bound", "coeff", "shift", "recur", "apply", "sparse"]
 T_IDENTITY, T_HAAR1_LOWPASS, T_BLOCK_DCT8, T_DCT = 0, 1, 2, 3
 SPARSE_OFF, SPARSE_ABS, SPARSE_TOPK = 0, 1, 2

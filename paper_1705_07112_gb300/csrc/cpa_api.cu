@@ -34,6 +34,7 @@ struct cpa_ctx {
     WaitPolicy wait;                   // grid-barrier wait limit, test stall
     int *d_err = nullptr;              // error word of the last cpa_svt's tensor-core kernels
     int sparse_skip = 1;               // skip zero tiles of the thresholded operand
+    int sparse_compact = 1;            // recurrence on the thresholded operand's nonzero block
     bool have_learn = false;           // the last call chose its order on the device
     int *d_L = nullptr;                // {L, fallback} of that call
     // pointer-form batches (cpa_svt_batched, cpa_serve_learned): the
@@ -217,6 +218,10 @@ struct SvtWs {
     int *Lsel = nullptr;
     // tile occupancy of the thresholded operand (sparsity-based reduction)
     uint8_t *amask = nullptr;
+    // compaction of the thresholded operand: row flags, the support S, {s},
+    // the series' value on the zero block
+    int *sflags = nullptr, *sidx = nullptr, *sinfo = nullptr;
+    double *cout = nullptr;
     size_t bytes = 0;
 };
 
@@ -262,12 +267,17 @@ SvtWs carve(char *base, int64_t m, int64_t n, int L, int iters, int prec, bool s
         w.eps = c.take<float>(4);
         w.removed2 = c.take<double>(2);
         w.counts = c.take<unsigned long long>(32);
+        w.sflags = c.take<int>(round_up(p, 4));
+        w.sidx = c.take<int>(round_up(p, 4));
+        w.sinfo = c.take<int>(4);
+        w.cout = c.take<double>(2);
     }
     if (prec != CPA_FP32) {
         // Gram and final product always use the hi/lo split (their BF16
         // rounding would otherwise dominate the error); the recurrence
         // operands carry a lo part only in the all-split mode.
-        bool split_rec = prec == CPA_BF16X3 || p < kSplitRecBelow;
+        // (the transform products of the sparsity reduction use the lo parts too)
+        bool split_rec = prec == CPA_BF16X3 || p < kSplitRecBelow || sparse;
         w.ldn = round_up(n, 8);
         w.ldm = round_up(m, 8);
         w.ldk = round_up(p, 128);
@@ -614,13 +624,30 @@ cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
         Epilogue e1;
         e1.D = w.A;   // T G (w.A is free until the shift)
         e1.ldd = w.ldp;
-        CK(gemm_f32((int)p, (int)p, (int)p, w.T, w.ldp, true, w.G, w.ldp, true, e1, st));
         Epilogue e2;
         e2.D = w.G;   // (T G) T^T, exactly symmetric
         e2.ldd = w.ldp;
         e2.symmetric_upper = 1;
-        CK(gemm_f32((int)p, (int)p, (int)p, w.A, w.ldp, true, w.T, w.ldp, true, e2, st));
-        h->launches[CPA_STAGE_SPARSE] += 3;
+        if (!tc) {
+            CK(gemm_f32((int)p, (int)p, (int)p, w.T, w.ldp, true, w.G, w.ldp, true, e1, st));
+            CK(gemm_f32((int)p, (int)p, (int)p, w.A, w.ldp, true, w.T, w.ldp, true, e2, st));
+            h->launches[CPA_STAGE_SPARSE] += 3;
+        } else {
+            // on the tensor cores with the hi/lo split: rows of T and of G
+            // (symmetric) give T G; rows of T G and of T give (T G) T^T
+            e1.err = e2.err = w.flag + 5;
+            e2.sym_full_d = 1;
+            CK(split_bf16(w.T, (int)p, (int)p, w.ldp, false, w.Zhi[0], w.Zlo[0], w.ldk, st));
+            CK(split_bf16(w.G, (int)p, (int)p, w.ldp, false, w.Zhi[1], w.Zlo[1], w.ldk, st));
+            TcOperand tr, gr, tg;
+            tr.hi = w.Zhi[0]; tr.lo = w.Zlo[0]; tr.ld = w.ldk; tr.rows = (int)p;
+            gr.hi = w.Zhi[1]; gr.lo = w.Zlo[1]; gr.ld = w.ldk; gr.rows = (int)p;
+            CK(gemm_tc((int)p, (int)p, (int)p, tr, gr, 3, e1, st, h->num_sms));
+            CK(split_bf16(w.A, (int)p, (int)p, w.ldp, false, w.Ahi, w.Alo, w.ldk, st));
+            tg.hi = w.Ahi; tg.lo = w.Alo; tg.ld = w.ldk; tg.rows = (int)p;
+            CK(gemm_tc((int)p, (int)p, (int)p, tg, tr, 3, e2, st, h->num_sms));
+            h->launches[CPA_STAGE_SPARSE] += 6;
+        }
         if (guarded) CK(cudaMemsetAsync(w.removed2, 0, sizeof(double), st));
         if (sp->mode == CPA_SPARSE_ABS) {
             CK(threshold_entries(w.G, (int)p, w.ldp, nullptr, (float)sp->eps_or_frac, st, h->num_sms,
@@ -634,6 +661,28 @@ cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
                         h->num_sms));
             CK(threshold_entries(w.G, (int)p, w.ldp, w.eps, 0.f, st, h->num_sms, guarded ? w.removed2 : nullptr));
             h->launches[CPA_STAGE_SPARSE] += 2;
+        }
+    }
+    // compaction: when the thresholded operand's nonzero rows S are at most
+    // half of them, the bound, shift and recurrence run on the |S| x |S|
+    // block Phi_[S, S] (its polynomials are those of Phi_ on S and a
+    // constant elsewhere; sparsify.cu's header); one synchronisation reads |S|
+    int64_t pr = p;   // the order of the matrix the series is built on
+    bool compact = false;
+    if (sparse && sp->mode != CPA_SPARSE_OFF && !learn && h->sparse_compact && iters >= 1) {
+        StageScope sc(h, CPA_STAGE_SPARSE, st, 2);
+        CK(sparse_support(w.G, (int)p, w.ldp, w.sflags, w.sidx, w.sinfo, st, h->num_sms));
+        int *pin = reinterpret_cast<int *>(h->h_pin + 10);
+        CK(cudaMemcpyAsync(pin, w.sinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const int sdim = pin[0];
+        if (sdim >= 1 && 2 * (int64_t)sdim <= p) {
+            compact = true;
+            pr = sdim;
+            CK(gather_block(w.G, w.ldp, w.sidx, sdim, w.Z[0], w.ldp, st, h->num_sms));
+            CK(cudaMemcpy2DAsync(w.G, (size_t)w.ldp * sizeof(float), w.Z[0], (size_t)w.ldp * sizeof(float),
+                                 (size_t)sdim * sizeof(float), (size_t)sdim, cudaMemcpyDeviceToDevice, st));
+            h->launches[CPA_STAGE_SPARSE] += 1;
         }
     }
     // interval bound
@@ -653,8 +702,9 @@ cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
     } else {
         // the bound's launch also forms the coefficients (FP64) in its last block
         StageScope sc(h, CPA_STAGE_BOUND, st, 1);
-        CK(power_bound_persistent(w.G, w.ldp, (int)p, iters, w.v0, w.v1, w.norm2, (unsigned int *)w.flag,
-                                  w.flag + 1, w.out, st, h->num_sms, L, &sp_, w.coef, h->wait));
+        CK(power_bound_persistent(w.G, w.ldp, (int)pr, iters, w.v0, w.v1, w.norm2, (unsigned int *)w.flag,
+                                  w.flag + 1, w.out, st, h->num_sms, L, &sp_, w.coef, h->wait,
+                                  compact ? w.sidx : nullptr));
     }
     // guarded interval [-|Phi - Phi_|_F, Lambda_max]: its ends are read
     // once (one synchronisation) and its coefficients formed on the host
@@ -679,7 +729,7 @@ cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
     // shift and initial sum; Psi_1 = B_hat lives in ring slot 1
     {
         StageScope sc(h, CPA_STAGE_SHIFT, st, 1);
-        CK(shift_init(w.G, w.ldp, (int)p, w.out + 3, w.coef, L, tc ? nullptr : w.A, w.Z[1], w.H, w.ldp,
+        CK(shift_init(w.G, w.ldp, (int)pr, w.out + 3, w.coef, L, tc ? nullptr : w.A, w.Z[1], w.H, w.ldp,
                       tc ? w.Ahi : nullptr, tc ? w.Alo : nullptr, tc ? w.Zhi[1] : nullptr,
                       tc ? w.Zlo[1] : nullptr, tc ? w.ldk : w.ldp, st, h->num_sms, clenshaw,
                       tc ? w.Zhi[0] : nullptr, tc ? w.Zlo[0] : nullptr, span, sigma));
@@ -707,10 +757,12 @@ cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
         e.symmetric_upper = 1;
         e.err = w.flag + 5;
         TcOperand a;
-        a.hi = w.Ahi; a.lo = w.Alo; a.ld = w.ldk; a.rows = (int)p;
-        CK(gemm_tc_recurrence((int)p, a, nsplit_rec, e, 2, L, w.Z, w.Zhi, w.Zlo, (unsigned int *)(w.flag + 2), st,
-                              h->num_sms, clenshaw, L, &closed, (int)w.ldk, h->wait, learn ? w.Lsel : nullptr,
-                              (sparse && sp->mode != CPA_SPARSE_OFF && h->sparse_skip) ? w.amask : nullptr));
+        a.hi = w.Ahi; a.lo = w.Alo; a.ld = w.ldk; a.rows = (int)pr;
+        CK(gemm_tc_recurrence((int)pr, a, nsplit_rec, e, 2, L, w.Z, w.Zhi, w.Zlo, (unsigned int *)(w.flag + 2), st,
+                              h->num_sms, clenshaw, L, &closed, compact ? (int)round_up(pr, 128) : (int)w.ldk,
+                              h->wait, learn ? w.Lsel : nullptr,
+                              (sparse && sp->mode != CPA_SPARSE_OFF && h->sparse_skip && !compact) ? w.amask
+                                                                                                    : nullptr));
     }
     if (learn && !tc) {
         // the CUDA-core recurrence is driven from the host: read the order
@@ -753,7 +805,7 @@ cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
             e.C2 = w.Z[prev];
             e.ldc2 = w.ldp;
             e.s_c2 = (float)(-2.0 * sigma);
-            CK(gemm_f32((int)p, (int)p, (int)p, w.A, w.ldp, true, w.Z[prev], w.ldp, true, e, st));
+            CK(gemm_f32((int)pr, (int)pr, (int)pr, w.A, w.ldp, true, w.Z[prev], w.ldp, true, e, st));
         } else {
             e.C2 = w.Z[prev];                  // Psi_{k-1}
             e.ldc2 = w.ldp;
@@ -763,32 +815,67 @@ cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
             e.ldb = w.ldk;
             e.err = w.flag + 5;
             TcOperand a, b;
-            a.hi = w.Ahi; a.lo = w.Alo; a.ld = w.ldk; a.rows = (int)p;
-            b.hi = w.Zhi[prev]; b.lo = w.Zlo[prev]; b.ld = w.ldk; b.rows = (int)p;
-            CK(gemm_tc((int)p, (int)p, (int)p, a, b, nsplit_rec, e, st, h->num_sms));
+            a.hi = w.Ahi; a.lo = w.Alo; a.ld = w.ldk; a.rows = (int)pr;
+            b.hi = w.Zhi[prev]; b.lo = w.Zlo[prev]; b.ld = w.ldk; b.rows = (int)pr;
+            CK(gemm_tc((int)pr, (int)pr, (int)pr, a, b, nsplit_rec, e, st, h->num_sms));
         }
     }
     // Clenshaw's closing step: H = (b_0 - b_2) / 2, b_2 in ring slot (L-1)&1
     // (L = 3: b_2 = c_2 Id); the tensor-core path keeps the lower triangle
     if (clenshaw && L >= 3 && !closed) {
         StageScope sc(h, CPA_STAGE_RECUR, st, 1);
-        CK(clenshaw_finish(w.H, L == 3 ? nullptr : w.Z[(L - 1) & 1], (int)p, w.ldp, w.coef, tc ? 1 : 0, st,
+        CK(clenshaw_finish(w.H, L == 3 ? nullptr : w.Z[(L - 1) & 1], (int)pr, w.ldp, w.coef, tc ? 1 : 0, st,
                            h->num_sms));
     }
     // with the sparsity option the filter applied to X is T^T H T (Eq. SVD_fil)
     float *Hf = w.H;
-    if (sparse) {
-        StageScope sc(h, CPA_STAGE_SPARSE, st, 2 + (tc ? 1 : 0));
-        if (tc) CK(symmetrize_lower(w.H, (int)p, w.ldp, st, h->num_sms));
+    if (sparse && compact) {
+        // T^T H T = T_S^T (H_hat(A) - c_out Id) T_S + c_out T^T T
+        StageScope sc(h, CPA_STAGE_SPARSE, st, 6 + (tc ? 1 : 0));
+        if (tc) CK(symmetrize_lower(w.H, (int)pr, w.ldp, st, h->num_sms));
+        const double sig = guarded ? sigma : 1.0;
+        CK(zero_block_value(w.coef, L, sig, w.cout, st));
+        CK(diag_add(w.H, (int)pr, w.ldp, w.cout, -1.0, st));
+        CK(gather_rows(w.T, w.ldp, w.sidx, (int)pr, (int)p, w.Z[0], w.ldp, st, h->num_sms));
+        Epilogue ew;
+        ew.D = w.Z[1];   // (H_hat(A) - c_out Id) T_S, |S| x p
+        ew.ldd = w.ldp;
+        CK(gemm_f32((int)pr, (int)p, (int)pr, w.H, w.ldp, true, w.Z[0], w.ldp, false, ew, st));
+        Epilogue ef;
+        ef.D = w.A;      // T_S^T (...) T_S, p x p, exactly symmetric
+        ef.ldd = w.ldp;
+        ef.symmetric_upper = 1;
+        CK(gemm_f32((int)p, (int)p, (int)pr, w.Z[0], w.ldp, false, w.Z[1], w.ldp, false, ef, st));
+        CK(add_transform_gram(w.A, (int)p, w.ldp, sp->transform, w.cout, st));
+        Hf = w.A;
+    } else if (sparse) {
+        StageScope sc(h, CPA_STAGE_SPARSE, st, tc ? 6 : 2);
         Epilogue e1;
         e1.D = w.Z[0];   // T^T H
         e1.ldd = w.ldp;
-        CK(gemm_f32((int)p, (int)p, (int)p, w.T, w.ldp, false, w.H, w.ldp, true, e1, st));
         Epilogue e2;
         e2.D = w.Z[1];   // (T^T H) T
         e2.ldd = w.ldp;
         e2.symmetric_upper = 1;
-        CK(gemm_f32((int)p, (int)p, (int)p, w.Z[0], w.ldp, true, w.T, w.ldp, false, e2, st));
+        if (!tc) {
+            CK(gemm_f32((int)p, (int)p, (int)p, w.T, w.ldp, false, w.H, w.ldp, true, e1, st));
+            CK(gemm_f32((int)p, (int)p, (int)p, w.Z[0], w.ldp, true, w.T, w.ldp, false, e2, st));
+        } else {
+            // tensor cores: rows of T^T and of H (symmetric) give T^T H; rows
+            // of T^T H and of T^T give (T^T H) T
+            CK(symmetrize_lower(w.H, (int)p, w.ldp, st, h->num_sms));
+            e1.err = e2.err = w.flag + 5;
+            e2.sym_full_d = 1;
+            CK(split_bf16(w.T, (int)p, (int)p, w.ldp, true, w.Zhi[0], w.Zlo[0], w.ldk, st));
+            CK(split_bf16(w.H, (int)p, (int)p, w.ldp, false, w.Zhi[1], w.Zlo[1], w.ldk, st));
+            TcOperand ttr, hr, th;
+            ttr.hi = w.Zhi[0]; ttr.lo = w.Zlo[0]; ttr.ld = w.ldk; ttr.rows = (int)p;
+            hr.hi = w.Zhi[1]; hr.lo = w.Zlo[1]; hr.ld = w.ldk; hr.rows = (int)p;
+            CK(gemm_tc((int)p, (int)p, (int)p, ttr, hr, 3, e1, st, h->num_sms));
+            CK(split_bf16(w.Z[0], (int)p, (int)p, w.ldp, false, w.Ahi, w.Alo, w.ldk, st));
+            th.hi = w.Ahi; th.lo = w.Alo; th.ld = w.ldk; th.rows = (int)p;
+            CK(gemm_tc((int)p, (int)p, (int)p, th, ttr, 3, e2, st, h->num_sms));
+        }
         Hf = w.Z[1];
     }
     // final product: Y = X H (m >= n) or H X (m < n)
@@ -909,6 +996,11 @@ cpa_status cpa_set_option(cpa_handle h, int option, int value) {
         h->sparse_skip = value;
         return CPA_OK;
     }
+    if (option == CPA_OPT_SPARSE_COMPACT) {
+        if (value != 0 && value != 1) return CPA_ERR_INVALID_ARG;
+        h->sparse_compact = value;
+        return CPA_OK;
+    }
     if (option == CPA_OPT_STALL_TEST) {
         if (value != 0 && value != 1) return CPA_ERR_INVALID_ARG;
         h->wait.stall = value;
@@ -920,14 +1012,17 @@ cpa_status cpa_set_option(cpa_handle h, int option, int value) {
 cpa_status cpa_profile_enable(cpa_handle h, int enable) {
     if (!h) return CPA_ERR_INVALID_ARG;
     h->profiling = enable != 0;
+    for (int k = 0; k < kMaxStreams; ++k)
+        if (h->sub[k]) h->sub[k]->profiling = h->profiling;
     return CPA_OK;
 }
 
-cpa_status cpa_profile_read(cpa_handle h, double *ms, int64_t *launches, int reset) {
-    if (!h) return CPA_ERR_INVALID_ARG;
-    cpa_status s = set_device(h);
-    if (s != CPA_OK) return s;
-    CK(cudaDeviceSynchronize());
+}  // extern "C"
+
+namespace {
+
+// The stage times of a handle's finished event pairs into its totals.
+void collect_profile(cpa_ctx *h) {
     for (auto &p : h->pending) {
         float t = 0.f;
         if (cudaEventElapsedTime(&t, p.second.first, p.second.second) == cudaSuccess) h->ms[p.first] += t;
@@ -935,14 +1030,43 @@ cpa_status cpa_profile_read(cpa_handle h, double *ms, int64_t *launches, int res
         h->event_pool.push_back(p.second.second);
     }
     h->pending.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+cpa_status cpa_profile_read(cpa_handle h, double *ms, int64_t *launches, int reset) {
+    if (!h) return CPA_ERR_INVALID_ARG;
+    cpa_status s = set_device(h);
+    if (s != CPA_OK) return s;
+    CK(cudaDeviceSynchronize());
+    // the handle's own stages and those of its member sub-handles (members
+    // of pointer-form batches run there)
+    collect_profile(h);
     for (int i = 0; i < CPA_NSTAGES; ++i) {
-        if (ms) ms[i] = h->ms[i];
-        if (launches) launches[i] = h->launches[i];
-        if (reset) {
+        double t = h->ms[i];
+        int64_t n = h->launches[i];
+        for (int k = 0; k < kMaxStreams; ++k) {
+            cpa_ctx *c = h->sub[k];
+            if (!c) continue;
+            if (i == 0) collect_profile(c);
+            t += c->ms[i];
+            n += c->launches[i];
+        }
+        if (ms) ms[i] = t;
+        if (launches) launches[i] = n;
+    }
+    if (reset)
+        for (int i = 0; i < CPA_NSTAGES; ++i) {
             h->ms[i] = 0.0;
             h->launches[i] = 0;
+            for (int k = 0; k < kMaxStreams; ++k)
+                if (h->sub[k]) {
+                    h->sub[k]->ms[i] = 0.0;
+                    h->sub[k]->launches[i] = 0;
+                }
         }
-    }
     return CPA_OK;
 }
 
@@ -1139,8 +1263,10 @@ cpa_status run_members(cpa_ctx *h, const std::vector<int> &order, cudaStream_t s
         }
         h->sub[j]->series = h->series;
         h->sub[j]->num_sms = sms;
+        h->sub[j]->profiling = h->profiling;
         h->sub[j]->wait = h->wait;
         h->sub[j]->sparse_skip = h->sparse_skip;
+        h->sub[j]->sparse_compact = h->sparse_compact;
     }
     if (!h->fork_ev) CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
     CK(cudaEventRecord(h->fork_ev, st));

@@ -155,6 +155,20 @@ cudaError_t threshold_entries(float *Phi, int p, int64_t ld, const float *eps_de
 cudaError_t symmetrize_lower(float *S, int p, int64_t ld, cudaStream_t st, int num_sms);
 cudaError_t topk_eps(const float *Phi, int p, int64_t ld, long long k, unsigned long long *counts, unsigned int *bar,
                      int *err, float *eps_out, cudaStream_t st, int num_sms);
+// Compaction of a thresholded Phi_ to the block of its nonzero rows S (the
+// identities in sparsify.cu's header): S (idx, ascending) and s = |S| on
+// the device (flags: p ints of scratch); the s x s block; rows S of T; the
+// series' value c_out on the zero block; H += scale c on the diagonal; F +=
+// c T^T T for a transform type.
+cudaError_t sparse_support(const float *Phi, int p, int64_t ld, int *flags, int *idx, int *s_dev, cudaStream_t st,
+                           int num_sms);
+cudaError_t gather_block(const float *Phi, int64_t ld, const int *idx, int s, float *A, int64_t lda, cudaStream_t st,
+                         int num_sms);
+cudaError_t gather_rows(const float *T, int64_t ld, const int *idx, int s, int p, float *R, int64_t ldr,
+                        cudaStream_t st, int num_sms);
+cudaError_t zero_block_value(const double *c, int L, double sigma, double *c_out, cudaStream_t st);
+cudaError_t diag_add(float *H, int s, int64_t ld, const double *c, double scale, cudaStream_t st);
+cudaError_t add_transform_gram(float *F, int p, int64_t ld, int type, const double *c, cudaStream_t st);
 
 // Elementwise conversion of a row-major FP32 matrix to BF16 hi/lo parts,
 // optionally transposed (out is cols x rows then).
@@ -176,7 +190,11 @@ cudaError_t power_bound(const float *G, int64_t ldg, int p, int iters, float *v0
 cudaError_t power_bound_persistent(const float *G, int64_t ldg, int p, int iters, float *v0, float *v1,
                                    double *norm2, unsigned int *bar, int *err, double *out, cudaStream_t st,
                                    int num_sms, int L = 0, const ShrinkParams *sp = nullptr,
-                                   double *coef = nullptr, const WaitPolicy &wp = WaitPolicy());
+                                   double *coef = nullptr, const WaitPolicy &wp = WaitPolicy(),
+                                   const int *start_idx = nullptr);
+// start_idx (optional, p ints): the start vector's entry i is entry
+// start_idx[i] of the standard one (the bound of a principal block,
+// computed as the bound of the matrix it is the nonzero block of).
 cudaError_t device_coeffs(const double *lam_dev, double lam_host, int L, const ShrinkParams &s, double *c,
                           cudaStream_t st);
 // B_hat = (2/lambda) G - Id: Z1 = B_hat, H = c0/2 Id + c1 B_hat (FP32), and

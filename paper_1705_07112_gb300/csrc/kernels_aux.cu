@@ -356,7 +356,8 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
                                                                double *norm2, unsigned int *bar, double margin,
                                                                double *out, int *err, int cache, int stage,
                                                                int L, ShrinkParams sp, double *coef,
-                                                               long long wait_cycles, int stall) {
+                                                               long long wait_cycles, int stall,
+                                                               const int *__restrict__ start_idx) {
     extern __shared__ __align__(16) float grow[];
     __shared__ float wpart[16];    // per-warp |w|^2 partials
     __shared__ float sscale;       // 1 / |v| of the current iterate
@@ -372,7 +373,9 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
             v1[i] = 0.f;
         }
         for (int i = threadIdx.x; i < p; i += blockDim.x) {
-            uint64_t z = splitmix64_output(seed, (uint64_t)i);
+            // entry i of the start vector, or entry start_idx[i] of the
+            // start vector of the matrix this one is the block of
+            uint64_t z = splitmix64_output(seed, (uint64_t)(start_idx ? start_idx[i] : i));
             float x = (float)((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
             v0[i] = x;
             sacc += (double)x * (double)x;
@@ -545,7 +548,8 @@ __global__ void __launch_bounds__(512) power_persistent_kernel(const float *__re
 
 cudaError_t power_bound_persistent(const float *G, int64_t ldg, int p, int iters, float *v0, float *v1,
                                    double *norm2, unsigned int *bar, int *err, double *out, cudaStream_t st,
-                                   int num_sms, int L, const ShrinkParams *sp, double *coef, const WaitPolicy &wp) {
+                                   int num_sms, int L, const ShrinkParams *sp, double *coef, const WaitPolicy &wp,
+                                   const int *start_idx) {
     cudaError_t r = cudaMemsetAsync(bar, 0, sizeof(unsigned int), st);
     if (r != cudaSuccess) return r;
     r = cudaMemsetAsync(err, 0, sizeof(int), st);
@@ -582,7 +586,7 @@ cudaError_t power_bound_persistent(const float *G, int64_t ldg, int p, int iters
     const uint64_t seed = kStartSeed;
     const ShrinkParams spv = sp ? *sp : ShrinkParams{};
     return cudaLaunchKernelEx(&cfg, power_persistent_kernel, G, ldg, p, iters, seed, v0, v1, norm2, bar, margin, out,
-                              err, cache, stage, coef ? L : 0, spv, coef, wait_limit(wp), wp.stall);
+                              err, cache, stage, coef ? L : 0, spv, coef, wait_limit(wp), wp.stall, start_idx);
 }
 
 cudaError_t power_bound(const float *G, int64_t ldg, int p, int iters, float *v0, float *v1,

@@ -15,6 +15,20 @@
 // eps: given (mode ABS) or the k-th largest |Phi_ij|, k = ceil(frac p^2)
 // clamped to [1, p^2] (mode TOPK, Eq. recommendation_epsilon's K(|Phi|, k));
 // entries equal to eps are kept.
+//
+// Compaction.  Let S be the indices of the rows of Phi_ with a nonzero
+// entry (s = |S|; Phi_ is symmetric, so its columns outside S are zero
+// too).  After a permutation Phi_ = blockdiag(A, 0) with A = Phi_[S, S], so
+// every polynomial of Phi_ -- each T_k(B_hat) and the truncated series H_hat
+// -- is blockdiag(H_hat(A), c_out I) with c_out the series' value on the
+// zero block: c_out = c_0 / 2 + sum_k c_k T_k(-sigma) (sigma = 1 on [0, b],
+// (a + b) / (b - a) on the guarded interval).  The recurrence then runs on
+// the s x s block A alone, and the filter applied to X is
+//   T^T H T = T_S^T (H_hat(A) - c_out I) T_S + c_out T^T T
+// with T_S the rows S of T (T^T T = I for the orthonormal transforms; for
+// the masked Haar transform a 2 x 2 block-diagonal projection).  The power
+// iteration on A from the start vector's entries at S gives the bound of
+// Phi_ itself: every product with Phi_ is supported on S.
 #include <algorithm>
 
 #include "internal.h"
@@ -125,7 +139,143 @@ __global__ void topk_eps_kernel(const float *__restrict__ Phi, int p, int64_t ld
     if (blockIdx.x == 0 && threadIdx.x == 0) *eps_out = __uint_as_float(t);
 }
 
+// flags[i] = 1 when row i of Phi has a nonzero entry (a warp per row).
+__global__ void support_kernel(const float *__restrict__ Phi, int p, int64_t ld, int *flags) {
+    const int lane = threadIdx.x & 31;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < p; i += (gridDim.x * blockDim.x) >> 5) {
+        const float *r = Phi + (int64_t)i * ld;
+        bool nz = false;
+        for (int j = lane; j < p && !nz; j += 32) nz = __ldg(r + j) != 0.f;
+        nz = __any_sync(0xffffffffu, nz);
+        if (lane == 0) flags[i] = nz ? 1 : 0;
+    }
+}
+
+// idx[0 .. s) = the flagged rows in ascending order, *s_out = s (one block).
+__global__ void compact_kernel(const int *__restrict__ flags, int p, int *idx, int *s_out) {
+    __shared__ int warp_tot[32];
+    __shared__ int base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < p; c0 += blockDim.x) {
+        const int i = c0 + threadIdx.x;
+        const int f = i < p ? flags[i] : 0;
+        const unsigned int bal = __ballot_sync(0xffffffffu, f);
+        const int before = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) warp_tot[warp] = __popc(bal);
+        __syncthreads();
+        int off = base;
+        for (int w = 0; w < warp; ++w) off += warp_tot[w];
+        if (f) idx[off + before] = i;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int w = 0; w < nw; ++w) base += warp_tot[w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *s_out = base;
+}
+
+// A[a][b] = Phi[idx[a]][idx[b]], a, b < s.
+__global__ void gather_block_kernel(const float *__restrict__ Phi, int64_t ld, const int *__restrict__ idx, int s,
+                                    float *A, int64_t lda) {
+    const int64_t total = (int64_t)s * s;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(e / s), b = (int)(e % s);
+        A[(int64_t)a * lda + b] = Phi[(int64_t)__ldg(idx + a) * ld + __ldg(idx + b)];
+    }
+}
+
+// R[a][j] = T[idx[a]][j], a < s, j < p.
+__global__ void gather_rows_kernel(const float *__restrict__ T, int64_t ld, const int *__restrict__ idx, int s, int p,
+                                   float *R, int64_t ldr) {
+    const int64_t total = (int64_t)s * p;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(e / p), j = (int)(e % p);
+        R[(int64_t)a * ldr + j] = T[(int64_t)__ldg(idx + a) * ld + j];
+    }
+}
+
+// *c_out = c_0 / 2 + sum_{k=1}^{L-1} c_k T_k(-sigma) (FP64, the three-term
+// recurrence of the Chebyshev polynomials at the scalar -sigma).
+__global__ void zero_block_value_kernel(const double *__restrict__ c, int L, double sigma, double *c_out) {
+    const double x = -sigma;
+    double t0 = 1.0, t1 = x, v = 0.5 * c[0];
+    if (L > 1) v += c[1] * t1;
+    for (int k = 2; k < L; ++k) {
+        const double t2 = 2.0 * x * t1 - t0;
+        v += c[k] * t2;
+        t0 = t1;
+        t1 = t2;
+    }
+    *c_out = v;
+}
+
+// H[i][i] += scale * (*c), i < s (FP32 result).
+__global__ void diag_add_kernel(float *H, int s, int64_t ld, const double *__restrict__ c, double scale) {
+    const float v = (float)(scale * *c);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < s; i += gridDim.x * blockDim.x) H[(int64_t)i * ld + i] += v;
+}
+
+// F += (*c) T^T T for the transform `type` (p x p): the identity for the
+// orthonormal transforms; for the masked Haar transform 1/2 on each 2 x 2
+// block of the pairs (2i, 2i + 1), i < floor(p/2), and 1 at (p-1, p-1) for
+// odd p.
+__global__ void add_transform_gram_kernel(float *F, int p, int64_t ld, int type, const double *__restrict__ c) {
+    const float v = (float)*c;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p; i += gridDim.x * blockDim.x) {
+        if (type != CPA_T_HAAR1_LOWPASS) {
+            F[(int64_t)i * ld + i] += v;
+        } else if ((p & 1) && i == p - 1) {
+            F[(int64_t)i * ld + i] += v;
+        } else {
+            const int j = i ^ 1;   // the pair's other index
+            F[(int64_t)i * ld + i] += 0.5f * v;
+            F[(int64_t)i * ld + j] += 0.5f * v;
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t sparse_support(const float *Phi, int p, int64_t ld, int *flags, int *idx, int *s_dev, cudaStream_t st,
+                           int num_sms) {
+    const int blocks = std::max(1, std::min((p + 7) / 8, num_sms * 4));
+    support_kernel<<<blocks, 256, 0, st>>>(Phi, p, ld, flags);
+    compact_kernel<<<1, 1024, 0, st>>>(flags, p, idx, s_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t gather_block(const float *Phi, int64_t ld, const int *idx, int s, float *A, int64_t lda, cudaStream_t st,
+                         int num_sms) {
+    const int64_t total = (int64_t)s * s;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 8));
+    gather_block_kernel<<<blocks, 256, 0, st>>>(Phi, ld, idx, s, A, lda);
+    return cudaGetLastError();
+}
+
+cudaError_t gather_rows(const float *T, int64_t ld, const int *idx, int s, int p, float *R, int64_t ldr,
+                        cudaStream_t st, int num_sms) {
+    const int64_t total = (int64_t)s * p;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 8));
+    gather_rows_kernel<<<blocks, 256, 0, st>>>(T, ld, idx, s, p, R, ldr);
+    return cudaGetLastError();
+}
+
+cudaError_t zero_block_value(const double *c, int L, double sigma, double *c_out, cudaStream_t st) {
+    zero_block_value_kernel<<<1, 1, 0, st>>>(c, L, sigma, c_out);
+    return cudaGetLastError();
+}
+
+cudaError_t diag_add(float *H, int s, int64_t ld, const double *c, double scale, cudaStream_t st) {
+    diag_add_kernel<<<std::max(1, std::min((s + 255) / 256, 64)), 256, 0, st>>>(H, s, ld, c, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t add_transform_gram(float *F, int p, int64_t ld, int type, const double *c, cudaStream_t st) {
+    add_transform_gram_kernel<<<std::max(1, std::min((p + 255) / 256, 64)), 256, 0, st>>>(F, p, ld, type, c);
+    return cudaGetLastError();
+}
 
 cudaError_t make_transform(int type, int p, float *T, int64_t ld, cudaStream_t st, int num_sms) {
     const int64_t total = (int64_t)p * p;

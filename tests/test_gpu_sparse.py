@@ -1,5 +1,8 @@
 """The sparsity-based reduction on the device (transform, entry threshold,
-X T^T H(Phi_) T) against the oracle's Algorithm 1 with the same T and eps.
+X T^T H(Phi_) T) against the oracle's Algorithm 1 with the same T and eps,
+with the recurrence on the full thresholded operand and on the block of its
+nonzero rows (CPA_OPT_SPARSE_COMPACT), which the smooth inputs here make
+small: the two routes compute the same filter.
 
 T is built here from its definition (independently of the library's
 generator); eps is chosen in a wide gap of the oracle's |Phi| values so that
@@ -94,10 +97,13 @@ def smooth_matrix(rng, m, n):
 @pytest.mark.parametrize("tkind", [0, 1, 2, 3])
 @pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
-def test_sparsify_matches_oracle(cpa, handle, shape, tkind, mode, prec):
+@pytest.mark.parametrize("compact", [1, 0])
+def test_sparsify_matches_oracle(cpa, handle, shape, tkind, mode, prec, compact):
     import torch
     if tkind == 0 and mode == 0:
         pytest.skip("identical to the plain path")
+    if mode == 0 and compact == 0:
+        pytest.skip("no entry threshold: nothing to compact")
     rng = np.random.default_rng(shape[0] * 13 + shape[1] + 7 * tkind)
     X = smooth_matrix(rng, *shape)
     if tkind == 0:
@@ -120,11 +126,15 @@ def test_sparsify_matches_oracle(cpa, handle, shape, tkind, mode, prec):
     L = 15
     ref = O.cpa(X, s, L, lam, T=None if tkind == 0 else T, eps_thr=eps)
     Xd = torch.from_numpy(X.astype(np.float32)).cuda()
-    Y = cpa.cpa_svt(handle, Xd, {"kind": O.SOFT, "tau": s.tau}, L, lam, prec, sparsify=(tkind, mode, arg))
-    torch.cuda.synchronize()
+    cpa._lib.cpa_set_option(handle, cpa._lib.OPT_SPARSE_COMPACT, compact)
+    try:
+        Y = cpa.cpa_svt(handle, Xd, {"kind": O.SOFT, "tau": s.tau}, L, lam, prec, sparsify=(tkind, mode, arg))
+        torch.cuda.synchronize()
+    finally:
+        cpa._lib.cpa_set_option(handle, cpa._lib.OPT_SPARSE_COMPACT, 1)
     got = Y.cpu().numpy().astype(np.float64)
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    assert err <= TOL[prec], (shape, tkind, mode, prec, err)
+    assert err <= TOL[prec], (shape, tkind, mode, prec, compact, err)
 
 
 def test_sparsify_argument_errors(cpa, handle):
@@ -172,7 +182,8 @@ def wide_gap(Phi, lo_frac=0.0005, hi_frac=0.5):
 @pytest.mark.parametrize("tkind", [0, 1, 2, 3])
 @pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
-def test_sparsify_full_size_sampled(cpa, handle, tkind, mode, prec):
+@pytest.mark.parametrize("compact", [1, 0])
+def test_sparsify_full_size_sampled(cpa, handle, tkind, mode, prec, compact):
     """p = 1024 with every transform and both threshold modes: sampled rows
     of X T^T H_hat(Phi_) T against the oracle (Phi from the C oracle, the
     series on the sampled rows by the oracle's block vector form)."""
@@ -189,21 +200,25 @@ def test_sparsify_full_size_sampled(cpa, handle, tkind, mode, prec):
     rows = [0, 1, 550, 1098, 1099]
     want = (T.T @ O.filter_block(Phib, s, L, lam, T @ X[rows].T)).T
     Xd = torch.from_numpy(X.astype(np.float32)).cuda()
-    Y = cpa.cpa_svt(handle, Xd, {"kind": O.SOFT, "tau": s.tau}, L, lam, prec, sparsify=(tkind, mode, arg))
-    torch.cuda.synchronize()
+    cpa._lib.cpa_set_option(handle, cpa._lib.OPT_SPARSE_COMPACT, compact)
+    try:
+        Y = cpa.cpa_svt(handle, Xd, {"kind": O.SOFT, "tau": s.tau}, L, lam, prec, sparsify=(tkind, mode, arg))
+        torch.cuda.synchronize()
+    finally:
+        cpa._lib.cpa_set_option(handle, cpa._lib.OPT_SPARSE_COMPACT, 1)
     got = Y.cpu().numpy().astype(np.float64)
     scale = np.linalg.norm(got) / np.sqrt(len(got))
     for j, i in enumerate(rows):
         err = np.linalg.norm(got[i] - want[j]) / max(np.linalg.norm(want[j]), scale)
-        assert err <= TOL[prec], (tkind, mode, prec, i, err, k)
+        assert err <= TOL[prec], (tkind, mode, prec, compact, i, err, k)
 
 
 @pytest.mark.parametrize("tkind", [0, 1, 2, 3])
 @pytest.mark.parametrize("mode", [1, 2])
 def test_zero_tile_skip_is_bit_identical(cpa, handle, tkind, mode):
-    """The recurrence skips the all-zero tiles of the thresholded operand:
-    the same result, bit for bit, as running every tile (the skipped
-    products are exact zeros)."""
+    """The recurrence on the full thresholded operand (no compaction) skips
+    its all-zero tiles: the same result, bit for bit, as running every tile
+    (the skipped products are exact zeros)."""
     import torch
     from paper_1705_07112_gb300 import _lib
     X, T, Phi = _big_case(tkind)
@@ -214,12 +229,16 @@ def test_zero_tile_skip_is_bit_identical(cpa, handle, tkind, mode):
     lam = 1.05 * np.max(np.abs(np.linalg.eigvalsh(np.where(np.abs(Phi) >= eps, Phi, 0.0))))
     spec = {"kind": O.SOFT, "tau": 0.1 * math.sqrt(lam)}
     out = []
-    for skip in (1, 0):
-        _lib.cpa_set_option(handle, _lib.OPT_SPARSE_SKIP, skip)
-        Y = cpa.cpa_svt(handle, Xd, spec, 15, lam, "bf16x3", sparsify=(tkind, mode, arg))
-        torch.cuda.synchronize()
-        out.append(Y.cpu().numpy())
-    _lib.cpa_set_option(handle, _lib.OPT_SPARSE_SKIP, 1)
+    _lib.cpa_set_option(handle, _lib.OPT_SPARSE_COMPACT, 0)
+    try:
+        for skip in (1, 0):
+            _lib.cpa_set_option(handle, _lib.OPT_SPARSE_SKIP, skip)
+            Y = cpa.cpa_svt(handle, Xd, spec, 15, lam, "bf16x3", sparsify=(tkind, mode, arg))
+            torch.cuda.synchronize()
+            out.append(Y.cpu().numpy())
+    finally:
+        _lib.cpa_set_option(handle, _lib.OPT_SPARSE_SKIP, 1)
+        _lib.cpa_set_option(handle, _lib.OPT_SPARSE_COMPACT, 1)
     assert np.array_equal(out[0], out[1])
 
 
@@ -227,7 +246,8 @@ def test_zero_tile_skip_is_bit_identical(cpa, handle, tkind, mode):
 @pytest.mark.parametrize("tkind", [2, 3])
 @pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
-def test_guarded_interval_matches_oracle(cpa, handle, shape, tkind, mode, prec):
+@pytest.mark.parametrize("compact", [1, 0])
+def test_guarded_interval_matches_oracle(cpa, handle, shape, tkind, mode, prec, compact):
     """The guarded interval [-|Phi - Phi_|_F, Lambda_max] for the
     thresholded Phi_ (cpa_sparsify.interval = 1) against the oracle's
     guarded form (oracle/interval.py) with the same T, eps and Lambda_max."""
@@ -246,11 +266,15 @@ def test_guarded_interval_matches_oracle(cpa, handle, shape, tkind, mode, prec):
     L = 15
     ref = I.guarded_cpa(X, s, L, lam, T, eps)
     Xd = torch.from_numpy(X.astype(np.float32)).cuda()
-    Y = cpa.cpa_svt(handle, Xd, {"kind": O.SOFT, "tau": s.tau}, L, lam, prec, sparsify=(tkind, mode, arg, 1))
-    torch.cuda.synchronize()
+    cpa._lib.cpa_set_option(handle, cpa._lib.OPT_SPARSE_COMPACT, compact)
+    try:
+        Y = cpa.cpa_svt(handle, Xd, {"kind": O.SOFT, "tau": s.tau}, L, lam, prec, sparsify=(tkind, mode, arg, 1))
+        torch.cuda.synchronize()
+    finally:
+        cpa._lib.cpa_set_option(handle, cpa._lib.OPT_SPARSE_COMPACT, 1)
     got = Y.cpu().numpy().astype(np.float64)
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    assert err <= TOL[prec], (shape, tkind, mode, prec, err)
+    assert err <= TOL[prec], (shape, tkind, mode, prec, compact, err)
     # the unguarded result differs where Phi_ has negative eigenvalues
     if np.min(np.linalg.eigvalsh(np.where(np.abs(Phi) >= eps, Phi, 0.0))) < -1e-6 * lam:
         plain = O.cpa(X, s, L, lam, T=T, eps_thr=eps)

@@ -131,3 +131,51 @@ def test_interval_ends_and_convergence_to_h():
     H = I.filter_matrix(Phs, I.coeffs_interval(s, 400, a, b), a, b)
     hmu = np.array([O.h(s, x) if x > 0 else 0.0 for x in mu])
     assert np.abs(np.diag(Q.T @ H @ Q) - hmu).max() < 2e-2
+
+
+def test_block_compaction_identity():
+    """The identity the device's compaction of a thresholded operand rests
+    on: for a symmetric Phi_ whose nonzero rows (and columns) are S, the
+    series H_hat(Phi_) on [a, b] is H_hat(Phi_[S, S]) on S x S, zero between
+    S and its complement, and c_out Id on the complement with c_out the
+    series at the scalar -sigma, sigma = (a + b) / (b - a); the transformed
+    filter T^T H T is T_S^T (H_hat(Phi_[S,S]) - c_out Id) T_S + c_out T^T T.
+    Checked on both the plain interval [0, b] and a guarded one, for an
+    orthonormal T (DCT by QR of a random matrix) and the masked Haar T."""
+    p = 23
+    S = np.array([1, 4, 5, 11, 17, 22])
+    B = RNG.standard_normal((len(S), len(S)))
+    A = B @ B.T - 0.3 * np.eye(len(S))   # a spectrum reaching below zero, inside [a, b] below
+    Phi = np.zeros((p, p))
+    Phi[np.ix_(S, S)] = A
+    rest = np.setdiff1d(np.arange(p), S)
+    Q = rand_orth(p)
+    haar = np.zeros((p, p))
+    for i in range(p // 2):
+        haar[i, 2 * i] = haar[i, 2 * i + 1] = math.sqrt(0.5)
+    haar[p // 2, p - 1] = 1.0
+    s = O.Shrink(O.SOFT, 0.7)
+    lam = 1.02 * np.max(np.linalg.eigvalsh(A))
+    for (a, b) in ((0.0, lam), (-0.8, lam)):
+        for L in (1, 2, 3, 9, 16):
+            c = I.coeffs_interval(s, L, a, b)
+            Hf = I.filter_matrix(Phi, c, a, b)
+            Hb = I.filter_matrix(A, c, a, b)
+            ck = c.copy()
+            ck[0] *= 0.5
+            c_out = np.polynomial.chebyshev.chebval(-(a + b) / (b - a), ck)
+            assert np.allclose(Hf[np.ix_(S, S)], Hb, rtol=0, atol=1e-12)
+            assert np.allclose(Hf[np.ix_(S, rest)], 0.0, rtol=0, atol=1e-12)
+            assert np.allclose(Hf[np.ix_(rest, rest)], c_out * np.eye(len(rest)), rtol=0, atol=1e-12)
+            for T in (Q, haar):
+                TS = T[S]
+                want = T.T @ Hf @ T
+                got = TS.T @ (Hb - c_out * np.eye(len(S))) @ TS + c_out * (T.T @ T)
+                assert np.allclose(got, want, rtol=0, atol=1e-12 * max(1.0, np.abs(want).max()))
+    # the masked Haar transform's T^T T: 1/2 on the 2 x 2 blocks of the
+    # pairs (2i, 2i + 1) and 1 at (p - 1, p - 1) for odd p
+    want = np.zeros((p, p))
+    for i in range(p // 2):
+        want[2 * i:2 * i + 2, 2 * i:2 * i + 2] = 0.5
+    want[p - 1, p - 1] = 1.0
+    assert np.allclose(haar.T @ haar, want, rtol=0, atol=1e-15)
