@@ -318,6 +318,12 @@ CPA_API cpa_status cpa_kernel_gemm_bf16(int M, int N, int K, const void *A_hi, c
                                         void *Dhi, void *Dlo, int64_t ldh, void *stream);
 CPA_API cpa_status cpa_kernel_split_bf16(const float *X, int rows, int cols, int64_t ldx, int transpose, void *hi,
                                          void *lo, int64_t ldo, void *stream);
+/* cpa_kernel_topk_eps: the entry threshold of CPA_SPARSE_TOPK alone: the
+ * k-th largest |Phi_ij| (1 <= k <= p^2) of a p x p device matrix (ld >= p),
+ * the 𝒦(|Phi|, k) of Eq. recommendation_epsilon, to *eps_host.  Allocates
+ * and frees its scratch and synchronises `stream`. */
+CPA_API cpa_status cpa_kernel_topk_eps(const float *Phi, int p, int64_t ld, long long k, float *eps_host,
+                                       void *stream);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free Lambda_max bound.  The paper has no counterpart: this is a

@@ -23,7 +23,7 @@ PREC = {"fp32": FP32, "tf32": TF32, "bf16": BF16, "bf16x3": BF16X3}
 EXPORTS = ["cpa_create", "cpa_destroy", "cpa_status_string", "cpa_last_error", "cpa_coeffs",
            "cpa_lambda_bound", "cpa_svt", "cpa_svt_host", "cpa_get_lambda", "cpa_get_coeffs", "cpa_batch_create",
            "cpa_batch_destroy", "cpa_svt_batched_plan", "cpa_svt_batched", "cpa_batch_lambdas", "cpa_profile_enable",
-           "cpa_profile_read", "cpa_kernel_gemm_bf16", "cpa_kernel_split_bf16", "cpa_batch_read_lambdas",
+           "cpa_profile_read", "cpa_kernel_gemm_bf16", "cpa_kernel_split_bf16", "cpa_kernel_topk_eps", "cpa_batch_read_lambdas",
            "cpa_lambda_bound_noalloc", "cpa_mlp_create", "cpa_mlp_destroy", "cpa_mlp_param_count",
            "cpa_mlp_set_params", "cpa_mlp_get_params", "cpa_mlp_forward", "cpa_mlp_gradients",
            "cpa_mlp_train_step", "cpa_batch_features", "cpa_svt_batched_learned", "cpa_batch_read_choices",
@@ -135,6 +135,8 @@ def load(path: str = LIB_PATH):
                                                     ctypes.c_int, _vp, _i64, _vp, _vp, _i64, _vp]),
             "cpa_kernel_split_bf16": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, ctypes.c_int, _vp,
                                                      _vp, _i64, _vp]),
+            "cpa_kernel_topk_eps": (ctypes.c_int, [_vp, ctypes.c_int, _i64, ctypes.c_longlong, _P(ctypes.c_float),
+                                                   _vp]),
             "cpa_profile_read": (ctypes.c_int, [_vp, _P(_d), _P(_i64), ctypes.c_int]),
             "cpa_set_option": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
             "cpa_admm_create": (ctypes.c_int, [_vp, _i64, _i64, _P(_vp)]),
@@ -365,6 +367,15 @@ def kernel_split_bf16(X, transpose, hi, lo, stream=None):
     rows, cols = X.shape
     _check(load().cpa_kernel_split_bf16(_ptr(X), rows, cols, X.stride(0), 1 if transpose else 0, _ptr(hi),
                                         _ptr(lo), hi.stride(0), _stream_ptr(stream)), "cpa_kernel_split_bf16")
+
+
+def kernel_topk_eps(Phi, k, stream=None):
+    """The k-th largest |Phi_ij| of a square device matrix (cpa_kernel_topk_eps)."""
+    p = Phi.shape[0]
+    out = ctypes.c_float(0.0)
+    _check(load().cpa_kernel_topk_eps(_ptr(Phi), p, Phi.stride(0), int(k), ctypes.byref(out), _stream_ptr(stream)),
+           "cpa_kernel_topk_eps")
+    return float(out.value)
 
 
 class BatchPlan:

@@ -261,13 +261,17 @@ cpa_status cpa_completion_create(cpa_handle h, int64_t m, int64_t n, cpa_complet
     c->Xl = take(m * c->bn);
     c->Th = take(n * c->bm);
     c->Tl = take(n * c->bm);
-    if (make_transform(CPA_T_DCT, (int)m, c->Cm, m, 0, c->num_sms) != cudaSuccess ||
-        make_transform(CPA_T_DCT, (int)n, c->Cn, n, 0, c->num_sms) != cudaSuccess ||
+    float *tab = nullptr;   // the DCT's cosine table (4 max(m, n) floats), freed below
+    if (cudaMalloc(&tab, sizeof(float) * 4 * (size_t)std::max(m, n)) != cudaSuccess ||
+        make_transform(CPA_T_DCT, (int)m, c->Cm, m, 0, c->num_sms, tab) != cudaSuccess ||
+        make_transform(CPA_T_DCT, (int)n, c->Cn, n, 0, c->num_sms, tab) != cudaSuccess ||
         split_bf16(c->Cm, (int)m, (int)m, m, false, c->Cmh, c->Cml, c->bm, 0) != cudaSuccess ||
         split_bf16(c->Cm, (int)m, (int)m, m, true, c->CmTh, c->CmTl, c->bm, 0) != cudaSuccess ||
         split_bf16(c->Cn, (int)n, (int)n, n, false, c->Cnh, c->Cnl, c->bn, 0) != cudaSuccess ||
         split_bf16(c->Cn, (int)n, (int)n, n, true, c->CnTh, c->CnTl, c->bn, 0) != cudaSuccess ||
         cudaStreamSynchronize(0) != cudaSuccess) {
+        cudaGetLastError();
+        if (tab) cudaFree(tab);
         cudaFree(c->Cm);
         cudaFree(c->Cn);
         cudaFree(c->state);
@@ -275,6 +279,7 @@ cpa_status cpa_completion_create(cpa_handle h, int64_t m, int64_t n, cpa_complet
         delete c;
         return CPA_ERR_CUDA;
     }
+    cudaFree(tab);
     *out = c;
     return CPA_OK;
 }

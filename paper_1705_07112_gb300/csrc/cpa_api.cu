@@ -266,7 +266,7 @@ SvtWs carve(char *base, int64_t m, int64_t n, int L, int iters, int prec, bool s
         w.T = c.take<float>(pp);
         w.eps = c.take<float>(4);
         w.removed2 = c.take<double>(2);
-        w.counts = c.take<unsigned long long>(32);
+        w.counts = c.take<unsigned long long>(kTopkCounts);
         w.sflags = c.take<int>(round_up(p, 4));
         w.sidx = c.take<int>(round_up(p, 4));
         w.sinfo = c.take<int>(4);
@@ -620,7 +620,7 @@ cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
     // sparsity-based reduction: Phi = T G T^T, entries below eps set to zero
     if (sparse) {
         StageScope sc(h, CPA_STAGE_SPARSE, st, 0);
-        CK(make_transform(sp->transform, (int)p, w.T, w.ldp, st, h->num_sms));
+        CK(make_transform(sp->transform, (int)p, w.T, w.ldp, st, h->num_sms, w.Z[1]));   // Z[1]: free scratch
         Epilogue e1;
         e1.D = w.A;   // T G (w.A is free until the shift)
         e1.ldd = w.ldp;
@@ -649,9 +649,12 @@ cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
             h->launches[CPA_STAGE_SPARSE] += 6;
         }
         if (guarded) CK(cudaMemsetAsync(w.removed2, 0, sizeof(double), st));
+        // the threshold also marks the rows that keep a nonzero entry (the
+        // compaction's support)
+        int *rf = (sp->mode != CPA_SPARSE_OFF && !learn && h->sparse_compact && iters >= 1) ? w.sflags : nullptr;
         if (sp->mode == CPA_SPARSE_ABS) {
             CK(threshold_entries(w.G, (int)p, w.ldp, nullptr, (float)sp->eps_or_frac, st, h->num_sms,
-                                 guarded ? w.removed2 : nullptr));
+                                 guarded ? w.removed2 : nullptr, rf));
             h->launches[CPA_STAGE_SPARSE] += 1;
         } else if (sp->mode == CPA_SPARSE_TOPK) {
             const double pp2 = (double)p * (double)p;
@@ -659,7 +662,8 @@ cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
             k = std::max(1LL, std::min(k, (long long)pp2));
             CK(topk_eps(w.G, (int)p, w.ldp, k, w.counts, (unsigned int *)(w.flag + 3), w.flag + 4, w.eps, st,
                         h->num_sms));
-            CK(threshold_entries(w.G, (int)p, w.ldp, w.eps, 0.f, st, h->num_sms, guarded ? w.removed2 : nullptr));
+            CK(threshold_entries(w.G, (int)p, w.ldp, w.eps, 0.f, st, h->num_sms, guarded ? w.removed2 : nullptr,
+                                 rf));
             h->launches[CPA_STAGE_SPARSE] += 2;
         }
     }
@@ -670,8 +674,8 @@ cpa_status svt_impl(cpa_ctx *h, const float *dX, int64_t m, int64_t n, int64_t l
     int64_t pr = p;   // the order of the matrix the series is built on
     bool compact = false;
     if (sparse && sp->mode != CPA_SPARSE_OFF && !learn && h->sparse_compact && iters >= 1) {
-        StageScope sc(h, CPA_STAGE_SPARSE, st, 2);
-        CK(sparse_support(w.G, (int)p, w.ldp, w.sflags, w.sidx, w.sinfo, st, h->num_sms));
+        StageScope sc(h, CPA_STAGE_SPARSE, st, 1);
+        CK(compact_support(w.sflags, (int)p, w.sidx, w.sinfo, st));
         int *pin = reinterpret_cast<int *>(h->h_pin + 10);
         CK(cudaMemcpyAsync(pin, w.sinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -1123,6 +1127,34 @@ cpa_status cpa_kernel_split_bf16(const float *X, int rows, int cols, int64_t ldx
     return CPA_OK;
 }
 
+cpa_status cpa_kernel_topk_eps(const float *Phi, int p, int64_t ld, long long k, float *eps_host, void *stream) {
+    if (!Phi || !eps_host || p < 1 || ld < p || k < 1 || k > (long long)p * (long long)p) return CPA_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        return CPA_ERR_CUDA;
+    char *scratch = nullptr;
+    const size_t cbytes = (size_t)kTopkCounts * sizeof(unsigned long long);
+    if (cudaMalloc(&scratch, cbytes + 64) != cudaSuccess) {
+        cudaGetLastError();
+        return CPA_ERR_NO_MEMORY;
+    }
+    unsigned int *bar = reinterpret_cast<unsigned int *>(scratch + cbytes);
+    int *err = reinterpret_cast<int *>(scratch + cbytes + 16);
+    float *eps = reinterpret_cast<float *>(scratch + cbytes + 32);
+    int err_h = 0;
+    cudaError_t e = topk_eps(Phi, p, ld, k, reinterpret_cast<unsigned long long *>(scratch), bar, err, eps, st, sms);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(eps_host, eps, sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err_h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(scratch);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return CPA_ERR_CUDA;
+    }
+    return err_h ? (cpa_status)err_h : CPA_OK;
+}
 
 // A sequence of host matrices through cpa_svt with the copies overlapped:
 // slot i % 2 holds matrix i on the device.  The H2D copy of matrix i + 1

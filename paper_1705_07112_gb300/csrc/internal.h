@@ -149,19 +149,22 @@ cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epil
 // loads and products (the sparsity-based reduction's thresholded operand).
 
 // Sparsity-based reduction helpers (sparsify.cu).
-cudaError_t make_transform(int type, int p, float *T, int64_t ld, cudaStream_t st, int num_sms);
+// scratch: 4p floats, needed by the DCT (its table of cosines).
+cudaError_t make_transform(int type, int p, float *T, int64_t ld, cudaStream_t st, int num_sms, float *scratch);
+// row_flags (optional, p ints): set to 1 for the rows that keep a nonzero
+// entry (the support used by the compaction), 0 for the others.
 cudaError_t threshold_entries(float *Phi, int p, int64_t ld, const float *eps_dev, float eps_host, cudaStream_t st,
-                              int num_sms, double *removed2 = nullptr);
+                              int num_sms, double *removed2 = nullptr, int *row_flags = nullptr);
 cudaError_t symmetrize_lower(float *S, int p, int64_t ld, cudaStream_t st, int num_sms);
 cudaError_t topk_eps(const float *Phi, int p, int64_t ld, long long k, unsigned long long *counts, unsigned int *bar,
                      int *err, float *eps_out, cudaStream_t st, int num_sms);
+constexpr int kTopkCounts = 4 * 256;   // counts scratch of topk_eps (unsigned long long)
 // Compaction of a thresholded Phi_ to the block of its nonzero rows S (the
 // identities in sparsify.cu's header): S (idx, ascending) and s = |S| on
-// the device (flags: p ints of scratch); the s x s block; rows S of T; the
-// series' value c_out on the zero block; H += scale c on the diagonal; F +=
-// c T^T T for a transform type.
-cudaError_t sparse_support(const float *Phi, int p, int64_t ld, int *flags, int *idx, int *s_dev, cudaStream_t st,
-                           int num_sms);
+// the device from the row flags the threshold wrote; the s x s block; rows
+// S of T; the series' value c_out on the zero block; H += scale c on the
+// diagonal; F += c T^T T for a transform type.
+cudaError_t compact_support(const int *flags, int p, int *idx, int *s_dev, cudaStream_t st);
 cudaError_t gather_block(const float *Phi, int64_t ld, const int *idx, int s, float *A, int64_t lda, cudaStream_t st,
                          int num_sms);
 cudaError_t gather_rows(const float *T, int64_t ld, const int *idx, int s, int p, float *R, int64_t ldr,

@@ -41,7 +41,14 @@ __device__ double dct_entry(int size, int k, int j) {
     return s * cospi((2.0 * j + 1.0) * k / (2.0 * size));
 }
 
-__global__ void make_transform_kernel(int type, int p, float *T, int64_t ld) {
+// cos(pi n / (2 p)), n = 0 .. 4p - 1 (FP64, rounded to FP32): every entry
+// of the p x p DCT-II is s_k times one of them, n = (2j + 1) k mod 4p.
+__global__ void dct_table_kernel(int p, float *tab) {
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < 4 * p; n += gridDim.x * blockDim.x)
+        tab[n] = (float)cospi((double)n / (2.0 * p));
+}
+
+__global__ void make_transform_kernel(int type, int p, float *T, int64_t ld, const float *__restrict__ dct_tab) {
     const int64_t total = (int64_t)p * p;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(e / p), j = (int)(e % p);
@@ -59,7 +66,11 @@ __global__ void make_transform_kernel(int type, int p, float *T, int64_t ld) {
                 v = dct_entry(size, i - 8 * b, j - 8 * b);
             }
         } else {
-            v = dct_entry(p, i, j);
+            // s_k cos(pi (2j + 1) k / 2p) from the table (exact index arithmetic)
+            const int64_t n = ((int64_t)(2 * j + 1) * i) % (4 * (int64_t)p);
+            const float sk = i == 0 ? (float)sqrt(1.0 / p) : (float)sqrt(2.0 / p);
+            T[(int64_t)i * ld + j] = sk * __ldg(dct_tab + n);
+            continue;
         }
         T[(int64_t)i * ld + j] = (float)v;
     }
@@ -68,16 +79,19 @@ __global__ void make_transform_kernel(int type, int p, float *T, int64_t ld) {
 // Entries below eps set to zero; removed2 (optional) accumulates the sum of
 // their squares, |Phi - Phi_|_F^2 (per-warp FP32 partials, FP64 atomics).
 __global__ void threshold_kernel(float *Phi, int p, int64_t ld, const float *eps_dev, float eps_host,
-                                 double *removed2) {
+                                 double *removed2, int *row_flags) {
     const float eps = eps_dev ? *eps_dev : eps_host;
     const int64_t total = (int64_t)p * p;
     float r2 = 0.f;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        float *q = Phi + (e / p) * ld + e % p;
+        const int64_t i = e / p;
+        float *q = Phi + i * ld + e % p;
         const float v = *q;
         if (!(fabsf(v) >= eps)) {
             r2 = fmaf(v, v, r2);
             *q = 0.f;
+        } else if (row_flags && v != 0.f) {
+            row_flags[i] = 1;   // row i keeps a nonzero entry (same value from every writer)
         }
     }
     if (removed2) {
@@ -95,10 +109,13 @@ __global__ void symmetrize_lower_kernel(float *S, int p, int64_t ld) {
     }
 }
 
-// eps = k-th largest |Phi_ij| by a bitwise search over the IEEE bit patterns
-// of |Phi| (order-preserving for non-negative floats): bit b from 30 down to
-// 0 is kept when at least k entries are >= the candidate.  One cooperative
-// launch; a grid barrier per bit.
+// eps = k-th largest |Phi_ij| by a radix select over the IEEE bit patterns
+// of |Phi| (order-preserving for non-negative floats), most significant
+// digit first: bits 30..23, 22..15, 14..7, 6..0.  Each pass histograms the
+// digit of the entries that match the digits chosen so far (per-block
+// shared-memory histogram, added into global counts), then every block
+// picks, from the top bin down, the bin holding the remaining rank.  One
+// cooperative launch; a bounded grid barrier per pass.
 __device__ __forceinline__ void grid_sync_sp(unsigned int *count, unsigned int &target, int *err) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -118,37 +135,63 @@ __device__ __forceinline__ void grid_sync_sp(unsigned int *count, unsigned int &
     __syncthreads();
 }
 
-__global__ void topk_eps_kernel(const float *__restrict__ Phi, int p, int64_t ld, long long k,
-                                unsigned long long *counts /*[31]*/, unsigned int *bar, int *err, float *eps_out) {
-    unsigned int target = 0;
-    unsigned int t = 0;
-    const int64_t total = (int64_t)p * p;
-    for (int bit = 30; bit >= 0; --bit) {
-        const unsigned int cand = t | (1u << bit);
-        unsigned long long c = 0;
-        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-             e += (int64_t)gridDim.x * blockDim.x) {
-            const unsigned int b = __float_as_uint(fabsf(__ldg(Phi + (e / p) * ld + e % p)));
-            c += (b >= cand) ? 1ull : 0ull;
-        }
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        if ((threadIdx.x & 31) == 0 && c) atomicAdd(&counts[bit], c);
-        grid_sync_sp(bar, target, err);
-        if (__ldcg(&counts[bit]) >= (unsigned long long)k) t = cand;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *eps_out = __uint_as_float(t);
-}
+constexpr int kTopkPasses = 4;
+__device__ __constant__ int kTopkShift[kTopkPasses] = {23, 15, 7, 0};
+__device__ __constant__ int kTopkBits[kTopkPasses] = {8, 8, 8, 7};
 
-// flags[i] = 1 when row i of Phi has a nonzero entry (a warp per row).
-__global__ void support_kernel(const float *__restrict__ Phi, int p, int64_t ld, int *flags) {
-    const int lane = threadIdx.x & 31;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < p; i += (gridDim.x * blockDim.x) >> 5) {
-        const float *r = Phi + (int64_t)i * ld;
-        bool nz = false;
-        for (int j = lane; j < p && !nz; j += 32) nz = __ldg(r + j) != 0.f;
-        nz = __any_sync(0xffffffffu, nz);
-        if (lane == 0) flags[i] = nz ? 1 : 0;
+__global__ void __launch_bounds__(256) topk_eps_kernel(const float *__restrict__ Phi, int p, int64_t ld, long long k,
+                                                       unsigned long long *counts /*[4][256]*/, unsigned int *bar,
+                                                       int *err, float *eps_out) {
+    __shared__ unsigned int hist[256];
+    __shared__ unsigned int sel_prefix;
+    __shared__ unsigned long long sel_rank;
+    unsigned int target = 0;
+    unsigned int prefix = 0, pmask = 0;
+    unsigned long long rank = (unsigned long long)k;   // rank among the entries matching prefix
+    const int64_t total = (int64_t)p * p;
+    for (int pass = 0; pass < kTopkPasses; ++pass) {
+        const int sh = kTopkShift[pass];
+        const unsigned int dmask = (1u << kTopkBits[pass]) - 1u;
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0u;
+        __syncthreads();
+        // warp-uniform trip count; lanes with equal bins add once (most
+        // entries share a few exponent bins in the first pass)
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        const int64_t first = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31);
+        for (int64_t e0 = first; e0 < total; e0 += stride) {
+            const int64_t e = e0 + (threadIdx.x & 31);
+            int bin = -1;
+            if (e < total) {
+                const unsigned int b = __float_as_uint(fabsf(__ldg(Phi + (e / p) * ld + e % p)));
+                if ((b & pmask) == prefix) bin = (int)((b >> sh) & dmask);
+            }
+            const unsigned int peers = __match_any_sync(0xffffffffu, bin);
+            if (bin >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned int)__popc(peers));
+        }
+        __syncthreads();
+        unsigned long long *cnt = counts + pass * 256;
+        for (int i = threadIdx.x; i < 256; i += blockDim.x)
+            if (hist[i]) atomicAdd(&cnt[i], (unsigned long long)hist[i]);
+        grid_sync_sp(bar, target, err);
+        if (threadIdx.x == 0) {
+            // the bin of the rank-th largest entry: from the top bin down
+            unsigned long long above = 0;
+            int j = (int)dmask;
+            for (; j > 0; --j) {
+                const unsigned long long c = __ldcg(&cnt[j]);
+                if (above + c >= rank) break;
+                above += c;
+            }
+            sel_prefix = (unsigned int)j;
+            sel_rank = rank - above;
+        }
+        __syncthreads();
+        prefix |= sel_prefix << sh;
+        pmask |= dmask << sh;
+        rank = sel_rank;
+        __syncthreads();
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *eps_out = __uint_as_float(prefix);
 }
 
 // idx[0 .. s) = the flagged rows in ascending order, *s_out = s (one block).
@@ -238,10 +281,7 @@ __global__ void add_transform_gram_kernel(float *F, int p, int64_t ld, int type,
 
 }  // namespace
 
-cudaError_t sparse_support(const float *Phi, int p, int64_t ld, int *flags, int *idx, int *s_dev, cudaStream_t st,
-                           int num_sms) {
-    const int blocks = std::max(1, std::min((p + 7) / 8, num_sms * 4));
-    support_kernel<<<blocks, 256, 0, st>>>(Phi, p, ld, flags);
+cudaError_t compact_support(const int *flags, int p, int *idx, int *s_dev, cudaStream_t st) {
     compact_kernel<<<1, 1024, 0, st>>>(flags, p, idx, s_dev);
     return cudaGetLastError();
 }
@@ -277,18 +317,26 @@ cudaError_t add_transform_gram(float *F, int p, int64_t ld, int type, const doub
     return cudaGetLastError();
 }
 
-cudaError_t make_transform(int type, int p, float *T, int64_t ld, cudaStream_t st, int num_sms) {
+cudaError_t make_transform(int type, int p, float *T, int64_t ld, cudaStream_t st, int num_sms, float *scratch) {
     const int64_t total = (int64_t)p * p;
     int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 8);
-    make_transform_kernel<<<std::max(blocks, 1), 256, 0, st>>>(type, p, T, ld);
+    if (type == CPA_T_DCT) {
+        if (!scratch) return cudaErrorInvalidValue;
+        dct_table_kernel<<<std::max(1, std::min((4 * p + 255) / 256, num_sms * 4)), 256, 0, st>>>(p, scratch);
+    }
+    make_transform_kernel<<<std::max(blocks, 1), 256, 0, st>>>(type, p, T, ld, scratch);
     return cudaGetLastError();
 }
 
 cudaError_t threshold_entries(float *Phi, int p, int64_t ld, const float *eps_dev, float eps_host, cudaStream_t st,
-                              int num_sms, double *removed2) {
+                              int num_sms, double *removed2, int *row_flags) {
     const int64_t total = (int64_t)p * p;
     int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms * 8);
-    threshold_kernel<<<std::max(blocks, 1), 256, 0, st>>>(Phi, p, ld, eps_dev, eps_host, removed2);
+    if (row_flags) {
+        cudaError_t r = cudaMemsetAsync(row_flags, 0, sizeof(int) * (size_t)p, st);
+        if (r != cudaSuccess) return r;
+    }
+    threshold_kernel<<<std::max(blocks, 1), 256, 0, st>>>(Phi, p, ld, eps_dev, eps_host, removed2, row_flags);
     return cudaGetLastError();
 }
 
@@ -301,7 +349,7 @@ cudaError_t symmetrize_lower(float *S, int p, int64_t ld, cudaStream_t st, int n
 
 cudaError_t topk_eps(const float *Phi, int p, int64_t ld, long long k, unsigned long long *counts, unsigned int *bar,
                      int *err, float *eps_out, cudaStream_t st, int num_sms) {
-    cudaError_t r = cudaMemsetAsync(counts, 0, 31 * sizeof(unsigned long long), st);
+    cudaError_t r = cudaMemsetAsync(counts, 0, kTopkCounts * sizeof(unsigned long long), st);
     if (r == cudaSuccess) r = cudaMemsetAsync(bar, 0, sizeof(unsigned int), st);
     if (r == cudaSuccess) r = cudaMemsetAsync(err, 0, sizeof(int), st);
     if (r != cudaSuccess) return r;

@@ -114,3 +114,30 @@ def test_split_bf16(lib, rows, cols, transpose):
     h = Xr.cpu().to(torch.bfloat16)
     assert torch.equal(hi.cpu(), h)
     assert torch.equal(lo.cpu(), (Xr.cpu() - h.float()).to(torch.bfloat16))
+
+
+@pytest.mark.parametrize("p", [1, 7, 64, 300, 1024])
+def test_topk_eps_is_the_kth_largest_magnitude(lib, p):
+    """The entry threshold of the top-k mode (Eq. recommendation_epsilon's
+    K(|Phi|, k)): the k-th largest |Phi_ij| exactly, bit for bit against
+    numpy's sort, with ties, signed zeros, subnormals and a padded row
+    stride, for k = 1, p^2 and values between."""
+    import torch
+    rng = np.random.default_rng(p)
+    Phi = rng.standard_normal((p, p)).astype(np.float32) * np.exp(rng.uniform(-30, 30, (p, p))).astype(np.float32)
+    flat = Phi.ravel()
+    flat[rng.integers(0, flat.size, size=max(1, flat.size // 5))] = 0.0        # exact zeros
+    flat[rng.integers(0, flat.size, size=max(1, flat.size // 7))] = -0.0
+    flat[rng.integers(0, flat.size, size=max(1, flat.size // 9))] = 3.25         # ties
+    flat[rng.integers(0, flat.size, size=max(1, flat.size // 11))] = 1e-40       # subnormal
+    Phi = flat.reshape(p, p)
+    ld = p + 5
+    dev = torch.zeros((p, ld), dtype=torch.float32, device="cuda")
+    dev[:, p:] = 1e30   # padding beyond p must not be read
+    dev[:, :p] = torch.from_numpy(Phi).cuda()
+    srt = np.sort(np.abs(Phi).ravel())[::-1]
+    for k in sorted(k for k in {1, 2, max(1, p * p // 3), max(1, p * p // 2), p * p} if k <= p * p):
+        got = lib.kernel_topk_eps(dev[:, :p], k)
+        assert np.float32(got).view(np.uint32) == np.float32(srt[k - 1]).view(np.uint32), (p, k, got, srt[k - 1])
+    with pytest.raises(lib.CpaError):
+        lib.kernel_topk_eps(dev[:, :p], p * p + 1)
