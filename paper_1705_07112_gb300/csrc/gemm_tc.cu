@@ -619,12 +619,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int sym = e.symmetric_upper;
     const int ntiles = count_tiles(tiles_m, tiles_n, sym, BN);
     const int kb_per = (K + BK - 1) / BK;
-    const int nkb = kb_per * nsplit;
     // g > 0: 3-D operand maps with g slices per load (g divides kb_per);
-    // g == 0: 2-D maps, one slice per stage
+    // g == 0: 2-D maps, one slice per stage; g < 0 (split products, two
+    // slots per stage): 2-D maps, a stage holds one K slice of A hi, A lo,
+    // B hi and B lo and takes all three split products (hi*hi, hi*lo, lo*hi)
+    // from it, so each operand slice is fetched once instead of twice
+    const bool inter = g < 0 && S::kG == 2 && nsplit == 3;
+    const int nkb = inter ? kb_per : kb_per * nsplit;
     const bool tma3d = S::kG > 1 && g > 0;
     const int gs = tma3d ? g : 1;
-    const uint32_t stage_bytes = (uint32_t)gs * (uint32_t)(BM + BN) * (uint32_t)(BK * 2);
+    const uint32_t stage_bytes = (uint32_t)(inter ? 2 : gs) * (uint32_t)(BM + BN) * (uint32_t)(BK * 2);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -670,13 +674,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tile_of(t, tiles_m, tiles_n, sym, BN, tm, tn);
                     const int m0 = tm * BM, n0 = tn * BN;
                     for (int kb = 0; kb < nkb; kb += gs) {
-                        const int seg = kb / kb_per, z = kb % kb_per;
+                        const int seg = inter ? 0 : kb / kb_per, z = inter ? kb : kb % kb_per;
                         if (ms.amask && z > 0 && !ms.amask[tm * ms.mask_groups + z / gs]) continue;
                         if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) break;
                         const CUtensorMap *ma = (seg < 2) ? &maps.a_hi : &maps.a_lo;
                         const CUtensorMap *mb = (seg == 1) ? &sm.b_lo : &sm.b_hi;
                         mbar_expect_tx(&full[stage], stage_bytes);
-                        if (tma3d) {
+                        if (inter) {
+                            // slot 1 starts BM (BN) 128-byte rows after slot 0
+                            uint8_t *a0 = sA + stage * S::kStageA, *b0 = sB + stage * S::kStageB;
+                            tma_load_2d(a0, &maps.a_hi, &full[stage], z * BK, m0);
+                            tma_load_2d(a0 + BM * BK * 2, &maps.a_lo, &full[stage], z * BK, m0);
+                            tma_load_2d(b0, &sm.b_hi, &full[stage], z * BK, n0);
+                            tma_load_2d(b0 + BN * BK * 2, &sm.b_lo, &full[stage], z * BK, n0);
+                        } else if (tma3d) {
                             tma_load_3d(sA + stage * S::kStageA, ma, &full[stage], 0, m0, z);
                             tma_load_3d(sB + stage * S::kStageB, mb, &full[stage], 0, n0, z);
                         } else {
@@ -735,7 +746,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                         fence_after();
                         const uint64_t da = smem_desc(su32(sA + stage * S::kStageA));
                         const uint64_t db = smem_desc(su32(sB + stage * S::kStageB));
-                        for (int sub = 0; sub < gs; ++sub) {
+                        if (inter) {
+                            // hi*hi, hi*lo, lo*hi of this K slice (slot 1 = lo)
+                            const uint64_t dal = da + (uint64_t)(BM * 8), dbl = db + (uint64_t)(BN * 8);
+#pragma unroll
+                            for (int kk = 0; kk < BK / 16; ++kk) {
+                                mma_bf16(d_tmem, da + 2 * kk, db + 2 * kk, kIdesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                                mma_bf16(d_tmem, da + 2 * kk, dbl + 2 * kk, kIdesc, 1u);
+                                mma_bf16(d_tmem, dal + 2 * kk, db + 2 * kk, kIdesc, 1u);
+                            }
+                        }
+                        for (int sub = 0; sub < (inter ? 0 : gs); ++sub) {
                             // slice sub starts BM (BN) 128-byte rows further on;
                             // descriptor addresses count 16-byte units
                             const uint64_t das = da + (uint64_t)(sub * BM * 8), dbs = db + (uint64_t)(sub * BN * 8);
@@ -996,8 +1017,11 @@ cudaError_t launch(int M, int N, int K, const TcOperand &A, const TcOperand &B, 
     memset(&maps, 0, sizeof(maps));
     const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32, b16 = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     const __nv_bfloat16 *alo = A.lo ? A.lo : A.hi;
-    // grouped 3-D loads need whole 64-element slices (no K tail to fill)
-    const int g = (S::kG > 1 && K % BK == 0 && (K / BK) % S::kG == 0) ? S::kG : 0;
+    // split products with two-slot stages: interleaved hi/lo slices (2-D
+    // maps, g = -1); else grouped 3-D loads, which need whole 64-element
+    // slices (no K tail to fill)
+    const int g = (S::kG == 2 && nsplit == 3) ? -1
+                  : (S::kG > 1 && K % BK == 0 && (K / BK) % S::kG == 0) ? S::kG : 0;
     auto opmap = [&](CUtensorMap *m, const __nv_bfloat16 *ptr, int64_t ld, int rows, int box_rows) {
         return g > 0 ? make_map3(m, ptr, ld, rows, K, box_rows, g) : make_map(m, ptr, ld, rows, K, box_rows);
     };
@@ -1129,8 +1153,8 @@ cudaError_t gemm_tc_recurrence(int p, const TcOperand &A, int nsplit, const Epil
     if (K > A.ld) return cudaErrorInvalidValue;
     if (mask_buf) {
         // the K slices per stage of this launch: 2 when the grouped 3-D
-        // loads apply (K a multiple of 128 below BN = 256), else 1
-        const int gs = (bn < 256 && K % 128 == 0) ? 2 : 1;
+        // loads apply (K a multiple of 128 below BN = 256, one product), else 1
+        const int gs = (bn < 256 && K % 128 == 0 && nsplit != 3) ? 2 : 1;
         const int width = 64 * gs;
         ms.mask_groups = (K + width - 1) / width;
         amask_kernel<<<dim3(ms.mask_groups, (p + 127) / 128), 256, 0, st>>>(A.hi, A.lo, A.ld, p, K, width, mask_buf,
