@@ -41,6 +41,10 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the served mix runs its larger members on up to 32 streams side by side;
+# the device gives a process 8 hardware work queues unless this is raised
+# before CUDA starts (streams beyond the queues share them and serialise)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "SVT matrices/sec & tensor-pipe % at ≤1e-3 rel-Frob err: learned+BF16 vs plain FP32 CPA"
 L2_BYTES = 129 * 1024 * 1024
@@ -53,7 +57,7 @@ NCU_TRAFFIC = {("rpca_frame", "bf16"): 8.644608e6 + 0.498944e6,
 # tensor-pipe utilisation (%) of the dominant kernel (of the active cycles of
 # the SMs it runs on), from the committed ncu summaries under profiles/
 # (recurrence_served_mix_members.md); drop an entry when its kernel changes
-NCU_TENSOR_PIPE = {"served_mix": 22.74}
+NCU_TENSOR_PIPE = {"served_mix": 33.90}
 SEED = 0x1705071120000000
 
 
@@ -1226,8 +1230,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--served", type=int, default=5000, help="matrices of the served mix")
     ap.add_argument("--served-L-max", type=int, default=384)
-    ap.add_argument("--streams", type=int, default=8, help="concurrent streams for the served mix's larger members")
-    ap.add_argument("--member-sms", type=int, default=38,
+    ap.add_argument("--streams", type=int, default=32, help="concurrent streams for the served mix's larger members")
+    ap.add_argument("--member-sms", type=int, default=10,
                     help="SMs each larger member's launches are sized for (0: all), so several run side by side")
     ap.add_argument("--predicted-bound", action="store_true",
                     help="serve the predictor's Lambda_max instead of the 20-step power bound")

@@ -244,7 +244,10 @@ CPA_API cpa_status cpa_get_coeffs(cpa_handle h, double *c_out, int L, void *stre
  *   not taken by the batched kernel) round-robin on this many streams, each
  *   with a workspace of its own, forked from and joined back into the
  *   call's stream; matrices too small to fill the GPU then run side by
- *   side.  The results are those of one stream. */
+ *   side.  The results are those of one stream.  The device runs the work
+ *   of at most CUDA_DEVICE_MAX_CONNECTIONS streams side by side (an
+ *   environment variable read when the process first uses CUDA; 8 unless
+ *   set, 32 at most): more streams than that share its work queues. */
 /* CPA_OPT_MEMBER_SMS: >= 0 (default 0, all): the SMs each of those members'
  *   launches is sized for (tile widths and grids of its products, bound and
  *   recurrence), so that several large members run side by side instead of
