@@ -264,13 +264,15 @@ __device__ __forceinline__ void store_transposed_bf16x8(const Epilogue &e, const
 // Issues the TMA loads of one block's inputs (C, C2, H at the mirrored
 // position) into the warp's buffers, once the previous block's TMA stores
 // have finished reading them.
-__device__ __forceinline__ void epilogue_issue_loads(const Epilogue &e, const StepMaps &maps, const CUtensorMap &hmap,
+// Returns whether loads were issued (a phase of `bar` is then pending).
+__device__ __forceinline__ bool epilogue_issue_loads(const Epilogue &e, const StepMaps &maps, const CUtensorMap &hmap,
                                                      int r0, int j0, int lane, EpiSmem &es, uint64_t *bar) {
     fence_proxy_async();
     __syncwarp();
+    const bool any = e.C || e.C2 || e.H;
     if (lane == 0) {
         bulk_wait_read_all();
-        if (e.C || e.C2 || e.H) {
+        if (any) {
             const uint32_t bytes = 4096u * ((e.C ? 1u : 0u) + (e.C2 ? 1u : 0u) + (e.H ? 1u : 0u));
             mbar_expect_tx(bar, bytes);
             if (e.C) tma_load_2d(es.c, &maps.c, bar, r0, j0);
@@ -279,18 +281,19 @@ __device__ __forceinline__ void epilogue_issue_loads(const Epilogue &e, const St
         }
     }
     __syncwarp();
+    return any;
 }
 
 __device__ __forceinline__ void epilogue_sym_block(const Epilogue &e, const StepMaps &maps, const CUtensorMap &hmap,
                                                    float ck, int M, int N,
                                                    int r0, int j0, int lane, const float *acc, EpiSmem &es,
                                                    uint64_t *bar, uint32_t &phase, volatile int *abort_flag,
-                                                   bool preloaded, const CUtensorMap *dmap) {
+                                                   bool preloaded, const CUtensorMap *dmap, int next_j0, bool &epend) {
     const bool diag = (j0 == r0);
     const bool any_load = e.C || e.C2 || e.H;
-    if (!preloaded) epilogue_issue_loads(e, maps, hmap, r0, j0, lane, es, bar);
+    if (!preloaded) epend = epilogue_issue_loads(e, maps, hmap, r0, j0, lane, es, bar) || epend;
     if (any_load) {
-        mbar_wait(bar, phase, abort_flag);
+        if (mbar_wait(bar, phase, abort_flag)) epend = false;
         phase ^= 1u;
     }
     const int i = r0 + lane;
@@ -366,7 +369,15 @@ __device__ __forceinline__ void epilogue_sym_block(const Epilogue &e, const Step
         }
         bulk_commit();
     }
-    if (diag) return;
+    // the next block's inputs do not depend on its accumulator: once this
+    // block's inputs are no longer read (the stores above read c and h from
+    // shared memory; the full-D copy below reads c), load them, so that
+    // their latency overlaps this block's remaining stores and the next
+    // block's accumulator read
+    if (diag) {
+        if (next_j0 >= 0) epend = epilogue_issue_loads(e, maps, hmap, r0, next_j0, lane, es, bar) || epend;
+        return;
+    }
     // upper positions (i, j): the transposed values of the mirrored block
     if (e.sym_full_d) {
 #pragma unroll
@@ -375,6 +386,7 @@ __device__ __forceinline__ void epilogue_sym_block(const Epilogue &e, const Step
         store_transposed(e, es.t, 0, M, N, r0, j0, lane, false);
         __syncwarp();
     }
+    if (next_j0 >= 0) epend = epilogue_issue_loads(e, maps, hmap, r0, next_j0, lane, es, bar) || epend;
     if (e.Dhi) {
 #pragma unroll
         for (int c = 0; c < 32; ++c) es.t[lane * 33 + c] = hl[c];
@@ -400,7 +412,8 @@ __device__ __forceinline__ void epilogue_res_block(const Epilogue &e, const Step
                                                    const float *acc, EpiSmem &es, uint64_t *bar, uint32_t &phase,
                                                    volatile int *abort_flag, bool preloaded, const CUtensorMap *dmap,
                                                    bool from_tmem, uint32_t tC, uint32_t tC2, uint32_t tH,
-                                                   bool store_d, bool store_h, bool close, float close_diag) {
+                                                   bool store_d, bool store_h, bool close, float close_diag,
+                                                   bool &epend) {
     const bool diag = (j0 == r0);
     const bool hasc = e.C != nullptr, hasc2 = e.C2 != nullptr, hact = e.H != nullptr;
     if (from_tmem) {
@@ -409,9 +422,9 @@ __device__ __forceinline__ void epilogue_res_block(const Epilogue &e, const Step
         if (lane == 0) bulk_wait_read_all();
         __syncwarp();
     } else {
-        if (!preloaded) epilogue_issue_loads(e, maps, hmap, r0, j0, lane, es, bar);
+        if (!preloaded) epend = epilogue_issue_loads(e, maps, hmap, r0, j0, lane, es, bar) || epend;
         if (hasc || hasc2 || hact) {
-            mbar_wait(bar, phase, abort_flag);
+            if (mbar_wait(bar, phase, abort_flag)) epend = false;
             phase ^= 1u;
         }
     }
@@ -782,6 +795,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         EpiSmem &es = epi[quarter];
         uint64_t *bar = &ebar[quarter];
         uint32_t ephase = 0;
+        bool epend = false;   // a phase of this warp's block-load barrier is still to complete
         uint32_t tphase[2] = {0, 0};
         int local = 0;
         unsigned int target = 0;
@@ -838,7 +852,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                             break;
                         }
                     }
-                    if (c_pre >= 0) epilogue_issue_loads(es_e, maps.s[par], maps.h, r0, n0 + c_pre * 32, lane, es, bar);
+                    if (c_pre >= 0)
+                        epend = epilogue_issue_loads(es_e, maps.s[par], maps.h, r0, n0 + c_pre * 32, lane, es, bar) ||
+                                epend;
                 }
                 if (!mbar_wait(&tfull[buf], tphase[buf], abort_flag)) {
                     alive = false;
@@ -860,12 +876,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const uint32_t tq = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(c * 32);
                             epilogue_res_block(es_e, maps.s[par], maps.h, ck, M, N, r0, j0, lane, acc, es, bar,
                                                ephase, abort_flag, c == c_pre, dmap, !first, tq + sC, tq + sC2,
-                                               tq + sH, final_to_h, store_h, close, close_diag);
+                                               tq + sH, final_to_h, store_h, close, close_diag, epend);
                             continue;
                           }
                         }
+                        // the tile's next block on or above the diagonal: its
+                        // inputs are loaded ahead, at the end of this block
+                        int c_next = -1;
+                        for (int c2 = c + 1; c2 < BN / 32; ++c2) {
+                            const int jn = n0 + c2 * 32;
+                            if (jn < N && jn >= r0) {
+                                c_next = c2;
+                                break;
+                            }
+                        }
                         epilogue_sym_block(es_e, maps.s[par], maps.h, ck, M, N, r0, j0, lane, acc, es, bar, ephase,
-                                           abort_flag, c == c_pre, dmap);
+                                           abort_flag, c == c_pre, dmap, c_next >= 0 ? n0 + c_next * 32 : -1, epend);
+                        if (c_next >= 0) c_pre = c_next;
                     } else {
                         epilogue_general_block(es_e, M, N, r0, j0, lane, acc, es);
                     }
@@ -904,8 +931,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (*abort_flag) alive = false;
             }
         }
-        // the last TMA stores must complete before the CTA exits
-        if (lane == 0) bulk_wait_all();
+        // the last TMA stores must complete before the CTA exits, and a block
+        // load still in flight (a wait that gave up) must land first
+        if (lane == 0) {
+            bulk_wait_all();
+            if (epend) {
+                const long long t0 = clock64();
+                while (!mbar_try_wait(bar, ephase) && clock64() - t0 < kWaitCycles) {
+                }
+            }
+        }
         __syncwarp();
     }
 
