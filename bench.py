@@ -913,6 +913,7 @@ def _served_finish(args, world, rank, local, cpa, h, net, rule, mix, Xs, Yl, Yp,
                 for i in big)
     rec = prof["recur"]
     rec_ms = rec["ms"]
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     achieved = flops / (rec_ms / 1e3) / 1e12 if rec_ms > 0 else None
     stage_ms = {k: v["ms"] for k, v in prof.items()}
     roof = {"kernel": "recurrence (cooperative tcgen05 launch per single-matrix member, BF16 split)",
@@ -920,6 +921,10 @@ def _served_finish(args, world, rank, local, cpa, h, net, rule, mix, Xs, Yl, Yp,
             "frac": (achieved / peaks["bf16_tflops"]) if achieved else None, "traffic": None,
             "flops_per_step": flops, "recurrence_ms_per_step": rec_ms, "launches_per_step": rec["launches"],
             "recurrence_sms_per_launch": args.member_sms or None,
+            # the same rate against the share of the peak that the SMs a
+            # launch is sized for can deliver
+            "frac_of_launch_sms": (achieved / (peaks["bf16_tflops"] * min(args.member_sms, n_sms) / n_sms)
+                                   if achieved and args.member_sms else None),
             # the same flops over the timed step's wall time, all launches
             # side by side (the served throughput's own rate)
             "aggregate_tflops_in_timed_step": flops / (ms_l / args.steps / 1e3) / 1e12,

@@ -1083,7 +1083,11 @@ cudaError_t launch(int M, int N, int K, const TcOperand &A, const TcOperand &B, 
         if (!ok) return cudaErrorInvalidValue;
     }
     const int tiles = count_tiles((M + BM - 1) / BM, (N + BN - 1) / BN, e.symmetric_upper, BN);
-    const int grid = tiles < num_sms ? tiles : num_sms;
+    // as many waves of tiles as num_sms CTAs need, over the fewest CTAs that
+    // keep that count (every CTA then takes the same number of tiles; the
+    // SMs left over stay free for other work, e.g. other members' launches)
+    const int waves = tiles > num_sms ? (tiles + num_sms - 1) / num_sms : 1;
+    const int grid = tiles > 0 ? (tiles + waves - 1) / waves : 1;
     if (!ms.multi) {
         gemm_tc_kernel<BN><<<grid, kThreads, S::kBytes, st>>>(maps, M, N, K, nsplit, g, e, ms, err);
         return cudaGetLastError();

@@ -231,3 +231,31 @@ def test_router_streams_match_one_stream(lib):
         lib.cpa_set_option(h, lib.OPT_STREAMS, 65)
     net.close()
     h.close()
+
+
+def test_member_sm_budget_keeps_results(lib):
+    """Members' launches sized for a few SMs (CPA_OPT_MEMBER_SMS) on several
+    streams give the results of full-GPU launches on one stream: the tile
+    widths and grids change, the arithmetic per element does not beyond FP32
+    summation order.  Given bounds and orders, so the comparison is of the
+    recurrence and products alone."""
+    import torch
+    h = lib.Handle(0)
+    mix = inputs.served_mix(48, seed_index=11)
+    Xs = [torch.from_numpy(sm.X).cuda() for sm in mix]
+    specs = [spec_dict(sm.shrink) for sm in mix]
+    lams = [1.02 * float(np.linalg.norm(sm.X.astype(np.float64), 2)) ** 2 for sm in mix]
+    outs = []
+    for streams, sms in ((1, 0), (6, 10), (6, 3)):
+        lib.cpa_set_option(h, lib.OPT_STREAMS, streams)
+        lib.cpa_set_option(h, lib.OPT_MEMBER_SMS, sms)
+        Ys = [torch.zeros_like(X) for X in Xs]
+        lib.cpa_svt_batched(h, lib.MemberList(Xs, Ys, specs), L0=60, lambdas=lams, prec="bf16x3")
+        torch.cuda.synchronize()
+        outs.append([Y.cpu().numpy().astype(np.float64) for Y in Ys])
+    lib.cpa_set_option(h, lib.OPT_STREAMS, 1)
+    lib.cpa_set_option(h, lib.OPT_MEMBER_SMS, 0)
+    for other in outs[1:]:
+        for a, b, sm in zip(outs[0], other, mix):
+            assert rel(b, a) <= 1e-5, (sm.X.shape, rel(b, a))
+    h.close()
