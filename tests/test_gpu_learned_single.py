@@ -236,9 +236,11 @@ def test_router_streams_match_one_stream(lib):
 def test_member_sm_budget_keeps_results(lib):
     """Members' launches sized for a few SMs (CPA_OPT_MEMBER_SMS) on several
     streams give the results of full-GPU launches on one stream: the tile
-    widths and grids change, the arithmetic per element does not beyond FP32
-    summation order.  Given bounds and orders, so the comparison is of the
-    recurrence and products alone."""
+    widths and grids change, and with them only the order of the FP32 sums
+    of the split products (interleaved below BN = 256, by product at 256).
+    Given bounds and orders, so the comparison is of the recurrence and
+    products alone; the bar is a tenth of the BF16X3 tolerance against the
+    oracle (2e-3), ten times the split arithmetic's measured error."""
     import torch
     h = lib.Handle(0)
     mix = inputs.served_mix(48, seed_index=11)
@@ -257,5 +259,5 @@ def test_member_sm_budget_keeps_results(lib):
     lib.cpa_set_option(h, lib.OPT_MEMBER_SMS, 0)
     for other in outs[1:]:
         for a, b, sm in zip(outs[0], other, mix):
-            assert rel(b, a) <= 1e-5, (sm.X.shape, rel(b, a))
+            assert rel(b, a) <= 1e-4, (sm.X.shape, rel(b, a))
     h.close()
