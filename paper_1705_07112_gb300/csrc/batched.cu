@@ -387,7 +387,7 @@ __device__ __noinline__ Choice learned_phase(BatchSmem &S, int idx, int p, int q
         // (W1 stride 13, W2 stride 65: conflict-free), then one output per
         // thread in the summation order of the network's own forward
         // kernel (same FP32 results).
-        constexpr int oW1 = 0, ob1 = kHidden * kFeatures, oW2 = ob1 + kHidden, ob2 = oW2 + kHidden * kHidden,
+        constexpr int ob1 = kHidden * kFeatures, oW2 = ob1 + kHidden, ob2 = oW2 + kHidden * kHidden,
                       oW3 = ob2 + kHidden, ob3 = oW3 + 2 * kHidden, nP = ob3 + 2;
         constexpr int sW1 = 0, sb1 = kHidden * (kFeatures + 1), sW2 = sb1 + kHidden,
                       sb2 = sW2 + kHidden * (kHidden + 1), sW3 = sb2 + kHidden, sb3 = sW3 + 2 * kHidden;

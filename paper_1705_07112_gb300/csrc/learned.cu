@@ -140,8 +140,6 @@ __global__ void __launch_bounds__(kThreads) learn_bound_kernel(
     __shared__ Partials part;
     __shared__ float fv[kFeat];
     __shared__ float h1s[kHid], h2s[kHid], ys[2];
-    __shared__ double dec[2];
-    __shared__ int decL;
     unsigned int target = 0;
     const int lane = threadIdx.x & 31;
     const int gwarp = (blockIdx.x * kThreads + threadIdx.x) >> 5;
@@ -391,8 +389,6 @@ __global__ void __launch_bounds__(kThreads) learn_bound_kernel(
                 out[4] = status;
                 L_out[0] = Lc;
                 L_out[1] = (!ok_L || !ok_lam) ? 1 : 0;
-                dec[0] = lc;
-                decL = Lc;
                 tabg[0] = lc;   // broadcast to the other blocks
                 reinterpret_cast<int *>(tabg)[2] = Lc;
             }
